@@ -1,0 +1,154 @@
+/*
+ * nufft3d.h -- C ABI of the GB300 radial-line 3D NUFFT projector.
+ *
+ * The library computes the image-to-Radon step of a Fourier-based cone-beam CT
+ * forward projector (the paper's Sec. 2, step 1, and Sec. 2.2.1) and its
+ * transpose (the backprojection direction of Sec. 2.3):
+ *
+ *   forward   p = L_w  T  F  P  x
+ *   adjoint   x~ = P^H F^H T^H L_w^H p
+ *
+ *   P   deapodisation (the diagonal pre-scaling P of Eq. 2.11) of the N^3 volume
+ *       and zero padding to the oversampled K^3 grid;
+ *   F   unnormalised 3D DFT on the K^3 grid (e^{-i}, centred voxel index
+ *       n in [-N/2, N/2)^3);
+ *   T   separable J-tap min-max interpolation (the sparse interpolator
+ *       T_sparse of Eq. 2.11) onto points omega_{l,q} = r_q d_l on radial
+ *       lines through the origin (Eq. 2.1);
+ *   L_w per-line centred inverse DFT with radial weight w[q] and 1/M scaling,
+ *       which turns Fourier samples on a line into plane integrals by the
+ *       Fourier Slice Theorem (Sec. 2.2.1).
+ *
+ * Conventions
+ *   volume  C-ordered [z][y][x], x fastest, N^3 elements; float32 (real) or
+ *           interleaved complex64; voxel (z,y,x) has centred index
+ *           n = (x - N/2, y - N/2, z - N/2).
+ *   lines   [dir][m], m fastest, interleaved complex64, n_dirs * M elements;
+ *           sample m has radial index q = m - M/2; line-FFT output index t has
+ *           plane offset s = t - M/2 (voxel units along d).
+ *   dirs    unit vectors (x, y, z) in float64, copied at plan creation.
+ *   grid    u = omega / gamma, gamma = 2 pi / K; taps k0 + 1 .. k0 + J with
+ *           k0 = floor(u) - J/2 (J even); coefficients from a table of the
+ *           min-max interpolator at f = i / L, linearly interpolated.
+ *
+ * Ownership and threading
+ *   The caller owns every device buffer passed in and the CUDA stream.  A plan
+ *   owns its tables, its point sort and its workspace (device memory allocated
+ *   at creation).  All compute calls are asynchronous on the given stream; a
+ *   status raised by a device-side check is kept in a device word and
+ *   returned by nufft3d_plan_sync_status.  A plan must not be used from two
+ *   host threads at once; distinct plans are independent.
+ *
+ * Errors
+ *   Every function returns a nufft3d_status (0 = success).  No function
+ *   aborts, throws across the ABI or traps on the device.
+ */
+#ifndef NUFFT3D_H
+#define NUFFT3D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nufft3d_plan_s* nufft3d_plan;   /* opaque, library-owned */
+
+typedef enum {
+  NUFFT3D_OK = 0,
+  NUFFT3D_ERR_ARG = -1,           /* invalid argument (NULL, size out of range)        */
+  NUFFT3D_ERR_NOMEM = -2,         /* device or host allocation failed                 */
+  NUFFT3D_ERR_CUDA = -3,          /* a CUDA runtime call failed                        */
+  NUFFT3D_ERR_UNSUPPORTED = -4,   /* valid request this build does not implement       */
+  NUFFT3D_ERR_TIMEOUT = -5,       /* a bounded device wait ran out                     */
+  NUFFT3D_ERR_DEVICE_CHECK = -6   /* a device-side consistency check failed            */
+} nufft3d_status;
+
+typedef enum {
+  NUFFT3D_GRID_C64 = 0,           /* oversampled grid stored as complex64              */
+  NUFFT3D_GRID_BF16 = 1,          /* forward grid stored as bf16 pairs, FP32 math      */
+  NUFFT3D_GRID_FP16 = 2           /* forward grid stored as fp16 pairs, FP32 math      */
+} nufft3d_grid_dtype;
+
+typedef struct {
+  int n;                  /* volume edge N: even, 8 <= N <= 512                        */
+  int k;                  /* grid edge K: 0 selects 2N; K >= N, K = 2^a 3^b, K <= 1024 */
+  int j;                  /* taps per axis J: even, 2 <= J <= 8 (0 selects 6)          */
+  int table_oversamp;     /* coefficient table oversampling L (0 selects 1024), 2^p    */
+  int n_dirs;             /* number of radial lines D >= 1                             */
+  const double* dirs;     /* host, D x 3 unit vectors (x, y, z); copied               */
+  int m;                  /* samples per line M: even, 0 selects 2N; M = 2^a 3^b, <= 1024 */
+  const double* omega;    /* host, M radial frequencies (rad/voxel), or NULL for
+                             2 pi (m - M/2) / M; |omega| <= pi; copied                 */
+  const float* weight;    /* host, M interleaved complex radial weights w[q], or NULL
+                             for w = 1; copied                                         */
+  int grid_dtype;         /* nufft3d_grid_dtype                                        */
+  int complex_volume;     /* 0: float32 real volume in/out; 1: complex64              */
+  int do_line_fft;        /* 1: plane integrals (line inverse DFT applied);
+                             0: raw Fourier samples X^(omega) (no line DFT)            */
+} nufft3d_params;
+
+/* Create a plan.  Validates *p, computes in FP64 on the host the scaling
+ * factors s(n) (Kaiser-Bessel pre-window, Eq. 2.11), the min-max coefficient
+ * table and the FFT twiddles, uploads them, sorts the D*M points by grid tile
+ * (a device pass plus a host counting sort) and allocates the workspace, all
+ * on `cuda_stream` (a cudaStream_t, may be NULL for the legacy stream), which
+ * it synchronises before returning.  On success *out holds a new plan; on
+ * failure *out is NULL and nothing is leaked. */
+int nufft3d_plan_create(nufft3d_plan* out, const nufft3d_params* p, void* cuda_stream);
+
+/* Forward projection: vol_dev (device, N^3 float32 or complex64 per
+ * complex_volume) -> lines_dev (device, D*M complex64).  Enqueued on
+ * cuda_stream; buffers must not overlap; vol_dev is not modified.  The
+ * workspace of the plan is used, so calls on one plan serialise on the stream. */
+int nufft3d_forward(nufft3d_plan plan, const void* vol_dev, void* lines_dev, void* cuda_stream);
+
+/* Adjoint (backprojection direction): lines_dev (device, D*M complex64) ->
+ * vol_dev (device, N^3 float32 = real part, or complex64).  lines_dev is not
+ * modified.  Exact conjugate transpose of nufft3d_forward for complex volumes;
+ * for real volumes the adjoint with respect to Re<.,.>. */
+int nufft3d_adjoint(nufft3d_plan plan, const void* lines_dev, void* vol_dev, void* cuda_stream);
+
+/* Bytes of device memory a plan with these parameters holds (tables, point
+ * sort, workspace).  Host only: touches no device. */
+int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes);
+
+/* Synchronise the plan's last stream and return, in *device_status, the
+ * device-side check word (0 = clean; otherwise a nufft3d_status); the word is
+ * cleared.  Returns NUFFT3D_ERR_CUDA if the synchronisation itself failed. */
+int nufft3d_plan_sync_status(nufft3d_plan plan, int* device_status);
+
+/* Free a plan and everything it owns (NULL is accepted). */
+int nufft3d_plan_destroy(nufft3d_plan plan);
+
+/* Static description of a status code (never NULL). */
+const char* nufft3d_error_string(int status);
+
+/* Numbers of the plan: points P = D*M, tiles, subproblems, tile edge,
+ * gather/spread variants; out must hold 8 ints.  For tests and tuning. */
+int nufft3d_plan_info(nufft3d_plan plan, int* out);
+
+/* Select the gather and spread kernel variants (0: one thread per point,
+ * 1: one warp per point; -1 keeps the current choice) and the number of
+ * points per subproblem (0 keeps it) of a plan.  Synchronises the plan's
+ * last stream; rebuilds the subproblem list on cuda_stream.  Used by the
+ * autotuner. */
+int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
+                      int points_per_subproblem, void* cuda_stream);
+
+/* Per-stage timing with CUDA events recorded on the launching stream between
+ * the kernels of each call.  nufft3d_plan_set_timing(plan, n) arms timing of
+ * the next n forward and n adjoint calls (0 disarms; it synchronises the
+ * plan's last stream and recreates the events).  nufft3d_plan_stage_times
+ * synchronises, writes the summed milliseconds of each stage of the recorded
+ * calls to fwd_ms[5] (x pass, y pass, z pass, gather, line DFT) and
+ * adj_ms[6] (line DFT, grid clear, spread, z pass, y pass, x pass), the
+ * numbers of recorded forward and adjoint calls to calls[2], and re-arms. */
+int nufft3d_plan_set_timing(nufft3d_plan plan, int max_calls);
+int nufft3d_plan_stage_times(nufft3d_plan plan, float* fwd_ms, float* adj_ms, int* calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUFFT3D_H */

@@ -1,1 +1,6 @@
-"""GB300-native radial-line 3D NUFFT projector (forward + adjoint)."""
+"""GB300-native radial-line 3D NUFFT projector (forward + adjoint).
+
+The compute runs in libnufft3d.so (hand-written CUDA for sm_103a) behind the
+C ABI of include/nufft3d.h; ``binding`` marshals torch tensors to it.
+"""
+from .binding import Plan, NufftError, load_library, project, workspace_bytes  # noqa: F401

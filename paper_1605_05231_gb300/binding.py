@@ -1,0 +1,304 @@
+"""Python binding of libnufft3d: argument marshalling over the C ABI only.
+
+Every step of the projector runs in the library's CUDA kernels; this module
+checks shapes, dtypes and devices of torch tensors, passes their device
+pointers and the current CUDA stream to the C entry points, and turns status
+codes into exceptions.  There is no CPU fallback: without the built library
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libnufft3d.so")
+
+EXPORTS = (
+    "nufft3d_plan_create",
+    "nufft3d_forward",
+    "nufft3d_adjoint",
+    "nufft3d_workspace_bytes",
+    "nufft3d_plan_sync_status",
+    "nufft3d_plan_destroy",
+    "nufft3d_error_string",
+    "nufft3d_plan_info",
+    "nufft3d_plan_tune",
+    "nufft3d_plan_set_timing",
+    "nufft3d_plan_stage_times",
+)
+
+FWD_STAGES = ("x_pass", "y_pass", "z_pass", "gather", "line_dft")
+ADJ_STAGES = ("line_dft", "grid_clear", "spread", "z_pass", "y_pass", "x_pass")
+
+GRID_DTYPES = {"c64": 0, "complex64": 0, "bf16": 1, "fp16": 2, "f16": 2}
+
+
+class Params(ctypes.Structure):
+    """Mirror of nufft3d_params (include/nufft3d.h)."""
+
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("k", ctypes.c_int),
+        ("j", ctypes.c_int),
+        ("table_oversamp", ctypes.c_int),
+        ("n_dirs", ctypes.c_int),
+        ("dirs", ctypes.POINTER(ctypes.c_double)),
+        ("m", ctypes.c_int),
+        ("omega", ctypes.POINTER(ctypes.c_double)),
+        ("weight", ctypes.POINTER(ctypes.c_float)),
+        ("grid_dtype", ctypes.c_int),
+        ("complex_volume", ctypes.c_int),
+        ("do_line_fft", ctypes.c_int),
+    ]
+
+
+class NufftError(RuntimeError):
+    def __init__(self, what: str, status: int):
+        super().__init__(f"{what}: {error_string(status)} (status {status})")
+        self.status = status
+
+
+_LIB = None
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libnufft3d.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(the projector has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, ip, i = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int
+    lib.nufft3d_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), vp]
+    lib.nufft3d_forward.argtypes = [vp, vp, vp, vp]
+    lib.nufft3d_adjoint.argtypes = [vp, vp, vp, vp]
+    lib.nufft3d_workspace_bytes.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
+    lib.nufft3d_plan_sync_status.argtypes = [vp, ip]
+    lib.nufft3d_plan_destroy.argtypes = [vp]
+    lib.nufft3d_error_string.argtypes = [i]
+    lib.nufft3d_error_string.restype = ctypes.c_char_p
+    lib.nufft3d_plan_info.argtypes = [vp, ip]
+    lib.nufft3d_plan_tune.argtypes = [vp, i, i, i, vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.nufft3d_plan_set_timing.argtypes = [vp, i]
+    lib.nufft3d_plan_stage_times.argtypes = [vp, fp, fp, ip]
+    for name in EXPORTS:
+        if name != "nufft3d_error_string":
+            getattr(lib, name).restype = ctypes.c_int
+    if path == LIB_PATH:
+        _LIB = lib
+    return lib
+
+
+def error_string(status: int) -> str:
+    try:
+        return load_library().nufft3d_error_string(int(status)).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise NufftError(what, rc)
+
+
+def make_params(n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=None, grid_dtype="c64",
+                complex_volume=False, do_line_fft=True):
+    """Build a Params struct plus the host arrays it points to (kept alive by the caller)."""
+    dirs = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
+    keep = [dirs]
+    p = Params()
+    p.n = int(n)
+    p.k = int(k)
+    p.j = int(j)
+    p.table_oversamp = int(table_oversamp)
+    p.n_dirs = int(dirs.shape[0])
+    p.dirs = dirs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.m = int(m)
+    if omega is not None:
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        keep.append(om)
+        p.omega = om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if weight is not None:
+        w = np.asarray(weight, dtype=np.complex64)
+        wf = np.ascontiguousarray(np.stack([w.real, w.imag], axis=-1).astype(np.float32))
+        keep.append(wf)
+        p.weight = wf.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    p.grid_dtype = GRID_DTYPES[grid_dtype] if isinstance(grid_dtype, str) else int(grid_dtype)
+    p.complex_volume = 1 if complex_volume else 0
+    p.do_line_fft = 1 if do_line_fft else 0
+    return p, keep
+
+
+def workspace_bytes(**kw) -> int:
+    p, keep = make_params(**kw)
+    out = ctypes.c_size_t(0)
+    _check(load_library().nufft3d_workspace_bytes(ctypes.byref(p), ctypes.byref(out)), "nufft3d_workspace_bytes")
+    return int(out.value)
+
+
+def _stream_ptr(stream, device):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A projector plan: N^3 volume <-> D radial lines of M samples.
+
+    forward(x): x (N, N, N) float32 (or complex64 with complex_volume) on the
+    plan's CUDA device -> (D, M) complex64 plane integrals (or raw Fourier
+    samples with do_line_fft=False).  adjoint(y): the transpose.
+    """
+
+    def __init__(self, n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=None,
+                 grid_dtype="c64", complex_volume=False, do_line_fft=True, device=None, stream=None):
+        import torch
+
+        self.lib = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        p, keep = make_params(n, dirs, m, k, j, table_oversamp, omega, weight, grid_dtype, complex_volume,
+                              do_line_fft)
+        self.n = int(n)
+        self.n_dirs = p.n_dirs
+        self.m = int(m) if m else 2 * int(n)
+        self.k = int(k) if k else 2 * int(n)
+        self.j = int(j)
+        self.complex_volume = bool(complex_volume)
+        self.do_line_fft = bool(do_line_fft)
+        self._handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.nufft3d_plan_create(ctypes.byref(self._handle), ctypes.byref(p),
+                                                _stream_ptr(stream, self.device)), "nufft3d_plan_create")
+        del keep
+
+    # -- shapes ------------------------------------------------------------
+    @property
+    def n_points(self) -> int:
+        return self.n_dirs * self.m
+
+    @property
+    def vol_dtype(self):
+        import torch
+
+        return torch.complex64 if self.complex_volume else torch.float32
+
+    def _check_tensor(self, t, shape, dtype, name):
+        import torch
+
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+        if t.device != self.device:
+            raise ValueError(f"{name} must be on {self.device}, got {t.device}")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+
+    # -- operators ---------------------------------------------------------
+    def forward(self, vol, out=None, stream=None):
+        import torch
+
+        self._check_tensor(vol, (self.n,) * 3, self.vol_dtype, "vol")
+        if out is None:
+            out = torch.empty((self.n_dirs, self.m), dtype=torch.complex64, device=self.device)
+        self._check_tensor(out, (self.n_dirs, self.m), torch.complex64, "out")
+        _check(self.lib.nufft3d_forward(self._handle, ctypes.c_void_p(vol.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, self.device)),
+               "nufft3d_forward")
+        return out
+
+    def adjoint(self, lines, out=None, stream=None):
+        import torch
+
+        self._check_tensor(lines, (self.n_dirs, self.m), torch.complex64, "lines")
+        if out is None:
+            out = torch.empty((self.n,) * 3, dtype=self.vol_dtype, device=self.device)
+        self._check_tensor(out, (self.n,) * 3, self.vol_dtype, "out")
+        _check(self.lib.nufft3d_adjoint(self._handle, ctypes.c_void_p(lines.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, self.device)),
+               "nufft3d_adjoint")
+        return out
+
+    def sync_status(self) -> int:
+        v = ctypes.c_int(0)
+        _check(self.lib.nufft3d_plan_sync_status(self._handle, ctypes.byref(v)), "nufft3d_plan_sync_status")
+        return int(v.value)
+
+    def info(self) -> dict:
+        a = (ctypes.c_int * 8)()
+        _check(self.lib.nufft3d_plan_info(self._handle, a), "nufft3d_plan_info")
+        keys = ("tile", "tiles_per_axis", "subproblems", "gather_variant", "spread_variant",
+                "points_per_subproblem", "nonempty_tiles", "max_tile_points")
+        return dict(zip(keys, list(a)))
+
+    def tune(self, gather_variant=-1, spread_variant=-1, points_per_subproblem=0, stream=None):
+        _check(self.lib.nufft3d_plan_tune(self._handle, int(gather_variant), int(spread_variant),
+                                          int(points_per_subproblem), _stream_ptr(stream, self.device)),
+               "nufft3d_plan_tune")
+
+    def set_timing(self, max_calls: int):
+        """Arm per-stage CUDA-event timing of the next max_calls calls."""
+        _check(self.lib.nufft3d_plan_set_timing(self._handle, int(max_calls)), "nufft3d_plan_set_timing")
+
+    def stage_times(self) -> dict:
+        """Summed per-stage milliseconds of the recorded calls (synchronises)."""
+        f = (ctypes.c_float * len(FWD_STAGES))()
+        a = (ctypes.c_float * len(ADJ_STAGES))()
+        c = (ctypes.c_int * 2)()
+        _check(self.lib.nufft3d_plan_stage_times(self._handle, f, a, c), "nufft3d_plan_stage_times")
+        return {"forward": dict(zip(FWD_STAGES, list(f))), "adjoint": dict(zip(ADJ_STAGES, list(a))),
+                "forward_calls": c[0], "adjoint_calls": c[1]}
+
+    def close(self):
+        if getattr(self, "_handle", None) is not None and self._handle.value:
+            self.lib.nufft3d_plan_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _autograd_function():
+    import torch
+
+    class _Project(torch.autograd.Function):
+        """y = A x with the hand-written adjoint kernel as backward: dL/dx = A^H g
+        (real part for a real volume)."""
+
+        @staticmethod
+        def forward(ctx, x, plan):
+            ctx.plan = plan
+            return plan.forward(x.contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            gx = ctx.plan.adjoint(g.contiguous().to(torch.complex64))
+            return gx, None
+
+    return _Project
+
+
+_PROJECT = None
+
+
+def project(x, plan: Plan):
+    """Differentiable forward projection: plan.forward with plan.adjoint as backward."""
+    global _PROJECT
+    if _PROJECT is None:
+        _PROJECT = _autograd_function()
+    return _PROJECT.apply(x, plan)

@@ -1,0 +1,160 @@
+// Shared-memory Stockham FFT (mixed radix 2/3/4/8) for W interleaved columns.
+//
+// Element i of column c lives at buf[i * pitch + c]; all NT threads of the
+// CTA cooperate.  Each stage reads every butterfly input into registers,
+// barriers, then writes the outputs (so the transform is in place in shared
+// memory).  Stage s of radix R with span Ns: butterfly j reads x[j + r L/R],
+// multiplies by w^(k r), k = j mod Ns, w = exp(-+2 pi i / (Ns R)), applies the
+// R-point DFT and writes y[(j / Ns) Ns R + k + r Ns] (Stockham autosort).
+// Twiddles come from a table tw[i] = exp(-2 pi i i / L) built in FP64 on the
+// host.  Forward (INV = false) is exp(-i), inverse exp(+i), both unnormalised.
+#pragma once
+
+#include "common.cuh"
+
+namespace nufft {
+
+__host__ __device__ constexpr int c_ilog2(int x) { int r = 0; while (x > 1) { x >>= 1; ++r; } return r; }
+__host__ __device__ constexpr int c_count3(int L) { int c = 0; while (L % 3 == 0) { L /= 3; ++c; } return c; }
+__host__ __device__ constexpr int c_pow2part(int L) { while (L % 3 == 0) L /= 3; return L; }
+__host__ __device__ constexpr int fft_num_stages(int L) { return c_count3(L) + (c_ilog2(c_pow2part(L)) + 2) / 3; }
+__host__ __device__ constexpr int fft_stage_radix(int L, int s) {
+  return s < c_count3(L) ? 3
+         : ((c_ilog2(c_pow2part(L)) % 3 != 0 && s == c_count3(L))
+                ? (c_ilog2(c_pow2part(L)) % 3 == 1 ? 2 : 4)
+                : 8);
+}
+__host__ __device__ constexpr int fft_span_before(int L, int s) {
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= fft_stage_radix(L, i);
+  return ns;
+}
+
+// R-point DFT in registers (forward exp(-i), inverse exp(+i))
+template <int R, bool INV>
+__device__ __forceinline__ void small_dft(float2* v);
+
+template <>
+__device__ __forceinline__ void small_dft<2, false>(float2* v) {
+  float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+template <>
+__device__ __forceinline__ void small_dft<2, true>(float2* v) { small_dft<2, false>(v); }
+
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  float2 s13 = cadd(a1, a3), d13 = mul_mi<INV>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<4, false>(float2* v) { dft4<false>(v[0], v[1], v[2], v[3]); }
+template <>
+__device__ __forceinline__ void small_dft<4, true>(float2* v) { dft4<true>(v[0], v[1], v[2], v[3]); }
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  // even / odd split: E = DFT4(v0, v2, v4, v6), O = DFT4(v1, v3, v5, v7)
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  const float h = 0.70710678118654752440f;  // 1 / sqrt(2)
+  // w8^1 = (1 -+ i)/sqrt2, w8^2 = -+i, w8^3 = (-1 -+ i)/sqrt2
+  float2 t1 = INV ? make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y))
+                  : make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
+  float2 t2 = mul_mi<INV>(o2);
+  float2 t3 = INV ? make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y))
+                  : make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, t1);
+  v[5] = csub(e1, t1);
+  v[2] = cadd(e2, t2);
+  v[6] = csub(e2, t2);
+  v[3] = cadd(e3, t3);
+  v[7] = csub(e3, t3);
+}
+template <>
+__device__ __forceinline__ void small_dft<8, false>(float2* v) { dft8<false>(v); }
+template <>
+__device__ __forceinline__ void small_dft<8, true>(float2* v) { dft8<true>(v); }
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2* v) {
+  const float s3 = 0.86602540378443864676f;  // sqrt(3) / 2
+  float2 t = cadd(v[1], v[2]);
+  float2 d = csub(v[1], v[2]);
+  float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+  // (-+ i sqrt3/2) d
+  float2 r = INV ? make_float2(-s3 * d.y, s3 * d.x) : make_float2(s3 * d.y, -s3 * d.x);
+  v[0] = cadd(v[0], t);
+  v[1] = cadd(m, r);
+  v[2] = csub(m, r);
+}
+template <>
+__device__ __forceinline__ void small_dft<3, false>(float2* v) { dft3<false>(v); }
+template <>
+__device__ __forceinline__ void small_dft<3, true>(float2* v) { dft3<true>(v); }
+
+template <int L, int R, int NS, int W, int NT, bool INV>
+__device__ __forceinline__ void stockham_stage(float2* buf, int pitch, const float2* __restrict__ tw) {
+  constexpr int NBF = W * (L / R);
+  constexpr int PER = (NBF + NT - 1) / NT;
+  float2 v[PER][R];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int b = threadIdx.x + p * NT;
+    if (NBF % NT == 0 || b < NBF) {
+      const int c = b % W, j = b / W;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[p][r] = buf[(j + r * (L / R)) * pitch + c];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int b = threadIdx.x + p * NT;
+    if (NBF % NT == 0 || b < NBF) {
+      const int c = b % W, j = b / W;
+      const int k = j % NS;
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = __ldg(&tw[k * r * (L / (NS * R))]);
+          if (INV) w.y = -w.y;
+          v[p][r] = cmul(v[p][r], w);
+        }
+      }
+      small_dft<R, INV>(v[p]);
+      const int o = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[(o + r * NS) * pitch + c] = v[p][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int L, int W, int NT, bool INV, int S = 0>
+__device__ __forceinline__ void smem_fft(float2* buf, int pitch, const float2* __restrict__ tw) {
+  if constexpr (S < fft_num_stages(L)) {
+    constexpr int R = fft_stage_radix(L, S);
+    constexpr int NS = fft_span_before(L, S);
+    stockham_stage<L, R, NS, W, NT, INV>(buf, pitch, tw);
+    smem_fft<L, W, NT, INV, S + 1>(buf, pitch, tw);
+  }
+}
+
+}  // namespace nufft

@@ -1,0 +1,329 @@
+// FFT passes of the projector: the pruned 3D FFT (x, y, z passes) with the
+// deapodisation and zero padding fused into the first pass (P and F of
+// Eq. 2.11), the pruned inverse passes with cropping and deapodisation fused
+// into the last (their transposes), and the centred per-line DFTs that turn
+// Fourier samples on a radial line into plane integrals (Fourier Slice
+// Theorem, Sec. 2.2.1).  All are HBM-bound: each pass reads and writes its
+// array once; the butterflies run in shared memory.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace nufft {
+
+constexpr int FFT_W = 16;    // columns (rows) per CTA: 16 complex64 = 128 B segments
+constexpr int FFT_NT = 256;  // threads per CTA
+constexpr int FFT_PITCH = FFT_W + 1;
+
+__device__ __forceinline__ int centred_to_grid(int i, int half, int L) {
+  int k = i - half;
+  return k < 0 ? k + L : k;
+}
+
+// ----------------------------------------------------------------------------
+// forward x pass: volume rows (z, y) -> deapodised, zero-padded, FFT along x.
+// out[(z N + y) K + kx]
+// ----------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(FFT_NT) k_row_fwd(const void* __restrict__ vol, int cplx,
+                                                    float2* __restrict__ out, const float* __restrict__ s,
+                                                    int N, const float2* __restrict__ tw) {
+  extern __shared__ float2 buf[];
+  const int nrows = N * N;
+  const int row0 = blockIdx.x * FFT_W;
+  const int half = N / 2;
+  for (int idx = threadIdx.x; idx < FFT_W * N; idx += FFT_NT) {
+    const int c = idx / N, x = idx - c * N;
+    const int r = row0 + c;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nrows) {
+      const int z = r / N, y = r - z * N;
+      const float sc = __ldg(s + x) * __ldg(s + y) * __ldg(s + z);
+      if (cplx) {
+        v = cscale(((const float2*)vol)[(size_t)r * N + x], sc);
+      } else {
+        v = make_float2(((const float*)vol)[(size_t)r * N + x] * sc, 0.f);
+      }
+    }
+    buf[centred_to_grid(x, half, K) * FFT_PITCH + c] = v;
+  }
+  for (int idx = threadIdx.x; idx < FFT_W * (K - N); idx += FFT_NT) {
+    const int c = idx % FFT_W, i = idx / FFT_W + (N - half);
+    buf[i * FFT_PITCH + c] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  smem_fft<K, FFT_W, FFT_NT, false>(buf, FFT_PITCH, tw);
+  for (int idx = threadIdx.x; idx < FFT_W * K; idx += FFT_NT) {
+    const int c = idx / K, k = idx - c * K;
+    const int r = row0 + c;
+    if (r < nrows) out[(size_t)r * K + k] = buf[k * FFT_PITCH + c];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// column pass: for each outer index o and chunk of FFT_W contiguous columns,
+// transform along a strided axis.
+//   PAD_IN : input has N entries (centred), zero-padded to L (forward passes)
+//   CROP_OUT: only the N centred outputs are written (inverse passes)
+// element (i, c) of the input at in[o in_outer + i in_stride + ch W + c]
+// ----------------------------------------------------------------------------
+template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT>
+__global__ void __launch_bounds__(FFT_NT) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
+                                                int N, int n_chunks, long long in_outer, long long in_stride,
+                                                long long out_outer, long long out_stride,
+                                                const float2* __restrict__ tw, float out_scale) {
+  extern __shared__ float2 buf[];
+  const int ch = blockIdx.x % n_chunks;
+  const long long o = blockIdx.x / n_chunks;
+  const float2* ib = in + o * in_outer + (long long)ch * FFT_W;
+  OutT* ob = out + o * out_outer + (long long)ch * FFT_W;
+  const int half = N / 2;
+  const int in_len = PAD_IN ? N : L;
+  for (int idx = threadIdx.x; idx < FFT_W * in_len; idx += FFT_NT) {
+    const int c = idx % FFT_W, i = idx / FFT_W;
+    const int k = PAD_IN ? centred_to_grid(i, half, L) : i;
+    buf[k * FFT_PITCH + c] = ib[(long long)i * in_stride + c];
+  }
+  if (PAD_IN) {
+    for (int idx = threadIdx.x; idx < FFT_W * (L - N); idx += FFT_NT) {
+      const int c = idx % FFT_W, i = idx / FFT_W + (N - half);
+      buf[i * FFT_PITCH + c] = make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  smem_fft<L, FFT_W, FFT_NT, INV>(buf, FFT_PITCH, tw);
+  const int out_len = CROP_OUT ? N : L;
+  for (int idx = threadIdx.x; idx < FFT_W * out_len; idx += FFT_NT) {
+    const int c = idx % FFT_W, i = idx / FFT_W;
+    const int k = CROP_OUT ? centred_to_grid(i, half, L) : i;
+    if constexpr (sizeof(OutT) == sizeof(float2)) {
+      ob[(long long)i * out_stride + c] = *(const OutT*)&buf[k * FFT_PITCH + c];
+    } else {
+      // reduced-precision grid store (forward z pass only)
+      float2 v = buf[k * FFT_PITCH + c];
+      if constexpr (std::is_same<OutT, __nv_bfloat162>::value) {
+        ob[(long long)i * out_stride + c] = GridBF16::pack(v, out_scale);
+      } else {
+        ob[(long long)i * out_stride + c] = GridF16::pack(v, out_scale);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// inverse x pass: rows of K -> inverse FFT -> crop to N, deapodise, real part
+// ----------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(FFT_NT) k_row_adj(const float2* __restrict__ in, void* __restrict__ vol,
+                                                    int cplx, const float* __restrict__ s, int N,
+                                                    const float2* __restrict__ tw) {
+  extern __shared__ float2 buf[];
+  const int nrows = N * N;
+  const int row0 = blockIdx.x * FFT_W;
+  const int half = N / 2;
+  for (int idx = threadIdx.x; idx < FFT_W * K; idx += FFT_NT) {
+    const int c = idx / K, k = idx - c * K;
+    const int r = row0 + c;
+    buf[k * FFT_PITCH + c] = r < nrows ? in[(size_t)r * K + k] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  smem_fft<K, FFT_W, FFT_NT, true>(buf, FFT_PITCH, tw);
+  for (int idx = threadIdx.x; idx < FFT_W * N; idx += FFT_NT) {
+    const int c = idx / N, x = idx - c * N;
+    const int r = row0 + c;
+    if (r < nrows) {
+      const int z = r / N, y = r - z * N;
+      const float sc = __ldg(s + x) * __ldg(s + y) * __ldg(s + z);
+      const float2 v = cscale(buf[centred_to_grid(x, half, K) * FFT_PITCH + c], sc);
+      if (cplx) ((float2*)vol)[(size_t)r * N + x] = v;
+      else ((float*)vol)[(size_t)r * N + x] = v.x;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// per-line centred DFTs.  FWD (projection): a[m] = w[m] (-1)^m X[m];
+// p[t] = (-1)^{M/2} (-1)^t / M * sum_m a[m] e^{+2 pi i m t / M}.
+// ADJ: a[t] = (-1)^t y[t]; Y[m] = (-1)^{M/2} (-1)^m conj(w[m]) / M * sum_t a[t] e^{-2 pi i m t / M}.
+// Rows are lines (l0 + c); in-place operation (in == out) is allowed.
+// ----------------------------------------------------------------------------
+template <int M, bool FWD>
+__global__ void __launch_bounds__(FFT_NT) k_line(const float2* in, float2* out, int D,
+                                                 const float2* __restrict__ weight,
+                                                 const float2* __restrict__ tw) {
+  extern __shared__ float2 buf[];
+  const int l0 = blockIdx.x * FFT_W;
+  for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
+    const int c = idx / M, m = idx - c * M;
+    const int l = l0 + c;
+    float2 v = make_float2(0.f, 0.f);
+    if (l < D) {
+      v = in[(size_t)l * M + m];
+      if (FWD && weight) v = cmul(v, __ldg(weight + m));
+      if (m & 1) v = make_float2(-v.x, -v.y);
+    }
+    buf[m * FFT_PITCH + c] = v;
+  }
+  __syncthreads();
+  smem_fft<M, FFT_W, FFT_NT, FWD>(buf, FFT_PITCH, tw);
+  const float sc = (((M / 2) & 1) ? -1.f : 1.f) / (float)M;
+  for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
+    const int c = idx / M, t = idx - c * M;
+    const int l = l0 + c;
+    if (l < D) {
+      float2 v = cscale(buf[t * FFT_PITCH + c], (t & 1) ? -sc : sc);
+      if (!FWD && weight) v = cmulc(v, __ldg(weight + t));
+      out[(size_t)l * M + t] = v;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// host launchers
+// ----------------------------------------------------------------------------
+static size_t fft_smem(int L) { return (size_t)L * FFT_PITCH * sizeof(float2); }
+
+template <typename F>
+static cudaError_t set_smem(F* f, size_t bytes) {
+  return cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define NUFFT_FFT_SIZES(X) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+
+bool fft_length_supported(int L) {
+  switch (L) {
+#define CASE_L(V) case V:
+    NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+    return true;
+    default:
+      return false;
+  }
+}
+
+template <int K>
+static cudaError_t launch_row_fwd_t(const void* vol, int cplx, float2* out, const float* s, int N,
+                                    const float2* tw, cudaStream_t st) {
+  auto f = k_row_fwd<K>;
+  cudaError_t e = set_smem(f, fft_smem(K));
+  if (e != cudaSuccess) return e;
+  const int grid = (N * N + FFT_W - 1) / FFT_W;
+  f<<<grid, FFT_NT, fft_smem(K), st>>>(vol, cplx, out, s, N, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_fwd(int K, const void* vol, int cplx, float2* out, const float* s, int N,
+                           const float2* tw, cudaStream_t st) {
+  switch (K) {
+#define CASE_L(V) case V: return launch_row_fwd_t<V>(vol, cplx, out, s, N, tw, st);
+    NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int K>
+static cudaError_t launch_row_adj_t(const float2* in, void* vol, int cplx, const float* s, int N,
+                                    const float2* tw, cudaStream_t st) {
+  auto f = k_row_adj<K>;
+  cudaError_t e = set_smem(f, fft_smem(K));
+  if (e != cudaSuccess) return e;
+  const int grid = (N * N + FFT_W - 1) / FFT_W;
+  f<<<grid, FFT_NT, fft_smem(K), st>>>(in, vol, cplx, s, N, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_adj(int K, const float2* in, void* vol, int cplx, const float* s, int N,
+                           const float2* tw, cudaStream_t st) {
+  switch (K) {
+#define CASE_L(V) case V: return launch_row_adj_t<V>(in, vol, cplx, s, N, tw, st);
+    NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT>
+static cudaError_t launch_col_t(const float2* in, OutT* out, int N, int n_outer, int row_len,
+                                long long in_outer, long long in_stride, long long out_outer,
+                                long long out_stride, const float2* tw, float out_scale, cudaStream_t st) {
+  auto f = k_col<L, INV, PAD_IN, CROP_OUT, OutT>;
+  cudaError_t e = set_smem(f, fft_smem(L));
+  if (e != cudaSuccess) return e;
+  const int n_chunks = row_len / FFT_W;
+  const long long grid = (long long)n_outer * n_chunks;
+  f<<<(unsigned)grid, FFT_NT, fft_smem(L), st>>>(in, out, N, n_chunks, in_outer, in_stride, out_outer,
+                                                 out_stride, tw, out_scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
+                           long long in_outer, long long in_stride, long long out_outer, long long out_stride,
+                           const float2* tw, cudaStream_t st) {
+  switch (L) {
+#define CASE_L(V) case V: return launch_col_t<V, false, true, false, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, 1.f, st);
+    NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_col_fwd_lp(int L, int dtype, const float2* in, void* out, int N, int n_outer, int row_len,
+                              long long in_outer, long long in_stride, long long out_outer,
+                              long long out_stride, const float2* tw, float scale, cudaStream_t st) {
+  if (dtype == 1) {
+    switch (L) {
+#define CASE_L(V) case V: return launch_col_t<V, false, true, false, __nv_bfloat162>(in, (__nv_bfloat162*)out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, scale, st);
+      NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+    }
+  } else {
+    switch (L) {
+#define CASE_L(V) case V: return launch_col_t<V, false, true, false, __half2>(in, (__half2*)out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, scale, st);
+      NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
+                           long long in_outer, long long in_stride, long long out_outer, long long out_stride,
+                           const float2* tw, cudaStream_t st) {
+  switch (L) {
+#define CASE_L(V) case V: return launch_col_t<V, true, false, true, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, 1.f, st);
+    NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int M, bool FWD>
+static cudaError_t launch_line_t(const float2* in, float2* out, int D, const float2* w, const float2* tw,
+                                 cudaStream_t st) {
+  auto f = k_line<M, FWD>;
+  cudaError_t e = set_smem(f, fft_smem(M));
+  if (e != cudaSuccess) return e;
+  const int grid = (D + FFT_W - 1) / FFT_W;
+  f<<<grid, FFT_NT, fft_smem(M), st>>>(in, out, D, w, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_line(int M, bool fwd, const float2* in, float2* out, int D, const float2* w,
+                        const float2* tw, cudaStream_t st) {
+  if (fwd) {
+    switch (M) {
+#define CASE_L(V) case V: return launch_line_t<V, true>(in, out, D, w, tw, st);
+      NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+    }
+  } else {
+    switch (M) {
+#define CASE_L(V) case V: return launch_line_t<V, false>(in, out, D, w, tw, st);
+      NUFFT_FFT_SIZES(CASE_L)
+#undef CASE_L
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nufft

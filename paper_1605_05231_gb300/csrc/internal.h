@@ -1,0 +1,86 @@
+// Internal declarations shared by the translation units of libnufft3d.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <vector>
+
+#include "../../include/nufft3d.h"
+
+namespace nufft {
+
+// point-to-tile binning and the interpolation kernels' view of a plan
+struct InterpGeom {
+  int K, J, L, T, nT, M, D;
+  const float2* dir;     // [D][3] (hi, lo) direction components
+  const float2* rad;     // [M] (hi, lo) radius in grid units
+  const float2* table;   // [(L + 1) * J] min-max coefficients
+  const uint32_t* sorted;  // point ids sorted by tile
+  int* err;              // device check word
+};
+
+bool fft_length_supported(int L);
+cudaError_t launch_row_fwd(int K, const void* vol, int cplx, float2* out, const float* s, int N,
+                           const float2* tw, cudaStream_t st);
+cudaError_t launch_row_adj(int K, const float2* in, void* vol, int cplx, const float* s, int N,
+                           const float2* tw, cudaStream_t st);
+cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
+                           long long in_outer, long long in_stride, long long out_outer, long long out_stride,
+                           const float2* tw, cudaStream_t st);
+cudaError_t launch_col_fwd_lp(int L, int dtype, const float2* in, void* out, int N, int n_outer, int row_len,
+                              long long in_outer, long long in_stride, long long out_outer,
+                              long long out_stride, const float2* tw, float scale, cudaStream_t st);
+cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
+                           long long in_outer, long long in_stride, long long out_outer, long long out_stride,
+                           const float2* tw, cudaStream_t st);
+cudaError_t launch_line(int M, bool fwd, const float2* in, float2* out, int D, const float2* w,
+                        const float2* tw, cudaStream_t st);
+
+cudaError_t launch_bin_points(const InterpGeom& g, uint32_t* bins, cudaStream_t st);
+// subs: int4 (bin, start, count, 0); variant 0 = thread per point, 1 = warp per point
+cudaError_t launch_gather(const InterpGeom& g, int variant, int grid_dtype, const void* grid, float inv_scale,
+                          const int4* subs, int n_subs, float2* out, cudaStream_t st);
+cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, const int4* subs, int n_subs,
+                          float2* grid, cudaStream_t st);
+size_t interp_smem_bytes(int T, int J);
+
+}  // namespace nufft
+
+constexpr int FWD_STAGES = 5;  // x pass, y pass, z pass, gather, line DFT
+constexpr int ADJ_STAGES = 6;  // line DFT, grid clear, spread, z pass, y pass, x pass
+
+struct nufft3d_plan_s {
+  // resolved parameters
+  int N, K, J, L, D, M;
+  long long P;
+  int complex_volume, do_line_fft, grid_dtype;
+  int T, nT;  // tile edge and tiles per axis
+  int gather_variant, spread_variant, pts_per_sub;
+  float lp_scale;  // power-of-two scale of the reduced-precision grid
+  int device;
+  // device arrays (owned)
+  float2* d_dir = nullptr;
+  float2* d_rad = nullptr;
+  float2* d_weight = nullptr;  // null when w = 1
+  float* d_s = nullptr;
+  float2* d_table = nullptr;
+  float2* d_twK = nullptr;
+  float2* d_twM = nullptr;
+  uint32_t* d_sorted = nullptr;
+  int4* d_sub = nullptr;
+  int n_sub = 0;
+  float2* d_grid = nullptr;   // K^3
+  void* d_grid_lp = nullptr;  // K^3 reduced precision (grid_dtype != 0)
+  float2* d_bufA = nullptr;   // N * N * K
+  float2* d_bufB = nullptr;   // N * K * K
+  float2* d_lines = nullptr;  // D * M (adjoint line DFT output)
+  int* d_err = nullptr;
+  // optional per-stage CUDA-event timing (ring of event sets, one per call)
+  int timing_slots = 0, fwd_calls = 0, adj_calls = 0;
+  std::vector<cudaEvent_t> ev_fwd, ev_adj;  // slots * (FWD_STAGES + 1), slots * (ADJ_STAGES + 1)
+  // host copy of the per-bin offsets (for re-tuning the subproblem split)
+  std::vector<long long> bin_offsets;
+  cudaStream_t last_stream = nullptr;
+};

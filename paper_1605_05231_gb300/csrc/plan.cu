@@ -1,0 +1,621 @@
+// Host side of libnufft3d: parameter validation, FP64 plan precompute (the
+// Kaiser-Bessel deapodisation factors of Eq. 2.11, the min-max interpolation
+// table, FFT twiddles, direction and radius splits), the point sort by grid
+// tile, workspace management and the orchestration of the forward and adjoint
+// passes.  Every entry point of include/nufft3d.h is defined here.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using nufft::InterpGeom;
+typedef std::complex<double> cd;
+
+namespace {
+
+struct Resolved {
+  int N, K, J, L, D, M, grid_dtype, cplx, line_fft;
+  long long P;
+  int T, nT;
+};
+
+constexpr int kMaxEdge = 512;
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+int resolve(const nufft3d_params* p, Resolved& r) {
+  if (!p) return NUFFT3D_ERR_ARG;
+  r.N = p->n;
+  r.K = p->k ? p->k : 2 * p->n;
+  r.J = p->j ? p->j : 6;
+  r.L = p->table_oversamp ? p->table_oversamp : 1024;
+  r.M = p->m ? p->m : 2 * p->n;
+  r.D = p->n_dirs;
+  r.grid_dtype = p->grid_dtype;
+  r.cplx = p->complex_volume ? 1 : 0;
+  r.line_fft = p->do_line_fft ? 1 : 0;
+  if (r.N < 8 || r.N > kMaxEdge || (r.N & 1)) return NUFFT3D_ERR_ARG;
+  if (r.K < r.N || r.K > kMaxEdge) return NUFFT3D_ERR_ARG;
+  if (r.J < 2 || r.J > 8) return NUFFT3D_ERR_ARG;
+  if (r.J & 1) return NUFFT3D_ERR_UNSUPPORTED;
+  if (!is_pow2(r.L) || r.L < 2 || r.L > 65536) return NUFFT3D_ERR_ARG;
+  if (r.M < 2 || (r.M & 1) || r.M > 1 << 20) return NUFFT3D_ERR_ARG;
+  if (r.D < 1) return NUFFT3D_ERR_ARG;
+  if (!p->dirs) return NUFFT3D_ERR_ARG;
+  if (r.grid_dtype < 0 || r.grid_dtype > 2) return NUFFT3D_ERR_ARG;
+  r.P = (long long)r.D * r.M;
+  if (r.P >= (1ll << 32)) return NUFFT3D_ERR_ARG;
+  if (r.K % 16 != 0 || !nufft::fft_length_supported(r.K)) return NUFFT3D_ERR_UNSUPPORTED;
+  if (r.line_fft && !nufft::fft_length_supported(r.M)) return NUFFT3D_ERR_UNSUPPORTED;
+  for (int i = 0; i < 3 * r.D; ++i)
+    if (!std::isfinite(p->dirs[i])) return NUFFT3D_ERR_ARG;
+  for (int l = 0; l < r.D; ++l) {
+    const double* d = p->dirs + 3 * l;
+    if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > 1.0 + 1e-6) return NUFFT3D_ERR_ARG;
+  }
+  if (p->omega) {
+    for (int m = 0; m < r.M; ++m)
+      if (!std::isfinite(p->omega[m]) || std::fabs(p->omega[m]) > M_PI * (1 + 1e-12)) return NUFFT3D_ERR_ARG;
+  }
+  if (p->weight) {
+    for (int m = 0; m < 2 * r.M; ++m)
+      if (!std::isfinite(p->weight[m])) return NUFFT3D_ERR_ARG;
+  }
+  r.T = 16;
+  while (r.T > 4 && (r.K % r.T != 0 || r.T + r.J - 1 > r.K)) r.T /= 2;
+  r.nT = r.K / r.T;
+  return NUFFT3D_OK;
+}
+
+// Fourier transform of the Kaiser-Bessel window of width J, shape alpha,
+// at nu cycles per grid sample: J sinh(z) / z, z = sqrt(alpha^2 - (pi J nu)^2).
+double kb_ft(double nu, int J, double alpha) {
+  const double z2 = alpha * alpha - (M_PI * J * nu) * (M_PI * J * nu);
+  if (z2 > 0) {
+    const double z = std::sqrt(z2);
+    return J * std::sinh(z) / z;
+  }
+  const double z = std::sqrt(-z2);
+  return z > 0 ? J * std::sin(z) / z : (double)J;
+}
+
+// in-place inverse of a complex n x n matrix (Gauss-Jordan, partial pivoting)
+bool invert(std::vector<cd>& a, int n) {
+  std::vector<cd> inv(n * n, cd(0, 0));
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::abs(a[r * n + c]) > std::abs(a[piv * n + c])) piv = r;
+    if (std::abs(a[piv * n + c]) == 0.0) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[c * n + k], a[piv * n + k]);
+        std::swap(inv[c * n + k], inv[piv * n + k]);
+      }
+    const cd d = a[c * n + c];
+    for (int k = 0; k < n; ++k) {
+      a[c * n + k] /= d;
+      inv[c * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const cd f = a[r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[r * n + k] -= f * a[c * n + k];
+        inv[r * n + k] -= f * inv[c * n + k];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+struct HostTables {
+  std::vector<float> s;         // N
+  std::vector<float2> table;    // (L + 1) * J
+  std::vector<float2> twK, twM;
+  std::vector<float2> dir;      // D * 3 (hi, lo)
+  std::vector<float2> rad;      // M (hi, lo)
+  std::vector<float2> weight;   // M or empty
+};
+
+float2 split(double v) {
+  const float hi = (float)v;
+  const float lo = (float)(v - (double)hi);
+  return make_float2(hi, lo);
+}
+
+bool build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
+  const int N = r.N, K = r.K, J = r.J, L = r.L;
+  const double alpha = 2.34 * J;
+  const double gam = 2.0 * M_PI / K;
+  // scaling factors s(n) = Psi(0) / Psi(n / K), n = -N/2 .. N/2 - 1 (Eq. 2.11, P)
+  std::vector<double> s(N);
+  const double psi0 = kb_ft(0.0, J, alpha);
+  for (int i = 0; i < N; ++i) {
+    const int n = i - N / 2;
+    s[i] = psi0 / kb_ft((double)n / K, J, alpha);
+  }
+  h.s.resize(N);
+  for (int i = 0; i < N; ++i) h.s[i] = (float)s[i];
+  // min-max interpolator: T_{jj'} = sum_n s(n)^2 e^{i gam (j - j') n}
+  std::vector<cd> T(J * J);
+  for (int a = 0; a < J; ++a)
+    for (int b = 0; b < J; ++b) {
+      cd acc = 0;
+      for (int i = 0; i < N; ++i) {
+        const double n = i - N / 2;
+        acc += s[i] * s[i] * std::exp(cd(0, gam * (a - b) * n));
+      }
+      T[a * J + b] = acc;
+    }
+  if (!invert(T, J)) return false;
+  // table: c(f_i) = T^{-1} r(f_i), r_j(f) = sum_n s(n) e^{-i gam (f + J/2 - j) n}, j = 1..J
+  h.table.resize((size_t)(L + 1) * J);
+  std::vector<cd> rv(J);
+  for (int t = 0; t <= L; ++t) {
+    const double f = (double)t / L;
+    for (int j = 1; j <= J; ++j) {
+      cd acc = 0;
+      const double dist = f + 0.5 * J - j;
+      for (int i = 0; i < N; ++i) {
+        const double n = i - N / 2;
+        acc += s[i] * std::exp(cd(0, -gam * dist * n));
+      }
+      rv[j - 1] = acc;
+    }
+    for (int a = 0; a < J; ++a) {
+      cd c = 0;
+      for (int b = 0; b < J; ++b) c += T[a * J + b] * rv[b];
+      h.table[(size_t)t * J + a] = make_float2((float)c.real(), (float)c.imag());
+    }
+  }
+  auto twiddles = [](int Lt, std::vector<float2>& out) {
+    out.resize(Lt);
+    for (int k = 0; k < Lt; ++k) {
+      const double a = -2.0 * M_PI * k / Lt;
+      out[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+  };
+  twiddles(K, h.twK);
+  if (r.line_fft) twiddles(r.M, h.twM);
+  h.dir.resize((size_t)r.D * 3);
+  for (size_t i = 0; i < (size_t)r.D * 3; ++i) h.dir[i] = split(p->dirs[i]);
+  h.rad.resize(r.M);
+  for (int m = 0; m < r.M; ++m) {
+    const double rad = p->omega ? p->omega[m] * K / (2.0 * M_PI) : (double)(m - r.M / 2) * K / r.M;
+    h.rad[m] = split(rad);
+  }
+  if (p->weight) {
+    h.weight.resize(r.M);
+    for (int m = 0; m < r.M; ++m) h.weight[m] = make_float2(p->weight[2 * m], p->weight[2 * m + 1]);
+  }
+  return true;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return NUFFT3D_OK;
+  if (e == cudaErrorMemoryAllocation) return NUFFT3D_ERR_NOMEM;
+  return NUFFT3D_ERR_CUDA;
+}
+
+#define CK(expr)                              \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+template <typename T>
+cudaError_t upload(T** p, const std::vector<T>& v, cudaStream_t st) {
+  cudaError_t e = dalloc(p, v.size());
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+void free_plan(nufft3d_plan pl) {
+  if (!pl) return;
+  void* ptrs[] = {pl->d_dir, pl->d_rad, pl->d_weight, pl->d_s, pl->d_table, pl->d_twK, pl->d_twM,
+                  pl->d_sorted, pl->d_sub, pl->d_grid, pl->d_grid_lp, pl->d_bufA, pl->d_bufB,
+                  pl->d_lines, pl->d_err};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (cudaEvent_t e : pl->ev_fwd) cudaEventDestroy(e);
+  for (cudaEvent_t e : pl->ev_adj) cudaEventDestroy(e);
+  delete pl;
+}
+
+InterpGeom geom(const nufft3d_plan pl) {
+  InterpGeom g;
+  g.K = pl->K;
+  g.J = pl->J;
+  g.L = pl->L;
+  g.T = pl->T;
+  g.nT = pl->nT;
+  g.M = pl->M;
+  g.D = pl->D;
+  g.dir = pl->d_dir;
+  g.rad = pl->d_rad;
+  g.table = pl->d_table;
+  g.sorted = pl->d_sorted;
+  g.err = pl->d_err;
+  return g;
+}
+
+int build_subproblems(nufft3d_plan pl, int S, cudaStream_t st) {
+  std::vector<int4> subs;
+  const size_t nb = pl->bin_offsets.size() - 1;
+  for (size_t b = 0; b < nb; ++b) {
+    const long long a = pl->bin_offsets[b], e = pl->bin_offsets[b + 1];
+    for (long long s0 = a; s0 < e; s0 += S) {
+      const int cnt = (int)std::min<long long>(S, e - s0);
+      subs.push_back(make_int4((int)b, (int)s0, cnt, 0));
+    }
+  }
+  if (pl->d_sub) {
+    cudaFree(pl->d_sub);
+    pl->d_sub = nullptr;
+  }
+  pl->n_sub = (int)subs.size();
+  CK(upload(&pl->d_sub, subs, st));
+  CK(cudaStreamSynchronize(st));
+  pl->pts_per_sub = S;
+  return NUFFT3D_OK;
+}
+
+int sort_points(nufft3d_plan pl, cudaStream_t st) {
+  const long long P = pl->P;
+  uint32_t* d_bins = nullptr;
+  CK(dalloc(&d_bins, (size_t)P));
+  InterpGeom g = geom(pl);
+  cudaError_t e = nufft::launch_bin_points(g, d_bins, st);
+  std::vector<uint32_t> bins;
+  if (e == cudaSuccess) {
+    try {
+      bins.resize((size_t)P);
+    } catch (...) {
+      cudaFree(d_bins);
+      return NUFFT3D_ERR_NOMEM;
+    }
+    e = cudaMemcpyAsync(bins.data(), d_bins, (size_t)P * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(d_bins);
+  if (e != cudaSuccess) return cuda_status(e);
+  // stable counting sort by bin
+  const size_t nb = (size_t)pl->nT * pl->nT * pl->nT;
+  std::vector<long long> off(nb + 1, 0);
+  for (long long i = 0; i < P; ++i) {
+    if (bins[i] >= nb) return NUFFT3D_ERR_DEVICE_CHECK;
+    off[bins[i] + 1]++;
+  }
+  for (size_t b = 0; b < nb; ++b) off[b + 1] += off[b];
+  std::vector<uint32_t> sorted((size_t)P);
+  {
+    std::vector<long long> pos(off.begin(), off.end() - 1);
+    for (long long i = 0; i < P; ++i) sorted[pos[bins[i]]++] = (uint32_t)i;
+  }
+  pl->bin_offsets.swap(off);
+  CK(upload(&pl->d_sorted, sorted, st));
+  CK(cudaStreamSynchronize(st));
+  return NUFFT3D_OK;
+}
+
+int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st) {
+  Resolved r;
+  int rc = resolve(p, r);
+  if (rc != NUFFT3D_OK) return rc;
+  HostTables h;
+  if (!build_tables(p, r, h)) return NUFFT3D_ERR_ARG;
+  nufft3d_plan pl = new (std::nothrow) nufft3d_plan_s();
+  if (!pl) return NUFFT3D_ERR_NOMEM;
+  *out = pl;  // freed by the caller on failure
+  pl->N = r.N;
+  pl->K = r.K;
+  pl->J = r.J;
+  pl->L = r.L;
+  pl->D = r.D;
+  pl->M = r.M;
+  pl->P = r.P;
+  pl->complex_volume = r.cplx;
+  pl->do_line_fft = r.line_fft;
+  pl->grid_dtype = r.grid_dtype;
+  pl->T = r.T;
+  pl->nT = r.nT;
+  pl->gather_variant = 0;
+  pl->spread_variant = 0;
+  pl->lp_scale = 1.f;
+  CK(cudaGetDevice(&pl->device));
+  CK(upload(&pl->d_s, h.s, st));
+  CK(upload(&pl->d_table, h.table, st));
+  CK(upload(&pl->d_twK, h.twK, st));
+  CK(upload(&pl->d_twM, h.twM, st));
+  CK(upload(&pl->d_dir, h.dir, st));
+  CK(upload(&pl->d_rad, h.rad, st));
+  CK(upload(&pl->d_weight, h.weight, st));
+  CK(dalloc(&pl->d_err, 1));
+  CK(cudaMemsetAsync(pl->d_err, 0, sizeof(int), st));
+  CK(cudaStreamSynchronize(st));
+  rc = sort_points(pl, st);
+  if (rc != NUFFT3D_OK) return rc;
+  rc = build_subproblems(pl, 1024, st);
+  if (rc != NUFFT3D_OK) return rc;
+  const size_t K3 = (size_t)r.K * r.K * r.K;
+  CK(dalloc(&pl->d_grid, K3));
+  if (r.grid_dtype != NUFFT3D_GRID_C64) CK(cudaMalloc(&pl->d_grid_lp, K3 * 4));
+  CK(dalloc(&pl->d_bufA, (size_t)r.N * r.N * r.K));
+  CK(dalloc(&pl->d_bufB, (size_t)r.N * r.K * r.K));
+  if (r.line_fft) CK(dalloc(&pl->d_lines, (size_t)r.P));
+  CK(cudaStreamSynchronize(st));
+  pl->last_stream = st;
+  return NUFFT3D_OK;
+}
+
+int ensure_device(nufft3d_plan pl) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != pl->device) CK(cudaSetDevice(pl->device));
+  return NUFFT3D_OK;
+}
+
+// records the event closing stage `stage` of the current timed call (stage -1 opens it)
+struct StageClock {
+  cudaEvent_t* ev = nullptr;
+  cudaStream_t st;
+  StageClock(std::vector<cudaEvent_t>& v, int slots, int& calls, int nst, cudaStream_t s) : st(s) {
+    if (calls < slots) ev = v.data() + (size_t)calls++ * (nst + 1);
+  }
+  cudaError_t mark(int stage) { return ev ? cudaEventRecord(ev[stage + 1], st) : cudaSuccess; }
+};
+
+int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st) {
+  const int N = pl->N, K = pl->K;
+  const long long KK = (long long)K * K;
+  StageClock clk(pl->ev_fwd, pl->timing_slots, pl->fwd_calls, FWD_STAGES, st);
+  CK(clk.mark(-1));
+  CK(nufft::launch_row_fwd(K, vol, pl->complex_volume, pl->d_bufA, pl->d_s, N, pl->d_twK, st));
+  CK(clk.mark(0));
+  CK(nufft::launch_col_fwd(K, pl->d_bufA, pl->d_bufB, N, N, K, (long long)N * K, K, KK, K, pl->d_twK, st));
+  CK(clk.mark(1));
+  const void* grid = pl->d_grid;
+  float inv_scale = 1.f;
+  if (pl->grid_dtype == NUFFT3D_GRID_C64) {
+    CK(nufft::launch_col_fwd(K, pl->d_bufB, pl->d_grid, N, K, K, K, KK, K, KK, pl->d_twK, st));
+  } else {
+    CK(nufft::launch_col_fwd_lp(K, pl->grid_dtype, pl->d_bufB, pl->d_grid_lp, N, K, K, K, KK, K, KK, pl->d_twK,
+                                pl->lp_scale, st));
+    grid = pl->d_grid_lp;
+    inv_scale = 1.f / pl->lp_scale;
+  }
+  CK(clk.mark(2));
+  InterpGeom g = geom(pl);
+  CK(nufft::launch_gather(g, pl->gather_variant, pl->grid_dtype, grid, inv_scale, pl->d_sub, pl->n_sub,
+                          (float2*)lines, st));
+  CK(clk.mark(3));
+  if (pl->do_line_fft)
+    CK(nufft::launch_line(pl->M, true, (const float2*)lines, (float2*)lines, pl->D, pl->d_weight, pl->d_twM, st));
+  CK(clk.mark(4));
+  return NUFFT3D_OK;
+}
+
+int adjoint_impl(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st) {
+  const int N = pl->N, K = pl->K;
+  const long long KK = (long long)K * K;
+  const float2* src = (const float2*)lines;
+  StageClock clk(pl->ev_adj, pl->timing_slots, pl->adj_calls, ADJ_STAGES, st);
+  CK(clk.mark(-1));
+  if (pl->do_line_fft) {
+    CK(nufft::launch_line(pl->M, false, src, pl->d_lines, pl->D, pl->d_weight, pl->d_twM, st));
+    src = pl->d_lines;
+  }
+  CK(clk.mark(0));
+  CK(cudaMemsetAsync(pl->d_grid, 0, (size_t)K * KK * sizeof(float2), st));
+  CK(clk.mark(1));
+  InterpGeom g = geom(pl);
+  CK(nufft::launch_spread(g, pl->spread_variant, src, pl->d_sub, pl->n_sub, pl->d_grid, st));
+  CK(clk.mark(2));
+  CK(nufft::launch_col_inv(K, pl->d_grid, pl->d_bufB, N, K, K, K, KK, K, KK, pl->d_twK, st));
+  CK(clk.mark(3));
+  CK(nufft::launch_col_inv(K, pl->d_bufB, pl->d_bufA, N, N, K, KK, K, (long long)N * K, K, pl->d_twK, st));
+  CK(clk.mark(4));
+  CK(nufft::launch_row_adj(K, pl->d_bufA, vol, pl->complex_volume, pl->d_s, N, pl->d_twK, st));
+  CK(clk.mark(5));
+  return NUFFT3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nufft3d_plan_create(nufft3d_plan* out, const nufft3d_params* p, void* cuda_stream) {
+  if (!out) return NUFFT3D_ERR_ARG;
+  *out = nullptr;
+  nufft3d_plan pl = nullptr;
+  int rc;
+  try {
+    rc = plan_create_impl(&pl, p, (cudaStream_t)cuda_stream);
+  } catch (const std::bad_alloc&) {
+    rc = NUFFT3D_ERR_NOMEM;
+  } catch (...) {
+    rc = NUFFT3D_ERR_CUDA;
+  }
+  if (rc != NUFFT3D_OK) {
+    if (pl) {
+      cudaStreamSynchronize((cudaStream_t)cuda_stream);
+      free_plan(pl);
+    }
+    return rc;
+  }
+  *out = pl;
+  return NUFFT3D_OK;
+}
+
+int nufft3d_forward(nufft3d_plan plan, const void* vol_dev, void* lines_dev, void* cuda_stream) {
+  if (!plan || !vol_dev || !lines_dev) return NUFFT3D_ERR_ARG;
+  int rc = ensure_device(plan);
+  if (rc != NUFFT3D_OK) return rc;
+  plan->last_stream = (cudaStream_t)cuda_stream;
+  return forward_impl(plan, vol_dev, lines_dev, (cudaStream_t)cuda_stream);
+}
+
+int nufft3d_adjoint(nufft3d_plan plan, const void* lines_dev, void* vol_dev, void* cuda_stream) {
+  if (!plan || !vol_dev || !lines_dev) return NUFFT3D_ERR_ARG;
+  int rc = ensure_device(plan);
+  if (rc != NUFFT3D_OK) return rc;
+  plan->last_stream = (cudaStream_t)cuda_stream;
+  return adjoint_impl(plan, lines_dev, vol_dev, (cudaStream_t)cuda_stream);
+}
+
+int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes) {
+  if (!bytes) return NUFFT3D_ERR_ARG;
+  Resolved r;
+  const int rc = resolve(p, r);
+  if (rc != NUFFT3D_OK) return rc;
+  const size_t K3 = (size_t)r.K * r.K * r.K;
+  size_t b = 0;
+  b += K3 * sizeof(float2);
+  if (r.grid_dtype != NUFFT3D_GRID_C64) b += K3 * 4;
+  b += (size_t)r.N * r.N * r.K * sizeof(float2);
+  b += (size_t)r.N * r.K * r.K * sizeof(float2);
+  if (r.line_fft) b += (size_t)r.P * sizeof(float2);
+  b += (size_t)r.P * sizeof(uint32_t);                                   // point sort
+  b += (size_t)(r.L + 1) * r.J * sizeof(float2);                         // table
+  b += (size_t)r.D * 3 * sizeof(float2) + (size_t)r.M * 2 * sizeof(float2) + r.N * sizeof(float);
+  b += (size_t)(r.K + r.M) * sizeof(float2);
+  *bytes = b;
+  return NUFFT3D_OK;
+}
+
+int nufft3d_plan_sync_status(nufft3d_plan plan, int* device_status) {
+  if (!plan || !device_status) return NUFFT3D_ERR_ARG;
+  int rc = ensure_device(plan);
+  if (rc != NUFFT3D_OK) return rc;
+  int v = 0;
+  CK(cudaStreamSynchronize(plan->last_stream));
+  CK(cudaMemcpy(&v, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(plan->d_err, 0, sizeof(int)));
+  *device_status = v;
+  return NUFFT3D_OK;
+}
+
+int nufft3d_plan_destroy(nufft3d_plan plan) {
+  if (!plan) return NUFFT3D_OK;
+  ensure_device(plan);
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  return NUFFT3D_OK;
+}
+
+const char* nufft3d_error_string(int status) {
+  switch (status) {
+    case NUFFT3D_OK: return "success";
+    case NUFFT3D_ERR_ARG: return "invalid argument";
+    case NUFFT3D_ERR_NOMEM: return "out of memory";
+    case NUFFT3D_ERR_CUDA: return "CUDA runtime error";
+    case NUFFT3D_ERR_UNSUPPORTED: return "unsupported parameters";
+    case NUFFT3D_ERR_TIMEOUT: return "bounded device wait timed out";
+    case NUFFT3D_ERR_DEVICE_CHECK: return "device-side consistency check failed";
+  }
+  return "unknown status";
+}
+
+int nufft3d_plan_info(nufft3d_plan plan, int* out) {
+  if (!plan || !out) return NUFFT3D_ERR_ARG;
+  int nonempty = 0;
+  long long maxc = 0;
+  for (size_t b = 0; b + 1 < plan->bin_offsets.size(); ++b) {
+    const long long c = plan->bin_offsets[b + 1] - plan->bin_offsets[b];
+    nonempty += c > 0;
+    maxc = std::max(maxc, c);
+  }
+  out[0] = plan->T;
+  out[1] = plan->nT;
+  out[2] = plan->n_sub;
+  out[3] = plan->gather_variant;
+  out[4] = plan->spread_variant;
+  out[5] = plan->pts_per_sub;
+  out[6] = nonempty;
+  out[7] = (int)std::min<long long>(maxc, 0x7fffffff);
+  return NUFFT3D_OK;
+}
+
+int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
+                      void* cuda_stream) {
+  if (!plan) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 1 || spread_variant < -1 || spread_variant > 1) return NUFFT3D_ERR_ARG;
+  if (points_per_subproblem < 0) return NUFFT3D_ERR_ARG;
+  int rc = ensure_device(plan);
+  if (rc != NUFFT3D_OK) return rc;
+  CK(cudaStreamSynchronize(plan->last_stream));
+  if (gather_variant >= 0) plan->gather_variant = gather_variant;
+  if (spread_variant >= 0) plan->spread_variant = spread_variant;
+  if (points_per_subproblem > 0 && points_per_subproblem != plan->pts_per_sub) {
+    rc = build_subproblems(plan, points_per_subproblem, (cudaStream_t)cuda_stream);
+    if (rc != NUFFT3D_OK) return rc;
+  }
+  return NUFFT3D_OK;
+}
+
+int nufft3d_plan_set_timing(nufft3d_plan plan, int max_calls) {
+  if (!plan || max_calls < 0) return NUFFT3D_ERR_ARG;
+  int rc = ensure_device(plan);
+  if (rc != NUFFT3D_OK) return rc;
+  CK(cudaStreamSynchronize(plan->last_stream));
+  for (cudaEvent_t e : plan->ev_fwd) cudaEventDestroy(e);
+  for (cudaEvent_t e : plan->ev_adj) cudaEventDestroy(e);
+  plan->ev_fwd.clear();
+  plan->ev_adj.clear();
+  plan->timing_slots = 0;
+  plan->fwd_calls = plan->adj_calls = 0;
+  const size_t nf = (size_t)max_calls * (FWD_STAGES + 1), na = (size_t)max_calls * (ADJ_STAGES + 1);
+  for (size_t i = 0; i < nf + na; ++i) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    (i < nf ? plan->ev_fwd : plan->ev_adj).push_back(e);
+  }
+  plan->timing_slots = max_calls;
+  return NUFFT3D_OK;
+}
+
+int nufft3d_plan_stage_times(nufft3d_plan plan, float* fwd_ms, float* adj_ms, int* calls) {
+  if (!plan || !fwd_ms || !adj_ms || !calls) return NUFFT3D_ERR_ARG;
+  int rc = ensure_device(plan);
+  if (rc != NUFFT3D_OK) return rc;
+  CK(cudaStreamSynchronize(plan->last_stream));
+  for (int s = 0; s < FWD_STAGES; ++s) fwd_ms[s] = 0.f;
+  for (int s = 0; s < ADJ_STAGES; ++s) adj_ms[s] = 0.f;
+  for (int c = 0; c < plan->fwd_calls; ++c)
+    for (int s = 0; s < FWD_STAGES; ++s) {
+      float ms = 0.f;
+      cudaEvent_t* e = plan->ev_fwd.data() + (size_t)c * (FWD_STAGES + 1);
+      CK(cudaEventSynchronize(e[s + 1]));
+      CK(cudaEventElapsedTime(&ms, e[s], e[s + 1]));
+      fwd_ms[s] += ms;
+    }
+  for (int c = 0; c < plan->adj_calls; ++c)
+    for (int s = 0; s < ADJ_STAGES; ++s) {
+      float ms = 0.f;
+      cudaEvent_t* e = plan->ev_adj.data() + (size_t)c * (ADJ_STAGES + 1);
+      CK(cudaEventSynchronize(e[s + 1]));
+      CK(cudaEventElapsedTime(&ms, e[s], e[s + 1]));
+      adj_ms[s] += ms;
+    }
+  calls[0] = plan->fwd_calls;
+  calls[1] = plan->adj_calls;
+  plan->fwd_calls = plan->adj_calls = 0;
+  return NUFFT3D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar (the method's floating-point contract): relative L2 error at most 1e-5
+against the table-coefficient oracle on the same seeded inputs, for both the
+forward projection and its adjoint; the adjoint also passes the dot-product
+test to 1e-6.  Sizes span several shared-memory tiles, ragged line counts,
+radix-3 grid sizes, non-default taps, weights and radial frequencies.
+"""
+import numpy as np
+import pytest
+
+from oracle import nufft3d_oracle as O
+from paper_1605_05231_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _run(binding, n, dirs, m=0, k=0, j=6, L=1024, x=None, y=None, **kw):
+    import torch
+
+    plan = binding.Plan(n, dirs, m=m, k=k, j=j, table_oversamp=L, **kw)
+    out = {}
+    if x is not None:
+        out["fwd"] = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    if y is not None:
+        out["adj"] = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    plan.close()
+    return out
+
+
+def _oplan(n, dirs, m=0, k=0, j=6, L=1024, **kw):
+    return O.OraclePlan(n, k or 2 * n, j, L, dirs, m or 2 * n, **kw)
+
+
+def test_tiny_workload_forward_adjoint(cuda_lib):
+    """32^3 ellipsoids, K = 64, 64 x 32 umbrella lines, M = 64 (131k points)."""
+    w = I.workload("tiny32")
+    dirs = w.directions()
+    x = w.volume(np.float32)
+    y = I.random_lines(dirs.shape[0], w.m, 3).astype(np.complex64)
+    r = _run(cuda_lib, w.n, dirs, w.m, w.k, w.j, w.table_oversamp, x=x, y=y)
+    op = _oplan(w.n, dirs, w.m, w.k, w.j, w.table_oversamp)
+    ef = O.rel_l2(r["fwd"], O.nufft_forward(x.astype(np.float64), op))
+    ea = O.rel_l2(r["adj"], O.nufft_adjoint(y.astype(np.complex128), op))
+    assert ef < TOL, ef
+    assert ea < TOL, ea
+    # against the exact transform the NUFFT approximation error dominates
+    lines = np.arange(0, dirs.shape[0], 31)
+    ex = O.forward_exact(x.astype(np.float64), op, lines=lines)
+    assert O.rel_l2(r["fwd"][lines], ex) < 3e-5
+
+
+@pytest.mark.parametrize("n,k,m,ndir,j,L", [
+    (16, 32, 32, 37, 6, 1024),     # ragged line count (not a multiple of 16)
+    (24, 48, 48, 50, 6, 1024),     # radix-3 grid and line lengths
+    (32, 96, 64, 40, 6, 512),      # K = 3N, table L = 512
+    (16, 32, 32, 33, 4, 1024),     # J = 4
+    (16, 32, 32, 33, 8, 256),      # J = 8
+    (20, 64, 48, 17, 2, 2048),     # J = 2, M != K
+    (64, 128, 128, 300, 6, 1024),  # several 16^3 tiles per axis
+])
+def test_shapes_taps_tables(cuda_lib, n, k, m, ndir, j, L):
+    dirs = I.random_directions(ndir, n + ndir)
+    x = I.random_volume(n, 1).astype(np.float32)
+    y = I.random_lines(ndir, m, 2).astype(np.complex64)
+    r = _run(cuda_lib, n, dirs, m, k, j, L, x=x, y=y)
+    op = _oplan(n, dirs, m, k, j, L)
+    assert O.rel_l2(r["fwd"], O.nufft_forward(x.astype(np.float64), op)) < TOL
+    assert O.rel_l2(r["adj"], O.nufft_adjoint(y.astype(np.complex128), op)) < TOL
+
+
+def test_complex_volume_weights_and_raw_samples(cuda_lib):
+    n, ndir = 16, 45
+    dirs = I.random_directions(ndir, 5)
+    rng = np.random.default_rng(9)
+    w = (rng.normal(size=2 * n) + 1j * rng.normal(size=2 * n)).astype(np.complex64)
+    x = I.random_volume(n, 3, complex_values=True).astype(np.complex64)
+    y = I.random_lines(ndir, 2 * n, 4).astype(np.complex64)
+    r = _run(cuda_lib, n, dirs, x=x, y=y, weight=w, complex_volume=True)
+    op = _oplan(n, dirs, weight=w.astype(np.complex128), complex_volume=True)
+    assert O.rel_l2(r["fwd"], O.nufft_forward(x.astype(np.complex128), op)) < TOL
+    assert O.rel_l2(r["adj"], O.nufft_adjoint(y.astype(np.complex128), op)) < TOL
+    r = _run(cuda_lib, n, dirs, x=x, y=y, complex_volume=True, do_line_fft=False)
+    op = _oplan(n, dirs, complex_volume=True, do_line_fft=False)
+    assert O.rel_l2(r["fwd"], O.nufft_forward(x.astype(np.complex128), op)) < TOL
+    assert O.rel_l2(r["adj"], O.nufft_adjoint(y.astype(np.complex128), op)) < TOL
+
+
+def test_custom_radial_frequencies(cuda_lib):
+    n, ndir, m = 16, 20, 30
+    dirs = I.random_directions(ndir, 6)
+    omega = np.sort(np.random.default_rng(1).uniform(-np.pi, np.pi, m))
+    x = I.random_volume(n, 4).astype(np.float32)
+    y = I.random_lines(ndir, m, 5).astype(np.complex64)
+    r = _run(cuda_lib, n, dirs, m=m, x=x, y=y, omega=omega, do_line_fft=False)
+    op = _oplan(n, dirs, m=m, omega=omega, do_line_fft=False)
+    assert O.rel_l2(r["fwd"], O.nufft_forward(x.astype(np.float64), op)) < TOL
+    assert O.rel_l2(r["adj"], O.nufft_adjoint(y.astype(np.complex128), op)) < TOL
+
+
+def test_axis_aligned_lines_give_slice_sums(cuda_lib):
+    """Fourier-slice exactness: lines along the axes return plain slice sums."""
+    n = 32
+    x = I.random_volume(n, 8).astype(np.float32)
+    r = _run(cuda_lib, n, I.axis_directions(), x=x)
+    sums = [x.sum(axis=(0, 1)), x.sum(axis=(0, 2)), x.sum(axis=(1, 2))]
+    for a in range(3):
+        expect = np.zeros(2 * n)
+        expect[n // 2: n // 2 + n] = sums[a]
+        assert np.max(np.abs(r["fwd"][a] - expect)) < 3e-5 * np.abs(expect).max()
+
+
+def test_adjoint_dot_product_gpu(cuda_lib):
+    import torch
+
+    n, ndir = 32, 500
+    dirs = I.random_directions(ndir, 77)
+    plan = cuda_lib.Plan(n, dirs, complex_volume=True)
+    x = torch.from_numpy(I.random_volume(n, 1, complex_values=True).astype(np.complex64)).cuda()
+    y = torch.from_numpy(I.random_lines(ndir, 2 * n, 2).astype(np.complex64)).cuda()
+    Ax = plan.forward(x)
+    Ahy = plan.adjoint(y)
+    lhs = torch.vdot(y.flatten().to(torch.complex128), Ax.flatten().to(torch.complex128))
+    rhs = torch.vdot(Ahy.flatten().to(torch.complex128), x.flatten().to(torch.complex128))
+    denom = torch.linalg.norm(Ax.to(torch.complex128)) * torch.linalg.norm(y.to(torch.complex128))
+    assert abs(complex(lhs - rhs)) / float(denom) < 1e-6
+
+
+def test_degenerate_single_line_and_dc_only(cuda_lib):
+    """One line, and a line of two samples (q = -1, 0)."""
+    n = 8
+    x = I.random_volume(n, 2).astype(np.float32)
+    dirs = np.array([[0.0, 0.6, 0.8]])
+    r = _run(cuda_lib, n, dirs, m=16, x=x, y=I.random_lines(1, 16, 3).astype(np.complex64))
+    op = _oplan(n, dirs, m=16)
+    assert O.rel_l2(r["fwd"], O.nufft_forward(x.astype(np.float64), op)) < TOL
+    r = _run(cuda_lib, n, dirs, m=2, x=x, do_line_fft=False)
+    op = _oplan(n, dirs, m=2, do_line_fft=False)
+    X = O.nufft_forward(x.astype(np.float64), op)
+    assert O.rel_l2(r["fwd"], X) < TOL
+    assert abs(r["fwd"][0, 1] - x.sum()) < 1e-4 * np.abs(x).sum()
+
+
+def test_mid_workload_sampled_lines(cuda_lib):
+    """128^3, K = 256, 180 x 128 lines, M = 256 (5.9M points): forward on a
+    sample of lines and the full adjoint on a sub-plan, against the oracle."""
+    import torch
+
+    w = I.workload("mid128")
+    dirs = w.directions()
+    x = w.volume(np.float32)
+    plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp)
+    p = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    op = _oplan(w.n, dirs, w.m, w.k, w.j, w.table_oversamp)
+    lines = np.random.default_rng(0).choice(dirs.shape[0], 64, replace=False)
+    ref = O.nufft_forward(x.astype(np.float64), op, lines=lines)
+    assert O.rel_l2(p[lines], ref) < TOL
+    # adjoint: a sub-plan of 96 lines (the oracle spreads every point)
+    sub = dirs[lines[:48]]
+    y = I.random_lines(sub.shape[0], w.m, 11).astype(np.complex64)
+    r = _run(cuda_lib, w.n, sub, w.m, w.k, w.j, w.table_oversamp, y=y)
+    ref = O.nufft_adjoint(y.astype(np.complex128), _oplan(w.n, sub, w.m, w.k, w.j, w.table_oversamp))
+    assert O.rel_l2(r["adj"], ref) < TOL
