@@ -1,0 +1,457 @@
+#!/usr/bin/env python
+"""Throughput of the radial-line 3D NUFFT projector (forward + adjoint).
+
+Metric: nonuniform points per second, P / (t_forward + t_adjoint), on the
+256^3 workload (K = 512, J = 6, L = 1024, 360 x 256 umbrella lines of 512
+samples: P = 47,185,920 points) with a seeded ellipsoid phantom plus
+N(0, 0.01^2) noise.  A step is one forward projection of the volume followed
+by the adjoint of the resulting lines.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs an independent replica
+of the workload (the projector does not shard across GPUs here); the value is
+the points of all ranks over the slowest rank's time ("scaling": "weak").
+The reference arm times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nonuniform pts/s fwd+adj NUFFT at 256^3 FP32"
+UNIT = "pts/s"
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="full256")
+    ap.add_argument("--grid-dtype", default="c64")
+    ap.add_argument("--gather-variant", type=int, default=-1)
+    ap.add_argument("--spread-variant", type=int, default=-1)
+    ap.add_argument("--points-per-subproblem", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-lines", type=int, default=1500)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic work per stage
+# ----------------------------------------------------------------------------
+def stage_work(n, k, j, m, d):
+    """Algorithmic bytes and flops per launch of each stage."""
+    P = d * m
+    c8 = 8
+    ball = min(1.0, 4.0 / 3.0 * 3.141592653589793 * (0.5 + (j / 2) / k) ** 3)
+    interp_flops = 8 * (j ** 3 + j ** 2 + j) * P
+    return {
+        "forward": {
+            "x_pass": {"bytes": 4 * n ** 3 + c8 * n * n * k},
+            "y_pass": {"bytes": c8 * n * n * k + c8 * n * k * k},
+            "z_pass": {"bytes": c8 * n * k * k + c8 * k ** 3},
+            "gather": {"bytes": ball * c8 * k ** 3 + c8 * P + 4 * P, "flops": interp_flops},
+            "line_dft": {"bytes": 2 * c8 * P},
+        },
+        "adjoint": {
+            "line_dft": {"bytes": 2 * c8 * P},
+            "grid_clear": {"bytes": c8 * k ** 3},
+            "spread": {"bytes": 2 * ball * c8 * k ** 3 + c8 * P + 4 * P, "flops": interp_flops},
+            "z_pass": {"bytes": c8 * k ** 3 + c8 * n * k * k},
+            "y_pass": {"bytes": c8 * n * k * k + c8 * n * n * k},
+            "x_pass": {"bytes": c8 * n * n * k + 4 * n ** 3},
+        },
+    }
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return {"hbm_gbs": float(pk["hbm_gbs"]), "sm_max_mhz": float(pk.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("interp.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1605_05231_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_stage: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source
+    is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            tr = json.load(fh)
+        ent = tr.get(kernel_stage)
+        if ent and ent.get("source_hash") == source_hash():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# distributed helpers
+# ----------------------------------------------------------------------------
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    elif args.impl == "ours":
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_fixed(w, x, dirs):
+    """Time the oracle's size-fixed stages at full size: deapodise + pad + K^3
+    FFT (forward) and K^3 inverse FFT + crop + deapodise (adjoint)."""
+    import numpy as np
+
+    from oracle import nufft3d_oracle as O
+
+    op = O.OraclePlan(w.n, w.k, w.j, w.table_oversamp, dirs, w.m)
+    t0 = time.perf_counter()
+    Y = O.grid_fft(O.deapodize_pad(x.astype(np.float64), op))
+    t1 = time.perf_counter()
+    O.crop_deapodize(O.grid_ifft_unnormalised(Y), op)
+    t2 = time.perf_counter()
+    return op, Y, t2 - t0
+
+
+def oracle_points(op, Y, lines):
+    """Time the oracle's per-point stages (gather + line DFT, line DFT adjoint +
+    spread) on the selected lines."""
+    from oracle import nufft3d_oracle as O
+
+    t0 = time.perf_counter()
+    u = op.point_u(lines).reshape(-1, 3)
+    Xh = O.interp_gather(Y, u, op).reshape(len(lines), op.M)
+    p = O.radial_idft(Xh, op)
+    Yh = O.radial_idft_adjoint(p, op)
+    O.interp_spread(Yh.reshape(-1), u, op)
+    return time.perf_counter() - t0
+
+
+def oracle_time(w, x, dirs, sample_lines: int, seed: int = 0):
+    """Oracle time for the whole workload: the fixed stages at full size plus
+    the per-point stages on a sample of lines scaled to all points."""
+    import numpy as np
+
+    t0 = time.perf_counter()
+    op, Y, t_fixed = oracle_fixed(w, x, dirs)
+    lines = np.sort(np.random.default_rng(seed).choice(dirs.shape[0], sample_lines, replace=False))
+    t_pts = oracle_points(op, Y, lines)
+    P = dirs.shape[0] * w.m
+    Ps = len(lines) * w.m
+    return {"t_total": t_fixed + t_pts * P / Ps, "t_fixed": t_fixed, "t_points_sample": t_pts,
+            "sample_points": Ps, "sample_lines": len(lines), "wall": time.perf_counter() - t0}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------
+# arms
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    from paper_1605_05231_gb300 import inputs as I
+
+    w = I.workload(args.workload)
+    dirs = w.directions()
+    x = w.volume(np.float32)
+    op, Y, t_fixed = oracle_fixed(w, x, dirs)
+    per_step_lines = 8
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        oracle_points(op, Y, np.sort(rng.choice(dirs.shape[0], per_step_lines, replace=False)))
+    t_pts = []
+    for _ in range(args.steps):
+        t_pts.append(oracle_points(op, Y, np.sort(rng.choice(dirs.shape[0], per_step_lines, replace=False))))
+    P = w.n_points
+    t = t_fixed + statistics.mean(t_pts) * dirs.shape[0] / per_step_lines
+    value = P / t
+    sample = (f"K^3 FFT + inverse FFT of the FP64 oracle timed once at full size ({t_fixed:.1f} s); each step "
+              f"runs its gather, spread and line DFTs on {per_step_lines} random lines of {dirs.shape[0]}, "
+              f"scaled to all {P} points")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "table_oversamp": w.table_oversamp,
+                       "dirs": f"{w.n_az}x{w.n_pol}", "m": w.m, "points": P},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1605_05231_gb300 import Plan
+    from paper_1605_05231_gb300 import inputs as I
+
+    world, rank, local = dist_setup(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = I.workload(args.workload)
+    dirs = w.directions()
+    x = w.volume(np.float32)
+    t0 = time.perf_counter()
+    plan = Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp, grid_dtype=args.grid_dtype)
+    plan.tune(args.gather_variant, args.spread_variant, args.points_per_subproblem)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    P = plan.n_points
+    xd = torch.from_numpy(x).to(dev)
+    lines = torch.empty((plan.n_dirs, plan.m), dtype=torch.complex64, device=dev)
+    vout = torch.empty_like(xd)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.forward(xd, out=lines)
+        plan.adjoint(lines, out=vout)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if plan.sync_status() != 0:
+        raise RuntimeError("device check failed during warm-up")
+    plan.set_timing(args.steps)
+    clocks = ClockSampler(dev.index)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    stages = plan.stage_times()
+    plan.set_timing(0)
+    ms_max = max_over_ranks(world, ms)
+    value = world * P / (ms_max * 1e-3)
+
+    # ---- end to end through pinned host buffers -------------------------
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        lh = torch.empty((plan.n_dirs, plan.m), dtype=torch.complex64).pin_memory()
+        vh = torch.empty_like(xh).pin_memory()
+
+        def step_e2e():
+            xd.copy_(xh, non_blocking=True)
+            plan.forward(xd, out=lines)
+            lh.copy_(lines, non_blocking=True)
+            plan.adjoint(lines, out=vout)
+            vh.copy_(vout, non_blocking=True)
+
+        for _ in range(3):
+            step_e2e()
+        n_e2e = max(3, min(args.steps, 20))
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(n_e2e):
+            step_e2e()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(world, ev0.elapsed_time(ev1) / n_e2e)
+        e2e = {"value": world * P / (ms_e2e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(xh.numel() * 4),
+               "d2h_bytes_per_step": int(lh.numel() * 8 + vh.numel() * 4), "ms_per_step": ms_e2e}
+    if plan.sync_status() != 0:
+        raise RuntimeError("device check failed")
+
+    # ---- roofline of the dominant kernel ---------------------------------
+    peaks = load_peaks()
+    work = stage_work(w.n, w.k, w.j, w.m, plan.n_dirs)
+    per_call = {}
+    for side in ("forward", "adjoint"):
+        calls = max(1, stages[f"{side}_calls"])
+        for name, t in stages[side].items():
+            per_call[(side, name)] = t / calls
+    dom = max(per_call, key=per_call.get)
+    t_dom = per_call[dom] * 1e-3
+    wk = work[dom[0]][dom[1]]
+    if "flops" in wk:
+        f_mhz = peaks["sm_max_mhz"]
+        peak = SMS * FP32_LANES_PER_SM * 2 * f_mhz * 1e6 / 1e12
+        achieved = wk["flops"] / t_dom / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "kernel": f"{dom[0]}.{dom[1]}",
+                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {f_mhz:.0f} MHz"}
+    else:
+        achieved = wk["bytes"] / t_dom / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "kernel": f"{dom[0]}.{dom[1]}"}
+    roof["peak_source"] = peaks["source"]
+    roof["algorithmic_bytes"] = wk["bytes"]
+    roof["hbm_frac"] = wk["bytes"] / t_dom / 1e9 / peaks["hbm_gbs"]
+    roof["traffic"] = ncu_traffic(f"{dom[0]}.{dom[1]}")
+    stage_ms = {f"{side}.{name}": round(per_call[(side, name)], 4) for (side, name) in per_call}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) ----------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_time(w, x, dirs, args.cpu_sample_lines)
+        cpu = {"value": P / r["t_total"], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": (f"full-size K^3 FFT + inverse FFT of the FP64 oracle, its gather, spread and line DFTs "
+                          f"on {r['sample_lines']} of {plan.n_dirs} lines ({r['sample_points']} points), "
+                          f"per-point time scaled to all {P} points; {r['wall']:.1f} s of CPU work")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.grid_dtype == "c64" else f"f32+{args.grid_dtype} grid",
+                "data": "synthetic",
+                "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "table_oversamp": w.table_oversamp,
+                           "dirs": f"{w.n_az}x{w.n_pol}", "m": w.m, "points": P, "grid_dtype": args.grid_dtype,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "working set per step >> L2 (1.07 GB grid, 0.38 GB lines, 0.19 GB point ids)",
+                           "variants": plan.info()},
+                "gpu_launches": 10 * args.steps, "clocks": clk, "e2e": e2e, "roofline": roof,
+                "cpu_baseline": cpu, "stage_ms": stage_ms, "plan_s": plan_s}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -124,17 +124,22 @@ int nufft3d_plan_destroy(nufft3d_plan plan);
 /* Static description of a status code (never NULL). */
 const char* nufft3d_error_string(int status);
 
-/* Numbers of the plan: points P = D*M, tiles, subproblems, tile edge,
- * gather/spread variants; out must hold 8 ints.  For tests and tuning. */
+/* Numbers of the plan; out must hold 8 ints: tile edge T, tiles per axis,
+ * subproblems, gather variant, spread variant, points per subproblem,
+ * non-empty tiles, most points in one tile.  For tests and tuning. */
 int nufft3d_plan_info(nufft3d_plan plan, int* out);
 
-/* Select the gather and spread kernel variants (0: one thread per point,
- * 1: one warp per point; -1 keeps the current choice) and the number of
- * points per subproblem (0 keeps it) of a plan.  Synchronises the plan's
- * last stream; rebuilds the subproblem list on cuda_stream.  Used by the
- * autotuner. */
+/* Select the gather and spread kernel variants, the number of points per
+ * subproblem and the grid tile edge T of a plan (-1 / 0 keep the current
+ * choice).  Variants: 0 one thread per point, one CTA per subproblem (any
+ * J); 1 one warp per point, CTA-shared tile (J = 6); 2 one warp per point,
+ * warp-private tile, no shared atomics (J = 6, T = 8; the default when
+ * available).  T is 4, 8 or 16; changing it re-sorts the points.
+ * Synchronises the plan's last stream and works on cuda_stream.  Returns
+ * NUFFT3D_ERR_UNSUPPORTED for a combination the plan cannot run.  Used by
+ * the autotuner. */
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
-                      int points_per_subproblem, void* cuda_stream);
+                      int points_per_subproblem, int tile_edge, void* cuda_stream);
 
 /* Per-stage timing with CUDA events recorded on the launching stream between
  * the kernels of each call.  nufft3d_plan_set_timing(plan, n) arms timing of

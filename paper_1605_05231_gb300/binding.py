@@ -85,7 +85,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.nufft3d_error_string.argtypes = [i]
     lib.nufft3d_error_string.restype = ctypes.c_char_p
     lib.nufft3d_plan_info.argtypes = [vp, ip]
-    lib.nufft3d_plan_tune.argtypes = [vp, i, i, i, vp]
+    lib.nufft3d_plan_tune.argtypes = [vp, i, i, i, i, vp]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.nufft3d_plan_set_timing.argtypes = [vp, i]
     lib.nufft3d_plan_stage_times.argtypes = [vp, fp, fp, ip]
@@ -243,10 +243,11 @@ class Plan:
                 "points_per_subproblem", "nonempty_tiles", "max_tile_points")
         return dict(zip(keys, list(a)))
 
-    def tune(self, gather_variant=-1, spread_variant=-1, points_per_subproblem=0, stream=None):
+    def tune(self, gather_variant=-1, spread_variant=-1, points_per_subproblem=0, tile_edge=0, stream=None):
+        """Pick kernel variants (0, 1, 2), points per subproblem and tile edge (-1 / 0 keep)."""
         _check(self.lib.nufft3d_plan_tune(self._handle, int(gather_variant), int(spread_variant),
-                                          int(points_per_subproblem), _stream_ptr(stream, self.device)),
-               "nufft3d_plan_tune")
+                                          int(points_per_subproblem), int(tile_edge),
+                                          _stream_ptr(stream, self.device)), "nufft3d_plan_tune")
 
     def set_timing(self, max_calls: int):
         """Arm per-stage CUDA-event timing of the next max_calls calls."""

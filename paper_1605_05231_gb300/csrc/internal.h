@@ -19,6 +19,7 @@ struct InterpGeom {
   const float2* table;   // [(L + 1) * J] min-max coefficients
   const uint32_t* sorted;  // point ids sorted by tile
   int* err;              // device check word
+  int* counter;          // two work counters (gather, spread) for the persistent variants
 };
 
 bool fft_length_supported(int L);
@@ -45,6 +46,7 @@ cudaError_t launch_gather(const InterpGeom& g, int variant, int grid_dtype, cons
 cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, const int4* subs, int n_subs,
                           float2* grid, cudaStream_t st);
 size_t interp_smem_bytes(int T, int J);
+bool v2_supported(int T, int J, int L);
 
 }  // namespace nufft
 
@@ -77,6 +79,7 @@ struct nufft3d_plan_s {
   float2* d_bufB = nullptr;   // N * K * K
   float2* d_lines = nullptr;  // D * M (adjoint line DFT output)
   int* d_err = nullptr;
+  int* d_counter = nullptr;  // [2]
   // optional per-stage CUDA-event timing (ring of event sets, one per call)
   int timing_slots = 0, fwd_calls = 0, adj_calls = 0;
   std::vector<cudaEvent_t> ev_fwd, ev_adj;  // slots * (FWD_STAGES + 1), slots * (ADJ_STAGES + 1)

@@ -182,6 +182,548 @@ __global__ void __launch_bounds__(256) k_spread_v0(InterpGeom g, const float2* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// variant 1 (J = 6): persistent CTAs (one per SM, 16 warps), the coefficient
+// table resident in shared memory, one warp per point.
+//
+// Phase 1: each lane decodes one point of a batch of 32 and writes its 18
+// coefficients (x, y, z) to a per-warp buffer.  Phase 2: for each of the 32
+// points, lane (jx, jy) = (lane % 6, lane / 6) serves the taps (jx, jy, 0..5);
+// the four pairs (2..5, 5) left over are served by lanes 0..23 as
+// (jx, jz) = (2 + lane % 4, lane / 4).  With the tile's row pitch = 6 and
+// plane pitch = 4 (mod 16 float2), every tap load of a phase-2 instruction
+// hits a distinct bank pair.  The gather then sums each lane's 32 partial
+// values across the warp with a transpose-reduction (31 shuffles per
+// component for 32 points).
+// ---------------------------------------------------------------------------
+constexpr int V1_WARPS = 16;
+constexpr int V1_THREADS = V1_WARPS * 32;
+constexpr int V1_CSTRIDE = 20;  // float2 slots per point: cx[6] cy[6] cz[6] value pad
+
+struct V1Layout {
+  int E, P, PP;
+  int tile_f2, table_f2;
+  size_t bytes;
+};
+
+__host__ __device__ inline V1Layout v1_layout(int T, int L) {
+  V1Layout l;
+  l.E = T + 5;
+  l.P = l.E + ((6 - l.E % 16) + 16) % 16;
+  const int pp = l.E * l.P;
+  l.PP = pp + ((4 - pp % 16) + 16) % 16;
+  l.tile_f2 = l.E * l.PP;
+  l.table_f2 = (L + 1) * 6;
+  l.bytes = ((size_t)l.table_f2 + l.tile_f2 + (size_t)V1_WARPS * 32 * V1_CSTRIDE) * sizeof(float2) +
+            (size_t)V1_WARPS * 32 * sizeof(int4);
+  return l;
+}
+
+// Phase 1 for one lane: decode, locate in the tile, write coefficients.
+// Returns the tile offset of the first tap (or -1 when the lane has no point).
+__device__ __forceinline__ int v1_phase1(const InterpGeom& g, const float2* table, int pi, int cnt, int start,
+                                         int x0, int y0, int z0, int P, int PP, float2* cp, uint32_t& id) {
+  if (pi >= cnt) return -1;
+  id = g.sorted[start + pi];
+  int w0[3];
+  float f[3];
+  decode_point<6>(g, id, w0, f);
+  const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+  if ((unsigned)lx >= (unsigned)g.T || (unsigned)ly >= (unsigned)g.T || (unsigned)lz >= (unsigned)g.T) {
+    atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+    return -1;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float fl = f[a] * (float)g.L;
+    int i = (int)fl;
+    if (i > g.L - 1) i = g.L - 1;
+    const float t = fl - (float)i;
+    const float4* r0 = (const float4*)(table + i * 6);
+    const float4* r1 = (const float4*)(table + i * 6 + 6);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 a0 = r0[q], a1 = r1[q];
+      cp[a * 6 + 2 * q] = make_float2(fmaf(t, a1.x - a0.x, a0.x), fmaf(t, a1.y - a0.y, a0.y));
+      cp[a * 6 + 2 * q + 1] = make_float2(fmaf(t, a1.z - a0.z, a0.z), fmaf(t, a1.w - a0.w, a0.w));
+    }
+  }
+  return (lz * PP + ly * P + lx);
+}
+
+template <typename G>
+__device__ __forceinline__ void stage_tile_padded(const typename G::T* __restrict__ grid, float inv_scale, int K,
+                                                  int E, int P, int PP, int x0, int y0, int z0, float2* tile) {
+  const int n = E * E * E;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int ix = idx % E;
+    const int t = idx / E;
+    const int iy = t % E, iz = t / E;
+    int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+    gx -= gx >= K ? K : 0;
+    gy -= gy >= K ? K : 0;
+    gz -= gz >= K ? K : 0;
+    tile[iz * PP + iy * P + ix] = G::load(grid, ((size_t)gz * K + gy) * K + gx, inv_scale);
+  }
+}
+
+template <typename G>
+__global__ void __launch_bounds__(V1_THREADS, 1) k_gather_v1(InterpGeom g, const typename G::T* __restrict__ grid,
+                                                             float inv_scale, const int4* __restrict__ subs,
+                                                             int n_subs, float2* __restrict__ out) {
+  extern __shared__ __align__(16) float2 smem[];
+  const V1Layout lay = v1_layout(g.T, g.L);
+  float2* table = smem;
+  float2* tile = table + lay.table_f2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* coef = tile + lay.tile_f2 + warp * 32 * V1_CSTRIDE;
+  int* meta = (int*)(tile + lay.tile_f2 + V1_WARPS * 32 * V1_CSTRIDE) + warp * 32;
+  for (int i = threadIdx.x; i < lay.table_f2; i += V1_THREADS) table[i] = __ldg(g.table + i);
+  const int E = lay.E, P = lay.P, PP = lay.PP, T = g.T, nT = g.nT;
+  const int jx = lane % 6, jy = lane / 6;
+  const int ox = 2 + (lane & 3), oz = lane >> 2;
+  const int main_off = jy * P + jx;
+  const int ovf_off = 5 * P + ox + oz * PP;
+  for (int s = blockIdx.x; s < n_subs; s += gridDim.x) {
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    __syncthreads();
+    stage_tile_padded<G>(grid, inv_scale, g.K, E, P, PP, x0, y0, z0, tile);
+    __syncthreads();
+    for (int b0 = warp * 32; b0 < sp.z; b0 += V1_THREADS) {
+      uint32_t id = 0;
+      const int off = v1_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, P, PP, coef + lane * V1_CSTRIDE, id);
+      meta[lane] = off;
+      __syncwarp();
+      float2 acc[32];
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        const int mo = meta[p];
+        float2 r = make_float2(0.f, 0.f);
+        if (mo >= 0) {
+          const float2* cp = coef + p * V1_CSTRIDE;
+          const float2 cxy = cmul(cp[jx], cp[6 + jy]);
+          const float4 z01 = *(const float4*)(cp + 12);
+          const float4 z23 = *(const float4*)(cp + 14);
+          const float4 z45 = *(const float4*)(cp + 16);
+          const float2* tp = tile + mo + main_off;
+          float2 sa = make_float2(0.f, 0.f);
+          cmac(sa, make_float2(z01.x, z01.y), tp[0]);
+          cmac(sa, make_float2(z01.z, z01.w), tp[PP]);
+          cmac(sa, make_float2(z23.x, z23.y), tp[2 * PP]);
+          cmac(sa, make_float2(z23.z, z23.w), tp[3 * PP]);
+          cmac(sa, make_float2(z45.x, z45.y), tp[4 * PP]);
+          cmac(sa, make_float2(z45.z, z45.w), tp[5 * PP]);
+          r = cmul(cxy, sa);
+          if (lane < 24) {
+            const float2 w = cmul(cmul(cp[ox], cp[11]), cp[12 + oz]);
+            cmac(r, w, tile[mo + ovf_off]);
+          }
+        }
+        acc[p] = r;
+      }
+      // transpose-reduction: afterwards acc[0] of lane p holds the sum for point p
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const bool upper = (lane & sh) != 0;
+#pragma unroll
+        for (int i = 0; i < sh; ++i) {
+          const float2 send = upper ? acc[i] : acc[i + sh];
+          const float2 keep = upper ? acc[i + sh] : acc[i];
+          const float rx = __shfl_xor_sync(0xffffffffu, send.x, sh);
+          const float ry = __shfl_xor_sync(0xffffffffu, send.y, sh);
+          acc[i] = make_float2(keep.x + rx, keep.y + ry);
+        }
+      }
+      if (off >= 0) out[id] = acc[0];
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(V1_THREADS, 1) k_spread_v1(InterpGeom g, const float2* __restrict__ in,
+                                                             const int4* __restrict__ subs, int n_subs,
+                                                             float2* __restrict__ grid) {
+  extern __shared__ __align__(16) float2 smem[];
+  const V1Layout lay = v1_layout(g.T, g.L);
+  float2* table = smem;
+  float2* tile = table + lay.table_f2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* coef = tile + lay.tile_f2 + warp * 32 * V1_CSTRIDE;
+  int* meta = (int*)(tile + lay.tile_f2 + V1_WARPS * 32 * V1_CSTRIDE) + warp * 32;
+  for (int i = threadIdx.x; i < lay.table_f2; i += V1_THREADS) table[i] = __ldg(g.table + i);
+  for (int i = threadIdx.x; i < lay.tile_f2; i += V1_THREADS) tile[i] = make_float2(0.f, 0.f);
+  const int E = lay.E, P = lay.P, PP = lay.PP, T = g.T, nT = g.nT, K = g.K;
+  const int jx = lane % 6, jy = lane / 6;
+  const int ox = 2 + (lane & 3), oz = lane >> 2;
+  const int main_off = jy * P + jx;
+  const int ovf_off = 5 * P + ox + oz * PP;
+  for (int s = blockIdx.x; s < n_subs; s += gridDim.x) {
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    __syncthreads();  // the tile is zero again
+    for (int b0 = warp * 32; b0 < sp.z; b0 += V1_THREADS) {
+      uint32_t id = 0;
+      float2* mycp = coef + lane * V1_CSTRIDE;
+      const int off = v1_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, P, PP, mycp, id);
+      if (off >= 0) mycp[18] = in[id];
+      meta[lane] = off;
+      __syncwarp();
+      for (int p = 0; p < 32; ++p) {
+        const int mo = meta[p];
+        if (mo < 0) continue;
+        const float2* cp = coef + p * V1_CSTRIDE;
+        const float2 v = cp[18];
+        const float2 a = cmulc(v, cmul(cp[jx], cp[6 + jy]));  // v conj(cx cy)
+        float2* tp = tile + mo + main_off;
+#pragma unroll
+        for (int jz = 0; jz < 6; ++jz) {
+          const float2 w = cmulc(a, cp[12 + jz]);
+          atomicAdd(&tp[jz * PP].x, w.x);
+          atomicAdd(&tp[jz * PP].y, w.y);
+        }
+        if (lane < 24) {
+          const float2 w = cmulc(v, cmul(cmul(cp[ox], cp[11]), cp[12 + oz]));
+          atomicAdd(&tile[mo + ovf_off].x, w.x);
+          atomicAdd(&tile[mo + ovf_off].y, w.y);
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    const int n = E * E * E;
+    for (int idx = threadIdx.x; idx < n; idx += V1_THREADS) {
+      const int ix = idx % E;
+      const int t = idx / E;
+      const int iy = t % E, iz = t / E;
+      float2* cell = tile + iz * PP + iy * P + ix;
+      const float2 v = *cell;
+      if (v.x == 0.f && v.y == 0.f) continue;
+      *cell = make_float2(0.f, 0.f);
+      int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      gz -= gz >= K ? K : 0;
+      atomicAdd(&grid[((size_t)gz * K + gy) * K + gx], v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// variant 2 (J = 6): every warp owns a private, unpadded E^3 tile (E = T + 5)
+// and takes whole subproblems from a device work counter; the coefficient
+// table is shared by the CTA in shared memory.  The gather works as in
+// variant 1; the spread accumulates with plain read-modify-writes (no shared
+// atomics: the warp is the only writer of its tile, and within one point its
+// lanes touch distinct cells), then adds the tile to the grid with vector
+// atomics.
+//
+// Lane assignment: lanes 0..31 serve 32 of the 36 (jx, jy) tap pairs for every
+// jz; lanes 0..23 serve the remaining 4 pairs x 6 jz.  The assignment is chosen
+// so that within each half-warp the offsets jx + E jy (+ E^2 jz) are distinct
+// modulo 16 float2 (= 32 banks): every shared access is one wavefront per
+// half-warp with the unpadded pitch.  Encoded as jx + 8 jy (+ 64 jz).
+// ---------------------------------------------------------------------------
+__device__ const unsigned char kLaneMain13[32] = {0, 8, 16, 32, 9, 17, 25, 2, 10, 18, 26, 34, 3, 35, 12, 5, 24, 40, 33, 42, 11, 19, 27, 43, 20, 28, 36, 13, 21, 29, 37, 45};
+__device__ const unsigned short kLaneOvf13[24] = {1, 65, 129, 193, 257, 321, 41, 105, 4, 68, 132, 196, 260, 172, 236, 300, 169, 233, 297, 361, 324, 44, 108, 364};
+__device__ const unsigned char kLaneMain21[32] = {0, 8, 16, 32, 9, 17, 2, 10, 18, 26, 3, 11, 19, 12, 20, 21, 24, 40, 1, 25, 34, 42, 27, 35, 43, 28, 36, 44, 5, 13, 29, 45};
+__device__ const unsigned short kLaneOvf21[24] = {33, 97, 161, 225, 289, 41, 105, 169, 4, 68, 132, 196, 260, 324, 101, 165, 353, 233, 297, 361, 37, 229, 293, 357};
+
+constexpr int V2_WARPS = 8;
+constexpr int V2_CSTRIDE = 18;  // float2 per point: cx[6] cy[6] cz[6]
+
+struct V2Layout {
+  int E;
+  size_t table_bytes, warp_bytes, bytes;
+};
+
+__host__ __device__ inline V2Layout v2_layout(int T, int L) {
+  V2Layout l;
+  l.E = T + 5;
+  l.table_bytes = (size_t)(L + 1) * 6 * sizeof(float2);
+  size_t w = (size_t)32 * V2_CSTRIDE * sizeof(float2)   // coefficients
+             + 32 * sizeof(float2)                      // point values (spread)
+             + (size_t)l.E * l.E * l.E * sizeof(float2) // tile
+             + 32 * sizeof(int);                        // tile offsets
+  l.warp_bytes = (w + 15) / 16 * 16;
+  l.bytes = l.table_bytes + V2_WARPS * l.warp_bytes;
+  return l;
+}
+
+struct V2Lanes {
+  int main_off, ovf_off;
+  int mjx, mjy, ojx, ojy, ojz;
+};
+
+__device__ __forceinline__ V2Lanes v2_lanes(int E, int lane) {
+  const unsigned m = (E == 13) ? kLaneMain13[lane] : kLaneMain21[lane];
+  const unsigned o = lane < 24 ? ((E == 13) ? kLaneOvf13[lane] : kLaneOvf21[lane]) : 0u;
+  V2Lanes r;
+  r.mjx = m & 7;
+  r.mjy = (m >> 3) & 7;
+  r.ojx = o & 7;
+  r.ojy = (o >> 3) & 7;
+  r.ojz = (o >> 6) & 7;
+  r.main_off = r.mjx + E * r.mjy;
+  r.ovf_off = r.ojx + E * r.ojy + E * E * r.ojz;
+  return r;
+}
+
+// Phase 1 (one point per lane): decode, locate in the tile, interpolate the 18
+// coefficients from the shared table and store them as nine float4.
+__device__ __forceinline__ int v2_phase1(const InterpGeom& g, const float2* table, int pi, int cnt, int start,
+                                         int x0, int y0, int z0, int E, float2* cp, uint32_t& id) {
+  if (pi >= cnt) return -1;
+  id = g.sorted[start + pi];
+  int w0[3];
+  float f[3];
+  decode_point<6>(g, id, w0, f);
+  const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+  if ((unsigned)lx >= (unsigned)g.T || (unsigned)ly >= (unsigned)g.T || (unsigned)lz >= (unsigned)g.T) {
+    atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+    return -1;
+  }
+  float4* c4 = (float4*)cp;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float fl = f[a] * (float)g.L;
+    int i = (int)fl;
+    if (i > g.L - 1) i = g.L - 1;
+    const float t = fl - (float)i;
+    const float4* r0 = (const float4*)(table + i * 6);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 a0 = r0[q], a1 = r0[q + 3];
+      c4[a * 3 + q] = make_float4(fmaf(t, a1.x - a0.x, a0.x), fmaf(t, a1.y - a0.y, a0.y),
+                                  fmaf(t, a1.z - a0.z, a0.z), fmaf(t, a1.w - a0.w, a0.w));
+    }
+  }
+  return (lz * E + ly) * E + lx;
+}
+
+template <typename G>
+__global__ void __launch_bounds__(V2_WARPS * 32, 1) k_gather_v2(InterpGeom g, const typename G::T* __restrict__ grid,
+                                                                float inv_scale, const int4* __restrict__ subs,
+                                                                int n_subs, int* __restrict__ counter,
+                                                                float2* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const V2Layout lay = v2_layout(g.T, g.L);
+  float2* table = (float2*)smem_raw;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* coef = (float2*)(smem_raw + lay.table_bytes + warp * lay.warp_bytes);
+  float2* tile = coef + 32 * V2_CSTRIDE + 32;
+  const int E = lay.E, E3 = E * E * E, PP = E * E;
+  int* meta = (int*)(tile + E3);
+  for (int i = threadIdx.x; i < (g.L + 1) * 6; i += blockDim.x) table[i] = __ldg(g.table + i);
+  __syncthreads();
+  const V2Lanes ln = v2_lanes(E, lane);
+  const int T = g.T, nT = g.nT, K = g.K;
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(counter, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= n_subs) break;
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    for (int idx = lane; idx < E3; idx += 32) {
+      const int ix = idx % E;
+      const int t = idx / E;
+      const int iy = t % E, iz = t / E;
+      int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      gz -= gz >= K ? K : 0;
+      tile[idx] = G::load(grid, ((size_t)gz * K + gy) * K + gx, inv_scale);
+    }
+    __syncwarp();
+    for (int b0 = 0; b0 < sp.z; b0 += 32) {
+      uint32_t id = 0;
+      const int off = v2_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, E, coef + lane * V2_CSTRIDE, id);
+      meta[lane] = off;
+      __syncwarp();
+      float2 acc[32];
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        const int mo = meta[p];
+        float2 r = make_float2(0.f, 0.f);
+        if (mo >= 0) {
+          const float2* cp = coef + p * V2_CSTRIDE;
+          const float2 cxy = cmul(cp[ln.mjx], cp[6 + ln.mjy]);
+          const float4 z01 = *(const float4*)(cp + 12);
+          const float4 z23 = *(const float4*)(cp + 14);
+          const float4 z45 = *(const float4*)(cp + 16);
+          const float2* tp = tile + mo + ln.main_off;
+          float2 sa = make_float2(0.f, 0.f);
+          cmac(sa, make_float2(z01.x, z01.y), tp[0]);
+          cmac(sa, make_float2(z01.z, z01.w), tp[PP]);
+          cmac(sa, make_float2(z23.x, z23.y), tp[2 * PP]);
+          cmac(sa, make_float2(z23.z, z23.w), tp[3 * PP]);
+          cmac(sa, make_float2(z45.x, z45.y), tp[4 * PP]);
+          cmac(sa, make_float2(z45.z, z45.w), tp[5 * PP]);
+          r = cmul(cxy, sa);
+          if (lane < 24) {
+            const float2 w = cmul(cmul(cp[ln.ojx], cp[6 + ln.ojy]), cp[12 + ln.ojz]);
+            cmac(r, w, tile[mo + ln.ovf_off]);
+          }
+        }
+        acc[p] = r;
+      }
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const bool upper = (lane & sh) != 0;
+#pragma unroll
+        for (int i = 0; i < sh; ++i) {
+          const float2 send = upper ? acc[i] : acc[i + sh];
+          const float2 keep = upper ? acc[i + sh] : acc[i];
+          const float rx = __shfl_xor_sync(0xffffffffu, send.x, sh);
+          const float ry = __shfl_xor_sync(0xffffffffu, send.y, sh);
+          acc[i] = make_float2(keep.x + rx, keep.y + ry);
+        }
+      }
+      if (off >= 0) out[id] = acc[0];
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(V2_WARPS * 32, 1) k_spread_v2(InterpGeom g, const float2* __restrict__ in,
+                                                                const int4* __restrict__ subs, int n_subs,
+                                                                int* __restrict__ counter,
+                                                                float2* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const V2Layout lay = v2_layout(g.T, g.L);
+  float2* table = (float2*)smem_raw;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* coef = (float2*)(smem_raw + lay.table_bytes + warp * lay.warp_bytes);
+  float2* vals = coef + 32 * V2_CSTRIDE;
+  float2* tile = vals + 32;
+  const int E = lay.E, E3 = E * E * E, PP = E * E;
+  int* meta = (int*)(tile + E3);
+  for (int i = threadIdx.x; i < (g.L + 1) * 6; i += blockDim.x) table[i] = __ldg(g.table + i);
+  for (int i = lane; i < E3; i += 32) tile[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const V2Lanes ln = v2_lanes(E, lane);
+  const int T = g.T, nT = g.nT, K = g.K;
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(counter, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= n_subs) break;
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    for (int b0 = 0; b0 < sp.z; b0 += 32) {
+      uint32_t id = 0;
+      const int off = v2_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, E, coef + lane * V2_CSTRIDE, id);
+      vals[lane] = off >= 0 ? in[id] : make_float2(0.f, 0.f);
+      meta[lane] = off;
+      __syncwarp();
+      for (int p = 0; p < 32; ++p) {
+        const int mo = meta[p];
+        if (mo < 0) continue;
+        const float2* cp = coef + p * V2_CSTRIDE;
+        const float2 v = vals[p];
+        const float2 a = cmulc(v, cmul(cp[ln.mjx], cp[6 + ln.mjy]));  // v conj(cx cy)
+        float2* tp = tile + mo + ln.main_off;
+        float2 t[6];
+#pragma unroll
+        for (int jz = 0; jz < 6; ++jz) t[jz] = tp[jz * PP];
+#pragma unroll
+        for (int jz = 0; jz < 6; ++jz) {
+          const float2 cz = cp[12 + jz];
+          // t += a conj(cz)
+          t[jz].x = fmaf(a.x, cz.x, fmaf(a.y, cz.y, t[jz].x));
+          t[jz].y = fmaf(a.y, cz.x, fmaf(-a.x, cz.y, t[jz].y));
+        }
+#pragma unroll
+        for (int jz = 0; jz < 6; ++jz) tp[jz * PP] = t[jz];
+        if (lane < 24) {
+          const float2 w = cmulc(v, cmul(cmul(cp[ln.ojx], cp[6 + ln.ojy]), cp[12 + ln.ojz]));
+          float2* q = tile + mo + ln.ovf_off;
+          float2 u = *q;
+          u.x += w.x;
+          u.y += w.y;
+          *q = u;
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    for (int idx = lane; idx < E3; idx += 32) {
+      const float2 v = tile[idx];
+      if (v.x == 0.f && v.y == 0.f) continue;
+      tile[idx] = make_float2(0.f, 0.f);
+      const int ix = idx % E;
+      const int t = idx / E;
+      const int iy = t % E, iz = t / E;
+      int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      gz -= gz >= K ? K : 0;
+      atomicAdd(&grid[((size_t)gz * K + gy) * K + gx], v);
+    }
+    __syncwarp();
+  }
+}
+
+static int g_num_sms = 0;
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 152;
+  }
+  return g_num_sms;
+}
+
+static int max_optin_smem() {
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return maxsm;
+}
+
+bool v2_supported(int T, int J, int L) {
+  return J == 6 && (T == 8 || T == 16) && v2_layout(T, L).bytes <= (size_t)max_optin_smem();
+}
+
+static bool v1_fits(const InterpGeom& g) {
+  if (g.J != 6) return false;
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v1_layout(g.T, g.L).bytes <= (size_t)maxsm;
+}
+
+template <typename G>
+static cudaError_t launch_gather_v1_t(const InterpGeom& g, const void* grid, float inv_scale, const int4* subs,
+                                      int n_subs, float2* out, cudaStream_t st) {
+  auto f = k_gather_v1<G>;
+  const size_t smem = v1_layout(g.T, g.L).bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  const int grid_x = n_subs < num_sms() ? n_subs : num_sms();
+  f<<<grid_x, V1_THREADS, smem, st>>>(g, (const typename G::T*)grid, inv_scale, subs, n_subs, out);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_spread_v1(const InterpGeom& g, const float2* in, const int4* subs, int n_subs,
+                                    float2* grid, cudaStream_t st) {
+  auto f = k_spread_v1;
+  const size_t smem = v1_layout(g.T, g.L).bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  const int grid_x = n_subs < num_sms() ? n_subs : num_sms();
+  f<<<grid_x, V1_THREADS, smem, st>>>(g, in, subs, n_subs, grid);
+  return cudaGetLastError();
+}
+
 size_t interp_smem_bytes(int T, int J) {
   const size_t E = (size_t)T + J - 1;
   return E * E * E * sizeof(float2);
@@ -210,9 +752,38 @@ static cudaError_t launch_gather_v0_j(const InterpGeom& g, int dtype, const void
   return cudaErrorInvalidValue;
 }
 
+template <typename G>
+static cudaError_t launch_gather_v2_t(const InterpGeom& g, const void* grid, float inv_scale, const int4* subs,
+                                      int n_subs, int* counter, float2* out, cudaStream_t st) {
+  auto f = k_gather_v2<G>;
+  const size_t smem = v2_layout(g.T, g.L).bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  f<<<num_sms(), V2_WARPS * 32, smem, st>>>(g, (const typename G::T*)grid, inv_scale, subs, n_subs, counter, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const InterpGeom& g, int variant, int grid_dtype, const void* grid, float inv_scale,
                           const int4* subs, int n_subs, float2* out, cudaStream_t st) {
-  (void)variant;
+  if (variant == 2 && v2_supported(g.T, g.J, g.L)) {
+    switch (grid_dtype) {
+      case 0: return launch_gather_v2_t<GridC64>(g, grid, inv_scale, subs, n_subs, g.counter, out, st);
+      case 1: return launch_gather_v2_t<GridBF16>(g, grid, inv_scale, subs, n_subs, g.counter, out, st);
+      case 2: return launch_gather_v2_t<GridF16>(g, grid, inv_scale, subs, n_subs, g.counter, out, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+  if (variant == 1 && v1_fits(g)) {
+    switch (grid_dtype) {
+      case 0: return launch_gather_v1_t<GridC64>(g, grid, inv_scale, subs, n_subs, out, st);
+      case 1: return launch_gather_v1_t<GridBF16>(g, grid, inv_scale, subs, n_subs, out, st);
+      case 2: return launch_gather_v1_t<GridF16>(g, grid, inv_scale, subs, n_subs, out, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (g.J) {
     case 2: return launch_gather_v0_j<2>(g, grid_dtype, grid, inv_scale, subs, n_subs, out, st);
     case 4: return launch_gather_v0_j<4>(g, grid_dtype, grid, inv_scale, subs, n_subs, out, st);
@@ -236,7 +807,18 @@ static cudaError_t launch_spread_v0_t(const InterpGeom& g, const float2* in, con
 
 cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, const int4* subs, int n_subs,
                           float2* grid, cudaStream_t st) {
-  (void)variant;
+  if (variant == 2 && v2_supported(g.T, g.J, g.L)) {
+    auto f = k_spread_v2;
+    const size_t smem = v2_layout(g.T, g.L).bytes;
+    cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (n_subs == 0) return cudaSuccess;
+    e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    f<<<num_sms(), V2_WARPS * 32, smem, st>>>(g, in, subs, n_subs, g.counter + 1, grid);
+    return cudaGetLastError();
+  }
+  if (variant == 1 && v1_fits(g)) return launch_spread_v1(g, in, subs, n_subs, grid, st);
   switch (g.J) {
     case 2: return launch_spread_v0_t<2>(g, in, subs, n_subs, grid, st);
     case 4: return launch_spread_v0_t<4>(g, in, subs, n_subs, grid, st);

@@ -65,7 +65,7 @@ int resolve(const nufft3d_params* p, Resolved& r) {
     for (int m = 0; m < 2 * r.M; ++m)
       if (!std::isfinite(p->weight[m])) return NUFFT3D_ERR_ARG;
   }
-  r.T = 16;
+  r.T = r.J == 6 ? 8 : 16;
   while (r.T > 4 && (r.K % r.T != 0 || r.T + r.J - 1 > r.K)) r.T /= 2;
   r.nT = r.K / r.T;
   return NUFFT3D_OK;
@@ -229,7 +229,7 @@ void free_plan(nufft3d_plan pl) {
   if (!pl) return;
   void* ptrs[] = {pl->d_dir, pl->d_rad, pl->d_weight, pl->d_s, pl->d_table, pl->d_twK, pl->d_twM,
                   pl->d_sorted, pl->d_sub, pl->d_grid, pl->d_grid_lp, pl->d_bufA, pl->d_bufB,
-                  pl->d_lines, pl->d_err};
+                  pl->d_lines, pl->d_err, pl->d_counter};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : pl->ev_fwd) cudaEventDestroy(e);
@@ -251,19 +251,26 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.table = pl->d_table;
   g.sorted = pl->d_sorted;
   g.err = pl->d_err;
+  g.counter = pl->d_counter;
   return g;
 }
 
 int build_subproblems(nufft3d_plan pl, int S, cudaStream_t st) {
-  std::vector<int4> subs;
+  // subproblems of tiles holding more than S points (the dense centre of the
+  // radial pattern) come first, so the persistent kernels finish balanced;
+  // the rest follow in tile order (neighbouring tiles share halo cells in L2)
+  std::vector<int4> heavy, light;
   const size_t nb = pl->bin_offsets.size() - 1;
   for (size_t b = 0; b < nb; ++b) {
     const long long a = pl->bin_offsets[b], e = pl->bin_offsets[b + 1];
+    std::vector<int4>& dst = (e - a > S) ? heavy : light;
     for (long long s0 = a; s0 < e; s0 += S) {
       const int cnt = (int)std::min<long long>(S, e - s0);
-      subs.push_back(make_int4((int)b, (int)s0, cnt, 0));
+      dst.push_back(make_int4((int)b, (int)s0, cnt, 0));
     }
   }
+  std::vector<int4> subs(heavy);
+  subs.insert(subs.end(), light.begin(), light.end());
   if (pl->d_sub) {
     cudaFree(pl->d_sub);
     pl->d_sub = nullptr;
@@ -334,8 +341,8 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->grid_dtype = r.grid_dtype;
   pl->T = r.T;
   pl->nT = r.nT;
-  pl->gather_variant = 0;
-  pl->spread_variant = 0;
+  pl->gather_variant = nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0;
+  pl->spread_variant = pl->gather_variant;
   pl->lp_scale = 1.f;
   CK(cudaGetDevice(&pl->device));
   CK(upload(&pl->d_s, h.s, st));
@@ -346,6 +353,7 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   CK(upload(&pl->d_rad, h.rad, st));
   CK(upload(&pl->d_weight, h.weight, st));
   CK(dalloc(&pl->d_err, 1));
+  CK(dalloc(&pl->d_counter, 2));
   CK(cudaMemsetAsync(pl->d_err, 0, sizeof(int), st));
   CK(cudaStreamSynchronize(st));
   rc = sort_points(pl, st);
@@ -552,20 +560,37 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 }
 
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
-                      void* cuda_stream) {
+                      int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 1 || spread_variant < -1 || spread_variant > 1) return NUFFT3D_ERR_ARG;
-  if (points_per_subproblem < 0) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 2 || spread_variant < -1 || spread_variant > 2) return NUFFT3D_ERR_ARG;
+  if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
+  if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
+  if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
+  const int T = tile_edge > 0 ? tile_edge : plan->T;
+  const int gv = gather_variant >= 0 ? gather_variant : plan->gather_variant;
+  const int sv = spread_variant >= 0 ? spread_variant : plan->spread_variant;
+  if ((gv == 2 || sv == 2) && !nufft::v2_supported(T, plan->J, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
+  if ((gv == 1 || sv == 1) && plan->J != 6) return NUFFT3D_ERR_UNSUPPORTED;
   int rc = ensure_device(plan);
   if (rc != NUFFT3D_OK) return rc;
   CK(cudaStreamSynchronize(plan->last_stream));
-  if (gather_variant >= 0) plan->gather_variant = gather_variant;
-  if (spread_variant >= 0) plan->spread_variant = spread_variant;
-  if (points_per_subproblem > 0 && points_per_subproblem != plan->pts_per_sub) {
-    rc = build_subproblems(plan, points_per_subproblem, (cudaStream_t)cuda_stream);
+  plan->gather_variant = gv;
+  plan->spread_variant = sv;
+  const int S = points_per_subproblem > 0 ? points_per_subproblem : plan->pts_per_sub;
+  if (T != plan->T) {
+    plan->T = T;
+    plan->nT = plan->K / T;
+    if (plan->d_sorted) {
+      cudaFree(plan->d_sorted);
+      plan->d_sorted = nullptr;
+    }
+    rc = sort_points(plan, (cudaStream_t)cuda_stream);
     if (rc != NUFFT3D_OK) return rc;
+    rc = build_subproblems(plan, S, (cudaStream_t)cuda_stream);
+  } else if (S != plan->pts_per_sub) {
+    rc = build_subproblems(plan, S, (cudaStream_t)cuda_stream);
   }
-  return NUFFT3D_OK;
+  return rc;
 }
 
 int nufft3d_plan_set_timing(nufft3d_plan plan, int max_calls) {

@@ -166,3 +166,66 @@ def test_mid_workload_sampled_lines(cuda_lib):
     r = _run(cuda_lib, w.n, sub, w.m, w.k, w.j, w.table_oversamp, y=y)
     ref = O.nufft_adjoint(y.astype(np.complex128), _oplan(w.n, sub, w.m, w.k, w.j, w.table_oversamp))
     assert O.rel_l2(r["adj"], ref) < TOL
+
+
+@pytest.mark.parametrize("variant,pps,tile", [(0, 1024, 8), (0, 700, 16), (1, 1024, 16), (1, 300, 8),
+                                               (2, 1024, 8), (2, 64, 8), (2, 5000, 8)])
+def test_kernel_variants_and_subproblem_split(cuda_lib, variant, pps, tile):
+    """Every gather/spread variant, tile edge and subproblem size gives the same operator."""
+    import torch
+
+    n, ndir = 32, 700
+    dirs = I.umbrella_directions(35, 20)
+    x = I.random_volume(n, 12).astype(np.float32)
+    y = I.random_lines(ndir, 2 * n, 13).astype(np.complex64)
+    plan = cuda_lib.Plan(n, dirs)
+    plan.tune(variant, variant, pps, tile)
+    info = plan.info()
+    assert info["gather_variant"] == variant and info["points_per_subproblem"] == pps
+    assert info["tile"] == tile
+    p = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    a = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    op = _oplan(n, dirs)
+    assert O.rel_l2(p, O.nufft_forward(x.astype(np.float64), op)) < TOL
+    assert O.rel_l2(a, O.nufft_adjoint(y.astype(np.complex128), op)) < TOL
+
+
+def test_unsupported_tuning_is_refused(cuda_lib):
+    """Variant 2 needs a warp-private tile that fits shared memory (T = 8)."""
+    n = 32
+    plan = cuda_lib.Plan(n, I.random_directions(10, 1))
+    with pytest.raises(cuda_lib.NufftError) as ei:
+        plan.tune(2, 2, 1024, 16)
+    assert ei.value.status == -4
+    with pytest.raises(cuda_lib.NufftError):
+        plan.tune(3, 0, 0, 0)
+    assert plan.info()["gather_variant"] == 2 and plan.info()["tile"] == 8
+
+
+def test_variant1_dense_center_and_repeat_calls(cuda_lib):
+    """Many lines through the centre (dense tiles, split subproblems), repeated
+    calls on one plan give identical forward results."""
+    import torch
+
+    n = 32
+    dirs = I.umbrella_directions(90, 64)
+    x = torch.from_numpy(I.random_volume(n, 14).astype(np.float32)).cuda()
+    plan = cuda_lib.Plan(n, dirs)
+    assert plan.info()["gather_variant"] == 2  # the default for J = 6
+    plan.tune(-1, -1, 2048)
+    p1 = plan.forward(x).clone()
+    p2 = plan.forward(x)
+    assert torch.equal(p1, p2)
+    op = _oplan(n, dirs)
+    lines = np.arange(0, dirs.shape[0], 41)
+    ref = O.nufft_forward(x.cpu().numpy().astype(np.float64), op, lines=lines)
+    assert O.rel_l2(p1.cpu().numpy()[lines], ref) < TOL
+    y = torch.from_numpy(I.random_lines(dirs.shape[0], 2 * n, 15).astype(np.complex64)).cuda()
+    a1 = plan.adjoint(y).cpu().numpy()
+    sub = np.arange(0, dirs.shape[0], 7)
+    ysub = y.cpu().numpy()[sub]
+    r = _run(cuda_lib, n, dirs[sub], y=ysub)
+    ref = O.nufft_adjoint(ysub.astype(np.complex128), _oplan(n, dirs[sub]))
+    assert O.rel_l2(r["adj"], ref) < TOL
+    assert np.isfinite(a1).all()
