@@ -141,6 +141,26 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
                       int points_per_subproblem, int tile_edge, void* cuda_stream);
 
+/* Allocation-free adjoint.  The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory when they need the adjoint
+ * (code running while a stream is captured into a CUDA graph in global capture
+ * mode, host frameworks whose device memory belongs to their own pool
+ * allocator, real-time loops that must stay out of the driver's allocator).
+ * Same arguments and result as nufft3d_adjoint on the same plan, but every
+ * scratch buffer (line-DFT output, K^3 grid, inverse-FFT intermediates, work
+ * counters) comes from one static 8 MiB device array inside the library, not
+ * from the plan's workspace; it calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Limit: (D*M if the plan applies the line DFT) + K^3 +
+ * N*K^2 + N^2*K complex64 values, each rounded up to 256 bytes, plus 256 bytes,
+ * must fit in 8 MiB (for example N = 32, K = 64 with D*M up to about 500,000);
+ * larger plans return NUFFT3D_ERR_UNSUPPORTED.  Every GPU that loads the
+ * library holds the 8 MiB until the process exits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls share the one array
+ * (which keeps the last call's contents; the grid and counters are cleared on
+ * every call): calls that overlap on the GPU, on any streams or plans, race. */
+int nufft3d_adjoint_noalloc(nufft3d_plan plan, const void* lines_dev, void* vol_dev, void* cuda_stream);
+
 /* Per-stage timing with CUDA events recorded on the launching stream between
  * the kernels of each call.  nufft3d_plan_set_timing(plan, n) arms timing of
  * the next n forward and n adjoint calls (0 disarms; it synchronises the

@@ -28,6 +28,7 @@ EXPORTS = (
     "nufft3d_plan_tune",
     "nufft3d_plan_set_timing",
     "nufft3d_plan_stage_times",
+    "nufft3d_adjoint_noalloc",
 )
 
 FWD_STAGES = ("x_pass", "y_pass", "z_pass", "gather", "line_dft")
@@ -79,6 +80,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.nufft3d_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), vp]
     lib.nufft3d_forward.argtypes = [vp, vp, vp, vp]
     lib.nufft3d_adjoint.argtypes = [vp, vp, vp, vp]
+    lib.nufft3d_adjoint_noalloc.argtypes = [vp, vp, vp, vp]
     lib.nufft3d_workspace_bytes.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
     lib.nufft3d_plan_sync_status.argtypes = [vp, ip]
     lib.nufft3d_plan_destroy.argtypes = [vp]
