@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--gather-variant", type=int, default=-1)
     ap.add_argument("--spread-variant", type=int, default=-1)
     ap.add_argument("--points-per-subproblem", type=int, default=0)
+    ap.add_argument("--tile-edge", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-lines", type=int, default=1500)
@@ -319,7 +320,7 @@ def run_ours(args):
     x = w.volume(np.float32)
     t0 = time.perf_counter()
     plan = Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp, grid_dtype=args.grid_dtype)
-    plan.tune(args.gather_variant, args.spread_variant, args.points_per_subproblem)
+    plan.tune(args.gather_variant, args.spread_variant, args.points_per_subproblem, args.tile_edge)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     P = plan.n_points

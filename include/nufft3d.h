@@ -133,8 +133,10 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
  * subproblem and the grid tile edge T of a plan (-1 / 0 keep the current
  * choice).  Variants: 0 one thread per point, one CTA per subproblem (any
  * J); 1 one warp per point, CTA-shared tile (J = 6); 2 one warp per point,
- * warp-private tile, no shared atomics (J = 6, T = 8; the default when
- * available).  T is 4, 8 or 16; changing it re-sorts the points.
+ * warp-private tile, no shared atomics (J = 6, T = 8; the default spread
+ * when available); gather only: 3 one thread per point, points reordered so
+ * that every half-warp's tile accesses fall in distinct banks (any J; the
+ * default gather).  T is 4, 8 or 16; changing it re-sorts the points.
  * Synchronises the plan's last stream and works on cuda_stream.  Returns
  * NUFFT3D_ERR_UNSUPPORTED for a combination the plan cannot run.  Used by
  * the autotuner. */

@@ -20,6 +20,7 @@ struct InterpGeom {
   const uint32_t* sorted;  // point ids sorted by tile
   int* err;              // device check word
   int* counter;          // two work counters (gather, spread) for the persistent variants
+  int S;                 // most points in one subproblem
 };
 
 bool fft_length_supported(int L);
@@ -47,6 +48,7 @@ cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, co
                           float2* grid, cudaStream_t st);
 size_t interp_smem_bytes(int T, int J);
 bool v2_supported(int T, int J, int L);
+bool v3_supported(int T, int J, int S);
 
 }  // namespace nufft
 

@@ -669,6 +669,140 @@ __global__ void __launch_bounds__(V2_WARPS * 32, 1) k_spread_v2(InterpGeom g, co
   }
 }
 
+// ---------------------------------------------------------------------------
+// variant 3 (gather, any J): one thread per point, with the points of a
+// subproblem reordered so that the 16 lanes of every half-warp hold points
+// whose first-tap offsets in the unpadded tile differ modulo 16 float2.  All
+// lanes then add the same tap offset, so every tap load of the warp touches 16
+// distinct bank pairs per half-warp (one wavefront), while the arithmetic
+// stays at one thread per point (no cross-lane reduction, no shared
+// coefficient buffers).
+//
+// Order: points are counted per residue class c = off mod 16; the point of
+// rank r in class c goes to position sum_c' min(n_c', r) + #{c' < c : n_c' > r}
+// (round robin over the classes that still have points).
+// ---------------------------------------------------------------------------
+constexpr int V3_THREADS = 256;
+
+struct V3Layout {
+  int E;
+  size_t tile_bytes, bytes;
+};
+
+__host__ __device__ inline V3Layout v3_layout(int T, int J, int S) {
+  V3Layout l;
+  l.E = T + J - 1;
+  l.tile_bytes = ((size_t)l.E * l.E * l.E * sizeof(float2) + 15) / 16 * 16;
+  // per point: id, tile offset, f[3] (5 words) + ordered index (1 word); class counts
+  l.bytes = l.tile_bytes + (size_t)S * 6 * sizeof(int) + 32 * sizeof(int);
+  return l;
+}
+
+template <int J, typename G>
+__global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const typename G::T* __restrict__ grid,
+                                                          float inv_scale, const int4* __restrict__ subs, int S,
+                                                          float2* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int T = g.T, nT = g.nT, K = g.K;
+  const V3Layout lay = v3_layout(T, J, S);
+  const int E = lay.E, PP = E * E;
+  float2* tile = (float2*)smem_raw;
+  int* p_id = (int*)(smem_raw + lay.tile_bytes);
+  int* p_off = p_id + S;
+  float* p_f = (float*)(p_off + S);  // [3][S]
+  int* order = (int*)(p_f + 3 * S);
+  int* ncls = order + S;             // [16] counts, [16] cursors
+  const int4 sp = subs[blockIdx.x];
+  const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+  const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+  const int cnt = sp.z;
+  if (threadIdx.x < 32) ncls[threadIdx.x] = 0;
+  stage_tile_plain<G>(grid, inv_scale, K, E, x0, y0, z0, tile);
+  __syncthreads();
+  // decode every point of the subproblem once
+  for (int i = threadIdx.x; i < cnt; i += V3_THREADS) {
+    const uint32_t id = g.sorted[sp.y + i];
+    int w0[3];
+    float f[3];
+    decode_point<J>(g, id, w0, f);
+    const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+    int off = -1;
+    if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+      off = (lz * E + ly) * E + lx;
+    } else {
+      atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+    }
+    p_id[i] = (int)id;
+    p_off[i] = off;
+    p_f[i] = f[0];
+    p_f[S + i] = f[1];
+    p_f[2 * S + i] = f[2];
+    atomicAdd(&ncls[off < 0 ? 0 : (off & 15)], 1);
+  }
+  __syncthreads();
+  // rank within the class, then the round-robin position
+  for (int i = threadIdx.x; i < cnt; i += V3_THREADS) {
+    const int c = p_off[i] < 0 ? 0 : (p_off[i] & 15);
+    const int r = atomicAdd(&ncls[16 + c], 1);
+    int pos = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int n = ncls[q];
+      pos += n < r ? n : r;
+      pos += (q < c && n > r) ? 1 : 0;
+    }
+    order[pos] = i;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < cnt; k += V3_THREADS) {
+    const int i = order[k];
+    const int off = p_off[i];
+    if (off < 0) continue;
+    float2 cx[J], cy[J], cz[J];
+    table_coeffs<J>(g.table, g.L, p_f[i], cx);
+    table_coeffs<J>(g.table, g.L, p_f[S + i], cy);
+    table_coeffs<J>(g.table, g.L, p_f[2 * S + i], cz);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int jz = 0; jz < J; ++jz) {
+      float2 zacc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jy = 0; jy < J; ++jy) {
+        const float2* tp = tile + off + jz * PP + jy * E;
+        float2 row = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jx = 0; jx < J; ++jx) cmac(row, cx[jx], tp[jx]);
+        cmac(zacc, cy[jy], row);
+      }
+      cmac(acc, cz[jz], zacc);
+    }
+    out[p_id[i]] = acc;
+  }
+}
+
+template <int J, typename G>
+static cudaError_t launch_gather_v3_t(const InterpGeom& g, const void* grid, float inv_scale, const int4* subs,
+                                      int n_subs, int S, float2* out, cudaStream_t st) {
+  auto f = k_gather_v3<J, G>;
+  const size_t smem = v3_layout(g.T, J, S).bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  f<<<n_subs, V3_THREADS, smem, st>>>(g, (const typename G::T*)grid, inv_scale, subs, S, out);
+  return cudaGetLastError();
+}
+
+template <int J>
+static cudaError_t launch_gather_v3_j(const InterpGeom& g, int dtype, const void* grid, float inv_scale,
+                                      const int4* subs, int n_subs, int S, float2* out, cudaStream_t st) {
+  switch (dtype) {
+    case 0: return launch_gather_v3_t<J, GridC64>(g, grid, inv_scale, subs, n_subs, S, out, st);
+    case 1: return launch_gather_v3_t<J, GridBF16>(g, grid, inv_scale, subs, n_subs, S, out, st);
+    case 2: return launch_gather_v3_t<J, GridF16>(g, grid, inv_scale, subs, n_subs, S, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 static int g_num_sms = 0;
 static int num_sms() {
   if (g_num_sms == 0) {
@@ -685,6 +819,10 @@ static int max_optin_smem() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   return maxsm;
+}
+
+bool v3_supported(int T, int J, int S) {
+  return v3_layout(T, J, S).bytes <= (size_t)max_optin_smem();
 }
 
 bool v2_supported(int T, int J, int L) {
@@ -768,6 +906,15 @@ static cudaError_t launch_gather_v2_t(const InterpGeom& g, const void* grid, flo
 
 cudaError_t launch_gather(const InterpGeom& g, int variant, int grid_dtype, const void* grid, float inv_scale,
                           const int4* subs, int n_subs, float2* out, cudaStream_t st) {
+  if (variant == 3) {
+    switch (g.J) {
+      case 2: return launch_gather_v3_j<2>(g, grid_dtype, grid, inv_scale, subs, n_subs, g.S, out, st);
+      case 4: return launch_gather_v3_j<4>(g, grid_dtype, grid, inv_scale, subs, n_subs, g.S, out, st);
+      case 6: return launch_gather_v3_j<6>(g, grid_dtype, grid, inv_scale, subs, n_subs, g.S, out, st);
+      case 8: return launch_gather_v3_j<8>(g, grid_dtype, grid, inv_scale, subs, n_subs, g.S, out, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (variant == 2 && v2_supported(g.T, g.J, g.L)) {
     switch (grid_dtype) {
       case 0: return launch_gather_v2_t<GridC64>(g, grid, inv_scale, subs, n_subs, g.counter, out, st);

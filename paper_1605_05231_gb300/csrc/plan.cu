@@ -252,6 +252,7 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.sorted = pl->d_sorted;
   g.err = pl->d_err;
   g.counter = pl->d_counter;
+  g.S = pl->pts_per_sub;
   return g;
 }
 
@@ -341,8 +342,8 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->grid_dtype = r.grid_dtype;
   pl->T = r.T;
   pl->nT = r.nT;
-  pl->gather_variant = nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0;
-  pl->spread_variant = pl->gather_variant;
+  pl->spread_variant = nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0;
+  pl->gather_variant = nufft::v3_supported(r.T, r.J, 1024) ? 3 : 0;
   pl->lp_scale = 1.f;
   CK(cudaGetDevice(&pl->device));
   CK(upload(&pl->d_s, h.s, st));
@@ -562,7 +563,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 2 || spread_variant < -1 || spread_variant > 2) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 3 || spread_variant < -1 || spread_variant > 2) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -571,6 +572,8 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   const int sv = spread_variant >= 0 ? spread_variant : plan->spread_variant;
   if ((gv == 2 || sv == 2) && !nufft::v2_supported(T, plan->J, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
   if ((gv == 1 || sv == 1) && plan->J != 6) return NUFFT3D_ERR_UNSUPPORTED;
+  const int S_new = points_per_subproblem > 0 ? points_per_subproblem : plan->pts_per_sub;
+  if (gv == 3 && !nufft::v3_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   int rc = ensure_device(plan);
   if (rc != NUFFT3D_OK) return rc;
   CK(cudaStreamSynchronize(plan->last_stream));

@@ -17,10 +17,12 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def _run(binding, n, dirs, m=0, k=0, j=6, L=1024, x=None, y=None, **kw):
+def _run(binding, n, dirs, m=0, k=0, j=6, L=1024, x=None, y=None, gather_variant=-1, **kw):
     import torch
 
     plan = binding.Plan(n, dirs, m=m, k=k, j=j, table_oversamp=L, **kw)
+    if gather_variant >= 0:
+        plan.tune(gather_variant)
     out = {}
     if x is not None:
         out["fwd"] = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
@@ -54,6 +56,7 @@ def test_tiny_workload_forward_adjoint(cuda_lib):
     assert O.rel_l2(r["fwd"][lines], ex) < 3e-5
 
 
+@pytest.mark.parametrize("gv", [-1, 3])
 @pytest.mark.parametrize("n,k,m,ndir,j,L", [
     (16, 32, 32, 37, 6, 1024),     # ragged line count (not a multiple of 16)
     (24, 48, 48, 50, 6, 1024),     # radix-3 grid and line lengths
@@ -63,11 +66,11 @@ def test_tiny_workload_forward_adjoint(cuda_lib):
     (20, 64, 48, 17, 2, 2048),     # J = 2, M != K
     (64, 128, 128, 300, 6, 1024),  # several 16^3 tiles per axis
 ])
-def test_shapes_taps_tables(cuda_lib, n, k, m, ndir, j, L):
+def test_shapes_taps_tables(cuda_lib, n, k, m, ndir, j, L, gv):
     dirs = I.random_directions(ndir, n + ndir)
     x = I.random_volume(n, 1).astype(np.float32)
     y = I.random_lines(ndir, m, 2).astype(np.complex64)
-    r = _run(cuda_lib, n, dirs, m, k, j, L, x=x, y=y)
+    r = _run(cuda_lib, n, dirs, m, k, j, L, x=x, y=y, gather_variant=gv)
     op = _oplan(n, dirs, m, k, j, L)
     assert O.rel_l2(r["fwd"], O.nufft_forward(x.astype(np.float64), op)) < TOL
     assert O.rel_l2(r["adj"], O.nufft_adjoint(y.astype(np.complex128), op)) < TOL
@@ -168,9 +171,10 @@ def test_mid_workload_sampled_lines(cuda_lib):
     assert O.rel_l2(r["adj"], ref) < TOL
 
 
-@pytest.mark.parametrize("variant,pps,tile", [(0, 1024, 8), (0, 700, 16), (1, 1024, 16), (1, 300, 8),
-                                               (2, 1024, 8), (2, 64, 8), (2, 5000, 8)])
-def test_kernel_variants_and_subproblem_split(cuda_lib, variant, pps, tile):
+@pytest.mark.parametrize("gv,sv,pps,tile", [(0, 0, 1024, 8), (0, 0, 700, 16), (1, 1, 1024, 16), (1, 1, 300, 8),
+                                            (2, 2, 1024, 8), (2, 2, 64, 8), (2, 2, 5000, 8), (3, 2, 1024, 8),
+                                            (3, 0, 2048, 16), (3, 2, 37, 8)])
+def test_kernel_variants_and_subproblem_split(cuda_lib, gv, sv, pps, tile):
     """Every gather/spread variant, tile edge and subproblem size gives the same operator."""
     import torch
 
@@ -179,10 +183,10 @@ def test_kernel_variants_and_subproblem_split(cuda_lib, variant, pps, tile):
     x = I.random_volume(n, 12).astype(np.float32)
     y = I.random_lines(ndir, 2 * n, 13).astype(np.complex64)
     plan = cuda_lib.Plan(n, dirs)
-    plan.tune(variant, variant, pps, tile)
+    plan.tune(gv, sv, pps, tile)
     info = plan.info()
-    assert info["gather_variant"] == variant and info["points_per_subproblem"] == pps
-    assert info["tile"] == tile
+    assert info["gather_variant"] == gv and info["spread_variant"] == sv
+    assert info["points_per_subproblem"] == pps and info["tile"] == tile
     p = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     a = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
     assert plan.sync_status() == 0
@@ -199,8 +203,8 @@ def test_unsupported_tuning_is_refused(cuda_lib):
         plan.tune(2, 2, 1024, 16)
     assert ei.value.status == -4
     with pytest.raises(cuda_lib.NufftError):
-        plan.tune(3, 0, 0, 0)
-    assert plan.info()["gather_variant"] == 2 and plan.info()["tile"] == 8
+        plan.tune(4, 0, 0, 0)
+    assert plan.info()["gather_variant"] == 3 and plan.info()["tile"] == 8
 
 
 def test_variant1_dense_center_and_repeat_calls(cuda_lib):
@@ -212,7 +216,7 @@ def test_variant1_dense_center_and_repeat_calls(cuda_lib):
     dirs = I.umbrella_directions(90, 64)
     x = torch.from_numpy(I.random_volume(n, 14).astype(np.float32)).cuda()
     plan = cuda_lib.Plan(n, dirs)
-    assert plan.info()["gather_variant"] == 2  # the default for J = 6
+    assert plan.info()["spread_variant"] == 2  # the default for J = 6
     plan.tune(-1, -1, 2048)
     p1 = plan.forward(x).clone()
     p2 = plan.forward(x)
