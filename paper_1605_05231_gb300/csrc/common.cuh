@@ -110,6 +110,26 @@ __device__ __forceinline__ void table_coeffs(const float2* __restrict__ table, i
   }
 }
 
+// Same as table_coeffs, reading rows i and i + 1 (2 J contiguous values) as J
+// float4 loads (J even; rows are 16-byte aligned).
+template <int J>
+__device__ __forceinline__ void table_coeffs_v4(const float2* __restrict__ table, int L, float f, float2 (&c)[J]) {
+  float fl = f * (float)L;
+  int i = (int)fl;
+  if (i > L - 1) i = L - 1;
+  const float t = fl - (float)i;
+  const float4* r = (const float4*)(table + (size_t)i * J);
+  float4 v[J];
+#pragma unroll
+  for (int q = 0; q < J; ++q) v[q] = __ldg(r + q);
+#pragma unroll
+  for (int q = 0; q < J / 2; ++q) {
+    const float4 a = v[q], b = v[q + J / 2];
+    c[2 * q] = make_float2(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y));
+    c[2 * q + 1] = make_float2(fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
+  }
+}
+
 // device check word codes
 enum : int { DEVCHK_TILE_RANGE = -6 };
 

@@ -631,9 +631,10 @@ __global__ void __launch_bounds__(V2_WARPS * 32, 1) k_spread_v2(InterpGeom g, co
         float2 t[6];
 #pragma unroll
         for (int jz = 0; jz < 6; ++jz) t[jz] = tp[jz * PP];
+        const float4 z4[3] = {*(const float4*)(cp + 12), *(const float4*)(cp + 14), *(const float4*)(cp + 16)};
 #pragma unroll
         for (int jz = 0; jz < 6; ++jz) {
-          const float2 cz = cp[12 + jz];
+          const float2 cz = (jz & 1) ? make_float2(z4[jz >> 1].z, z4[jz >> 1].w) : make_float2(z4[jz >> 1].x, z4[jz >> 1].y);
           // t += a conj(cz)
           t[jz].x = fmaf(a.x, cz.x, fmaf(a.y, cz.y, t[jz].x));
           t[jz].y = fmaf(a.y, cz.x, fmaf(-a.x, cz.y, t[jz].y));
@@ -759,9 +760,9 @@ __global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const ty
     const int off = p_off[i];
     if (off < 0) continue;
     float2 cx[J], cy[J], cz[J];
-    table_coeffs<J>(g.table, g.L, p_f[i], cx);
-    table_coeffs<J>(g.table, g.L, p_f[S + i], cy);
-    table_coeffs<J>(g.table, g.L, p_f[2 * S + i], cz);
+    table_coeffs_v4<J>(g.table, g.L, p_f[i], cx);
+    table_coeffs_v4<J>(g.table, g.L, p_f[S + i], cy);
+    table_coeffs_v4<J>(g.table, g.L, p_f[2 * S + i], cz);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int jz = 0; jz < J; ++jz) {
