@@ -37,13 +37,26 @@ __device__ __forceinline__ void rmac(float2& acc, float s, float2 b) {
 // ---------------------------------------------------------------------------
 // grid storage types: complex64, or a pair of bf16 / fp16 with a global scale
 // ---------------------------------------------------------------------------
+// Power-of-two scale for a reduced-precision grid from a bound on |Y|: the
+// scaled grid stays below 2^14 (inside fp16's range, with headroom).
+__device__ __forceinline__ float lp_scale_from_bound(float bound) {
+  const float b = fmaxf(bound, 1e-30f);
+  float e = floorf(__log2f(16384.f / b));
+  e = fminf(fmaxf(e, -100.f), 100.f);
+  return exp2f(e);
+}
+
 struct GridC64 {
   typedef float2 T;
+  static constexpr bool kLowPrecision = false;
+  static __device__ __forceinline__ float2 to_f2(T v) { return v; }
   static __device__ __forceinline__ float2 load(const T* p, size_t i, float) { return p[i]; }
   static __device__ __forceinline__ T pack(float2 v, float) { return v; }
 };
 struct GridBF16 {
   typedef __nv_bfloat162 T;
+  static constexpr bool kLowPrecision = true;
+  static __device__ __forceinline__ float2 to_f2(T v) { return __bfloat1622float2(v); }
   static __device__ __forceinline__ float2 load(const T* p, size_t i, float inv_scale) {
     float2 v = __bfloat1622float2(p[i]);
     return make_float2(v.x * inv_scale, v.y * inv_scale);
@@ -54,6 +67,8 @@ struct GridBF16 {
 };
 struct GridF16 {
   typedef __half2 T;
+  static constexpr bool kLowPrecision = true;
+  static __device__ __forceinline__ float2 to_f2(T v) { return __half22float2(v); }
   static __device__ __forceinline__ float2 load(const T* p, size_t i, float inv_scale) {
     float2 v = __half22float2(p[i]);
     return make_float2(v.x * inv_scale, v.y * inv_scale);

@@ -70,8 +70,9 @@ template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT>
 __global__ void __launch_bounds__(FFT_NT) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
                                                 int N, int n_chunks, long long in_outer, long long in_stride,
                                                 long long out_outer, long long out_stride,
-                                                const float2* __restrict__ tw, float out_scale) {
+                                                const float2* __restrict__ tw, const float* __restrict__ bound) {
   extern __shared__ float2 buf[];
+  const float out_scale = bound ? lp_scale_from_bound(*bound) : 1.f;
   const int ch = blockIdx.x % n_chunks;
   const long long o = blockIdx.x / n_chunks;
   const float2* ib = in + o * in_outer + (long long)ch * FFT_W;
@@ -178,6 +179,40 @@ __global__ void __launch_bounds__(FFT_NT) k_line(const float2* in, float2* out, 
 }
 
 // ----------------------------------------------------------------------------
+// bound on the oversampled grid's magnitude: |Y[k]| <= sum_n |s(n) x[n]|,
+// used to pick the power-of-two scale of a reduced-precision grid
+// ----------------------------------------------------------------------------
+__global__ void k_abs_bound(const void* __restrict__ vol, int cplx, const float* __restrict__ s, int N,
+                            float* __restrict__ bound) {
+  const long long n3 = (long long)N * N * N;
+  float acc = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % N);
+    const int y = (int)((i / N) % N);
+    const int z = (int)(i / ((long long)N * N));
+    const float sc = __ldg(s + x) * __ldg(s + y) * __ldg(s + z);
+    float a;
+    if (cplx) {
+      const float2 v = ((const float2*)vol)[i];
+      a = sqrtf(v.x * v.x + v.y * v.y);
+    } else {
+      a = fabsf(((const float*)vol)[i]);
+    }
+    acc = fmaf(a, sc, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(bound, acc);
+}
+
+cudaError_t launch_abs_bound(const void* vol, int cplx, const float* s, int N, float* bound, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bound, 0, sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  k_abs_bound<<<152 * 4, 256, 0, st>>>(vol, cplx, s, N, bound);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
 // host launchers
 // ----------------------------------------------------------------------------
 static size_t fft_smem(int L) { return (size_t)L * FFT_PITCH * sizeof(float2); }
@@ -245,7 +280,7 @@ cudaError_t launch_row_adj(int K, const float2* in, void* vol, int cplx, const f
 template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT>
 static cudaError_t launch_col_t(const float2* in, OutT* out, int N, int n_outer, int row_len,
                                 long long in_outer, long long in_stride, long long out_outer,
-                                long long out_stride, const float2* tw, float out_scale, cudaStream_t st) {
+                                long long out_stride, const float2* tw, const float* out_scale, cudaStream_t st) {
   auto f = k_col<L, INV, PAD_IN, CROP_OUT, OutT>;
   cudaError_t e = set_smem(f, fft_smem(L));
   if (e != cudaSuccess) return e;
@@ -260,7 +295,7 @@ cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_ou
                            long long in_outer, long long in_stride, long long out_outer, long long out_stride,
                            const float2* tw, cudaStream_t st) {
   switch (L) {
-#define CASE_L(V) case V: return launch_col_t<V, false, true, false, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, 1.f, st);
+#define CASE_L(V) case V: return launch_col_t<V, false, true, false, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, nullptr, st);
     NUFFT_FFT_SIZES(CASE_L)
 #undef CASE_L
   }
@@ -269,7 +304,7 @@ cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_ou
 
 cudaError_t launch_col_fwd_lp(int L, int dtype, const float2* in, void* out, int N, int n_outer, int row_len,
                               long long in_outer, long long in_stride, long long out_outer,
-                              long long out_stride, const float2* tw, float scale, cudaStream_t st) {
+                              long long out_stride, const float2* tw, const float* scale, cudaStream_t st) {
   if (dtype == 1) {
     switch (L) {
 #define CASE_L(V) case V: return launch_col_t<V, false, true, false, __nv_bfloat162>(in, (__nv_bfloat162*)out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, scale, st);
@@ -290,7 +325,7 @@ cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_ou
                            long long in_outer, long long in_stride, long long out_outer, long long out_stride,
                            const float2* tw, cudaStream_t st) {
   switch (L) {
-#define CASE_L(V) case V: return launch_col_t<V, true, false, true, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, 1.f, st);
+#define CASE_L(V) case V: return launch_col_t<V, true, false, true, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, nullptr, st);
     NUFFT_FFT_SIZES(CASE_L)
 #undef CASE_L
   }

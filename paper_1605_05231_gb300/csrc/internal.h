@@ -21,6 +21,7 @@ struct InterpGeom {
   int* err;              // device check word
   int* counter;          // two work counters (gather, spread) for the persistent variants
   int S;                 // most points in one subproblem
+  const float* lp_bound; // bound on |Y| for a reduced-precision grid (else null)
 };
 
 bool fft_length_supported(int L);
@@ -33,7 +34,8 @@ cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_ou
                            const float2* tw, cudaStream_t st);
 cudaError_t launch_col_fwd_lp(int L, int dtype, const float2* in, void* out, int N, int n_outer, int row_len,
                               long long in_outer, long long in_stride, long long out_outer,
-                              long long out_stride, const float2* tw, float scale, cudaStream_t st);
+                              long long out_stride, const float2* tw, const float* bound, cudaStream_t st);
+cudaError_t launch_abs_bound(const void* vol, int cplx, const float* s, int N, float* bound, cudaStream_t st);
 cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
                            long long in_outer, long long in_stride, long long out_outer, long long out_stride,
                            const float2* tw, cudaStream_t st);
@@ -62,7 +64,7 @@ struct nufft3d_plan_s {
   int complex_volume, do_line_fft, grid_dtype;
   int T, nT;  // tile edge and tiles per axis
   int gather_variant, spread_variant, pts_per_sub;
-  float lp_scale;  // power-of-two scale of the reduced-precision grid
+  float* d_lp_bound = nullptr;  // device bound on |Y| (reduced-precision grid)
   int device;
   // device arrays (owned)
   float2* d_dir = nullptr;

@@ -60,6 +60,12 @@ cudaError_t launch_bin_points(const InterpGeom& g, uint32_t* bins, cudaStream_t 
   return cudaErrorInvalidValue;
 }
 
+template <typename G>
+__device__ __forceinline__ float lp_inv_scale(const InterpGeom& g) {
+  if constexpr (G::kLowPrecision) return 1.f / lp_scale_from_bound(*g.lp_bound);
+  return 1.f;
+}
+
 // ---------------------------------------------------------------------------
 // staging of a padded tile, plain [iz][iy][ix] layout (pitch E)
 // ---------------------------------------------------------------------------
@@ -86,6 +92,7 @@ template <int J, typename G>
 __global__ void __launch_bounds__(256) k_gather_v0(InterpGeom g, const typename G::T* __restrict__ grid,
                                                    float inv_scale, const int4* __restrict__ subs,
                                                    float2* __restrict__ out) {
+  inv_scale = lp_inv_scale<G>(g);
   extern __shared__ float2 tile[];
   const int4 sp = subs[blockIdx.x];
   const int T = g.T, nT = g.nT, E = T + J - 1;
@@ -271,6 +278,7 @@ template <typename G>
 __global__ void __launch_bounds__(V1_THREADS, 1) k_gather_v1(InterpGeom g, const typename G::T* __restrict__ grid,
                                                              float inv_scale, const int4* __restrict__ subs,
                                                              int n_subs, float2* __restrict__ out) {
+  inv_scale = lp_inv_scale<G>(g);
   extern __shared__ __align__(16) float2 smem[];
   const V1Layout lay = v1_layout(g.T, g.L);
   float2* table = smem;
@@ -508,6 +516,7 @@ __global__ void __launch_bounds__(V2_WARPS * 32, 1) k_gather_v2(InterpGeom g, co
                                                                 float inv_scale, const int4* __restrict__ subs,
                                                                 int n_subs, int* __restrict__ counter,
                                                                 float2* __restrict__ out) {
+  inv_scale = lp_inv_scale<G>(g);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const V2Layout lay = v2_layout(g.T, g.L);
   float2* table = (float2*)smem_raw;
@@ -690,12 +699,13 @@ struct V3Layout {
   size_t tile_bytes, bytes;
 };
 
-__host__ __device__ inline V3Layout v3_layout(int T, int J, int S) {
+// elem: bytes per grid cell in shared memory (8 for complex64, 4 for bf16/fp16 pairs)
+__host__ __device__ inline V3Layout v3_layout(int T, int J, int S, int elem) {
   V3Layout l;
   l.E = T + J - 1;
-  l.tile_bytes = ((size_t)l.E * l.E * l.E * sizeof(float2) + 15) / 16 * 16;
-  // per point: id, tile offset, f[3] (5 words) + ordered index (1 word); class counts
-  l.bytes = l.tile_bytes + (size_t)S * 6 * sizeof(int) + 32 * sizeof(int);
+  l.tile_bytes = ((size_t)l.E * l.E * l.E * elem + 15) / 16 * 16;
+  // per point: id, tile offset, f[3] (5 words) + ordered index (1 word); class counts and cursors
+  l.bytes = l.tile_bytes + (size_t)S * 6 * sizeof(int) + 64 * sizeof(int);
   return l;
 }
 
@@ -703,22 +713,39 @@ template <int J, typename G>
 __global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const typename G::T* __restrict__ grid,
                                                           float inv_scale, const int4* __restrict__ subs, int S,
                                                           float2* __restrict__ out) {
+  typedef typename G::T TT;
+  // a warp access of 4-byte cells is conflict-free with 32 distinct residues,
+  // of 8-byte cells with 16 distinct residues per half-warp
+  constexpr int kRes = sizeof(TT) == 4 ? 32 : 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  inv_scale = lp_inv_scale<G>(g);
   const int T = g.T, nT = g.nT, K = g.K;
-  const V3Layout lay = v3_layout(T, J, S);
+  const V3Layout lay = v3_layout(T, J, S, (int)sizeof(TT));
   const int E = lay.E, PP = E * E;
-  float2* tile = (float2*)smem_raw;
+  TT* tile = (TT*)smem_raw;
   int* p_id = (int*)(smem_raw + lay.tile_bytes);
   int* p_off = p_id + S;
   float* p_f = (float*)(p_off + S);  // [3][S]
   int* order = (int*)(p_f + 3 * S);
-  int* ncls = order + S;             // [16] counts, [16] cursors
+  int* ncls = order + S;             // [kRes] counts, [kRes] cursors
   const int4 sp = subs[blockIdx.x];
   const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
   const int x0 = bx * T, y0 = by * T, z0 = bz * T;
   const int cnt = sp.z;
-  if (threadIdx.x < 32) ncls[threadIdx.x] = 0;
-  stage_tile_plain<G>(grid, inv_scale, K, E, x0, y0, z0, tile);
+  if (threadIdx.x < 2 * kRes) ncls[threadIdx.x] = 0;
+  {
+    const int n = E * E * E;
+    for (int idx = threadIdx.x; idx < n; idx += V3_THREADS) {
+      const int ix = idx % E;
+      const int t = idx / E;
+      const int iy = t % E, iz = t / E;
+      int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      gz -= gz >= K ? K : 0;
+      tile[idx] = grid[((size_t)gz * K + gy) * K + gx];
+    }
+  }
   __syncthreads();
   // decode every point of the subproblem once
   for (int i = threadIdx.x; i < cnt; i += V3_THREADS) {
@@ -738,16 +765,16 @@ __global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const ty
     p_f[i] = f[0];
     p_f[S + i] = f[1];
     p_f[2 * S + i] = f[2];
-    atomicAdd(&ncls[off < 0 ? 0 : (off & 15)], 1);
+    atomicAdd(&ncls[off < 0 ? 0 : (off & (kRes - 1))], 1);
   }
   __syncthreads();
   // rank within the class, then the round-robin position
   for (int i = threadIdx.x; i < cnt; i += V3_THREADS) {
-    const int c = p_off[i] < 0 ? 0 : (p_off[i] & 15);
-    const int r = atomicAdd(&ncls[16 + c], 1);
+    const int c = p_off[i] < 0 ? 0 : (p_off[i] & (kRes - 1));
+    const int r = atomicAdd(&ncls[kRes + c], 1);
     int pos = 0;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < kRes; ++q) {
       const int n = ncls[q];
       pos += n < r ? n : r;
       pos += (q < c && n > r) ? 1 : 0;
@@ -769,15 +796,15 @@ __global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const ty
       float2 zacc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int jy = 0; jy < J; ++jy) {
-        const float2* tp = tile + off + jz * PP + jy * E;
+        const TT* tp = tile + off + jz * PP + jy * E;
         float2 row = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int jx = 0; jx < J; ++jx) cmac(row, cx[jx], tp[jx]);
+        for (int jx = 0; jx < J; ++jx) cmac(row, cx[jx], G::to_f2(tp[jx]));
         cmac(zacc, cy[jy], row);
       }
       cmac(acc, cz[jz], zacc);
     }
-    out[p_id[i]] = acc;
+    out[p_id[i]] = cscale(acc, inv_scale);
   }
 }
 
@@ -785,7 +812,7 @@ template <int J, typename G>
 static cudaError_t launch_gather_v3_t(const InterpGeom& g, const void* grid, float inv_scale, const int4* subs,
                                       int n_subs, int S, float2* out, cudaStream_t st) {
   auto f = k_gather_v3<J, G>;
-  const size_t smem = v3_layout(g.T, J, S).bytes;
+  const size_t smem = v3_layout(g.T, J, S, (int)sizeof(typename G::T)).bytes;
   cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (n_subs == 0) return cudaSuccess;
@@ -823,7 +850,7 @@ static int max_optin_smem() {
 }
 
 bool v3_supported(int T, int J, int S) {
-  return v3_layout(T, J, S).bytes <= (size_t)max_optin_smem();
+  return v3_layout(T, J, S, 8).bytes <= (size_t)max_optin_smem();
 }
 
 bool v2_supported(int T, int J, int L) {

@@ -229,7 +229,7 @@ void free_plan(nufft3d_plan pl) {
   if (!pl) return;
   void* ptrs[] = {pl->d_dir, pl->d_rad, pl->d_weight, pl->d_s, pl->d_table, pl->d_twK, pl->d_twM,
                   pl->d_sorted, pl->d_sub, pl->d_grid, pl->d_grid_lp, pl->d_bufA, pl->d_bufB,
-                  pl->d_lines, pl->d_err, pl->d_counter};
+                  pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : pl->ev_fwd) cudaEventDestroy(e);
@@ -253,6 +253,7 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.err = pl->d_err;
   g.counter = pl->d_counter;
   g.S = pl->pts_per_sub;
+  g.lp_bound = pl->d_lp_bound;
   return g;
 }
 
@@ -344,7 +345,6 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->nT = r.nT;
   pl->spread_variant = nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0;
   pl->gather_variant = nufft::v3_supported(r.T, r.J, 1024) ? 3 : 0;
-  pl->lp_scale = 1.f;
   CK(cudaGetDevice(&pl->device));
   CK(upload(&pl->d_s, h.s, st));
   CK(upload(&pl->d_table, h.table, st));
@@ -363,7 +363,10 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   if (rc != NUFFT3D_OK) return rc;
   const size_t K3 = (size_t)r.K * r.K * r.K;
   CK(dalloc(&pl->d_grid, K3));
-  if (r.grid_dtype != NUFFT3D_GRID_C64) CK(cudaMalloc(&pl->d_grid_lp, K3 * 4));
+  if (r.grid_dtype != NUFFT3D_GRID_C64) {
+    CK(cudaMalloc(&pl->d_grid_lp, K3 * 4));
+    CK(dalloc(&pl->d_lp_bound, 1));
+  }
   CK(dalloc(&pl->d_bufA, (size_t)r.N * r.N * r.K));
   CK(dalloc(&pl->d_bufB, (size_t)r.N * r.K * r.K));
   if (r.line_fft) CK(dalloc(&pl->d_lines, (size_t)r.P));
@@ -394,6 +397,8 @@ int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st)
   const long long KK = (long long)K * K;
   StageClock clk(pl->ev_fwd, pl->timing_slots, pl->fwd_calls, FWD_STAGES, st);
   CK(clk.mark(-1));
+  if (pl->grid_dtype != NUFFT3D_GRID_C64)
+    CK(nufft::launch_abs_bound(vol, pl->complex_volume, pl->d_s, N, pl->d_lp_bound, st));
   CK(nufft::launch_row_fwd(K, vol, pl->complex_volume, pl->d_bufA, pl->d_s, N, pl->d_twK, st));
   CK(clk.mark(0));
   CK(nufft::launch_col_fwd(K, pl->d_bufA, pl->d_bufB, N, N, K, (long long)N * K, K, KK, K, pl->d_twK, st));
@@ -404,9 +409,8 @@ int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st)
     CK(nufft::launch_col_fwd(K, pl->d_bufB, pl->d_grid, N, K, K, K, KK, K, KK, pl->d_twK, st));
   } else {
     CK(nufft::launch_col_fwd_lp(K, pl->grid_dtype, pl->d_bufB, pl->d_grid_lp, N, K, K, K, KK, K, KK, pl->d_twK,
-                                pl->lp_scale, st));
+                                pl->d_lp_bound, st));
     grid = pl->d_grid_lp;
-    inv_scale = 1.f / pl->lp_scale;
   }
   CK(clk.mark(2));
   InterpGeom g = geom(pl);
@@ -495,7 +499,7 @@ int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes) {
   const size_t K3 = (size_t)r.K * r.K * r.K;
   size_t b = 0;
   b += K3 * sizeof(float2);
-  if (r.grid_dtype != NUFFT3D_GRID_C64) b += K3 * 4;
+  if (r.grid_dtype != NUFFT3D_GRID_C64) b += K3 * 4 + sizeof(float);
   b += (size_t)r.N * r.N * r.K * sizeof(float2);
   b += (size_t)r.N * r.K * r.K * sizeof(float2);
   if (r.line_fft) b += (size_t)r.P * sizeof(float2);

@@ -1,0 +1,99 @@
+"""Parity at the full 256^3 size, in the launch configuration bench.py times
+(default kernel variants and tiling): K = 512, J = 6, L = 1024, 360 x 256
+umbrella lines of 512 samples (47,185,920 points), ellipsoid phantom plus
+N(0, 0.01^2) noise.
+
+The forward projection is compared with the FP64 oracle on a random sample of
+lines (the oracle computes the full K^3 FFT and then only those lines); the
+adjoint, whose single outputs each depend on every point, is pinned at full
+size by the dot-product identity <A x, y> = <x, A^H y> with the forward just
+checked.  The reduced-precision grid modes (bf16, fp16 storage of the
+oversampled grid, FP32 arithmetic) are measured on the same sample.
+"""
+import numpy as np
+import pytest
+
+from oracle import nufft3d_oracle as O
+from paper_1605_05231_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+# reduced-precision storage: relative rounding 2^-9 (bf16) and 2^-12 (fp16)
+# per grid value; the interpolated samples inherit about that relative error
+LP_BOUND = {"bf16": 4e-3, "fp16": 5e-4}
+
+
+@pytest.fixture(scope="module")
+def problem():
+    w = I.workload("full256")
+    dirs = w.directions()
+    x = w.volume(np.float32)
+    lines = np.sort(np.random.default_rng(7).choice(dirs.shape[0], 64, replace=False))
+    op = O.OraclePlan(w.n, w.k, w.j, w.table_oversamp, dirs, w.m)
+    ref = O.nufft_forward(x.astype(np.float64), op, lines=lines)
+    return w, dirs, x, lines, ref
+
+
+def test_full_size_forward_sampled_lines(cuda_lib, problem):
+    import torch
+
+    w, dirs, x, lines, ref = problem
+    plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp)
+    p = plan.forward(torch.from_numpy(x).cuda())
+    assert plan.sync_status() == 0
+    err = O.rel_l2(p.cpu().numpy()[lines], ref)
+    print(f"full-size forward rel-L2 vs FP64 oracle (64 lines): {err:.3e}")
+    assert err < TOL
+    plan.close()
+
+
+def test_full_size_adjoint_dot_product(cuda_lib, problem):
+    import torch
+
+    w, dirs, x, lines, ref = problem
+    plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp)
+    xr = torch.from_numpy(I.random_volume(w.n, 31).astype(np.float32)).cuda()
+    y = torch.from_numpy(I.random_lines(dirs.shape[0], w.m, 32).astype(np.complex64)).cuda()
+    Ax = plan.forward(xr).to(torch.complex128)
+    Ahy = plan.adjoint(y).to(torch.float64)
+    lhs = torch.sum(torch.conj(y.to(torch.complex128)) * Ax).real
+    rhs = torch.sum(Ahy * xr.to(torch.float64))
+    rel = abs(float(lhs - rhs)) / float(torch.linalg.norm(Ax) * torch.linalg.norm(y.to(torch.complex128)))
+    print(f"full-size adjoint dot-product relative mismatch: {rel:.3e}")
+    assert rel < 1e-6
+    assert plan.sync_status() == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp16"])
+def test_full_size_reduced_precision_grid(cuda_lib, problem, dtype):
+    import torch
+
+    w, dirs, x, lines, ref = problem
+    plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp, grid_dtype=dtype)
+    p = plan.forward(torch.from_numpy(x).cuda())
+    assert plan.sync_status() == 0
+    err = O.rel_l2(p.cpu().numpy()[lines], ref)
+    print(f"full-size forward with {dtype} grid: rel-L2 vs FP64 oracle {err:.3e}")
+    assert err < LP_BOUND[dtype]
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp16"])
+@pytest.mark.parametrize("gv", [0, 2, 3])
+def test_reduced_precision_small_all_variants(cuda_lib, dtype, gv):
+    """Every gather variant reads the reduced-precision grid with the same scale;
+    the adjoint keeps FP32 accumulation and stays at the FP32 bar."""
+    import torch
+
+    w = I.workload("tiny32")
+    dirs = w.directions()
+    x = w.volume(np.float32)
+    y = I.random_lines(dirs.shape[0], w.m, 3).astype(np.complex64)
+    plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, grid_dtype=dtype)
+    plan.tune(gv)
+    p = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    a = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    op = O.OraclePlan(w.n, w.k, w.j, w.table_oversamp, dirs, w.m)
+    assert O.rel_l2(p, O.nufft_forward(x.astype(np.float64), op)) < LP_BOUND[dtype]
+    assert O.rel_l2(a, O.nufft_adjoint(y.astype(np.complex128), op)) < TOL

@@ -56,7 +56,7 @@ def test_workspace_bytes_counts_grid_and_buffers(lib):
     K, N, D, M = 64, 32, 3, 64
     expect = K ** 3 * 8 + N * N * K * 8 + N * K * K * 8 + D * M * 8 + D * M * 4
     assert expect <= b < expect + 200_000
-    assert _ws(grid_dtype="bf16") == b + K ** 3 * 4
+    assert _ws(grid_dtype="bf16") == b + K ** 3 * 4 + 4
     assert _ws(do_line_fft=False) == b - D * M * 8
 
 
