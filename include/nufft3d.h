@@ -174,6 +174,29 @@ int nufft3d_adjoint_noalloc(nufft3d_plan plan, const void* lines_dev, void* vol_
 int nufft3d_plan_set_timing(nufft3d_plan plan, int max_calls);
 int nufft3d_plan_stage_times(nufft3d_plan plan, float* fwd_ms, float* adj_ms, int* calls);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent problems of mixed sizes and view counts (the
+ * batched use of one projector over several volumes; the paper runs one
+ * problem at a time).  A batch owns one plan per item (created from ps[i] as
+ * by nufft3d_plan_create).  nufft3d_batch_forward_adjoint runs, for every
+ * item i, vols[i] -> lines[i] (forward) then lines[i] -> vols_out[i]
+ * (adjoint), all device buffers laid out as for a single plan.  The first
+ * call captures the whole sequence into one CUDA graph (items dealt to up to
+ * 8 worker streams forked from cuda_stream) and every call replays it with a
+ * single graph launch on cuda_stream; passing different buffers, or calling
+ * nufft3d_batch_invalidate (after re-tuning an item plan), captures again.
+ * Item plans are reachable with nufft3d_batch_item for tuning; they must not
+ * be destroyed by the caller.
+ * ------------------------------------------------------------------------- */
+typedef struct nufft3d_batch_s* nufft3d_batch;   /* opaque, library-owned */
+int nufft3d_batch_create(nufft3d_batch* out, const nufft3d_params* ps, int count, void* cuda_stream);
+int nufft3d_batch_size(nufft3d_batch batch, int* count);
+int nufft3d_batch_item(nufft3d_batch batch, int i, nufft3d_plan* plan);
+int nufft3d_batch_forward_adjoint(nufft3d_batch batch, const void* const* vols, void* const* lines,
+                                  void* const* vols_out, void* cuda_stream);
+int nufft3d_batch_invalidate(nufft3d_batch batch);
+int nufft3d_batch_destroy(nufft3d_batch batch);
+
 #ifdef __cplusplus
 }
 #endif

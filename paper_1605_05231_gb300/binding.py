@@ -29,6 +29,12 @@ EXPORTS = (
     "nufft3d_plan_set_timing",
     "nufft3d_plan_stage_times",
     "nufft3d_adjoint_noalloc",
+    "nufft3d_batch_create",
+    "nufft3d_batch_size",
+    "nufft3d_batch_item",
+    "nufft3d_batch_forward_adjoint",
+    "nufft3d_batch_invalidate",
+    "nufft3d_batch_destroy",
 )
 
 FWD_STAGES = ("x_pass", "y_pass", "z_pass", "gather", "line_dft")
@@ -81,6 +87,12 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.nufft3d_forward.argtypes = [vp, vp, vp, vp]
     lib.nufft3d_adjoint.argtypes = [vp, vp, vp, vp]
     lib.nufft3d_adjoint_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.nufft3d_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), i, vp]
+    lib.nufft3d_batch_size.argtypes = [vp, ip]
+    lib.nufft3d_batch_item.argtypes = [vp, i, ctypes.POINTER(vp)]
+    lib.nufft3d_batch_forward_adjoint.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.nufft3d_batch_invalidate.argtypes = [vp]
+    lib.nufft3d_batch_destroy.argtypes = [vp]
     lib.nufft3d_workspace_bytes.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
     lib.nufft3d_plan_sync_status.argtypes = [vp, ip]
     lib.nufft3d_plan_destroy.argtypes = [vp]
@@ -162,10 +174,12 @@ class Plan:
     """
 
     def __init__(self, n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=None,
-                 grid_dtype="c64", complex_volume=False, do_line_fft=True, device=None, stream=None):
+                 grid_dtype="c64", complex_volume=False, do_line_fft=True, device=None, stream=None,
+                 _handle=None):
         import torch
 
         self.lib = load_library()
+        self._owned = _handle is None
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         p, keep = make_params(n, dirs, m, k, j, table_oversamp, omega, weight, grid_dtype, complex_volume,
@@ -177,10 +191,14 @@ class Plan:
         self.j = int(j)
         self.complex_volume = bool(complex_volume)
         self.do_line_fft = bool(do_line_fft)
+        self.grid_dtype = str(grid_dtype)
         self._handle = ctypes.c_void_p()
-        with torch.cuda.device(self.device):
-            _check(self.lib.nufft3d_plan_create(ctypes.byref(self._handle), ctypes.byref(p),
-                                                _stream_ptr(stream, self.device)), "nufft3d_plan_create")
+        if _handle is not None:
+            self._handle = _handle
+        else:
+            with torch.cuda.device(self.device):
+                _check(self.lib.nufft3d_plan_create(ctypes.byref(self._handle), ctypes.byref(p),
+                                                    _stream_ptr(stream, self.device)), "nufft3d_plan_create")
         del keep
 
     # -- shapes ------------------------------------------------------------
@@ -266,7 +284,8 @@ class Plan:
 
     def close(self):
         if getattr(self, "_handle", None) is not None and self._handle.value:
-            self.lib.nufft3d_plan_destroy(self._handle)
+            if getattr(self, "_owned", True):
+                self.lib.nufft3d_plan_destroy(self._handle)
             self._handle = ctypes.c_void_p()
 
     def __del__(self):
@@ -305,3 +324,65 @@ def project(x, plan: Plan):
     if _PROJECT is None:
         _PROJECT = _autograd_function()
     return _PROJECT.apply(x, plan)
+
+
+class Batch:
+    """Many independent problems of mixed sizes: one plan per item, forward +
+    adjoint of every item replayed as one CUDA graph launch.
+
+    items: list of dicts with the Plan keyword arguments (n, dirs, m, k, j,
+    table_oversamp, grid_dtype, complex_volume, ...).
+    """
+
+    def __init__(self, items, stream=None, device=None):
+        import torch
+
+        self.lib = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        built = [make_params(**it) for it in items]
+        arr = (Params * len(items))(*[b[0] for b in built])
+        self._handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.nufft3d_batch_create(ctypes.byref(self._handle), arr, len(items),
+                                                 _stream_ptr(stream, self.device)), "nufft3d_batch_create")
+        self.items = []
+        for idx, it in enumerate(items):
+            h = ctypes.c_void_p()
+            _check(self.lib.nufft3d_batch_item(self._handle, idx, ctypes.byref(h)), "nufft3d_batch_item")
+            kw = dict(it)
+            self.items.append(Plan(device=self.device, _handle=h, **kw))
+        del built
+
+    def __len__(self):
+        return len(self.items)
+
+    def invalidate(self):
+        """Capture the graph again on the next call (after re-tuning item plans)."""
+        _check(self.lib.nufft3d_batch_invalidate(self._handle), "nufft3d_batch_invalidate")
+
+    def forward_adjoint(self, vols, lines, vols_out, stream=None):
+        n = len(self.items)
+        if not (len(vols) == len(lines) == len(vols_out) == n):
+            raise ValueError("one volume, line buffer and output volume per item")
+        for it, v, l, o in zip(self.items, vols, lines, vols_out):
+            it._check_tensor(v, (it.n,) * 3, it.vol_dtype, "vol")
+            it._check_tensor(l, (it.n_dirs, it.m), __import__("torch").complex64, "lines")
+            it._check_tensor(o, (it.n,) * 3, it.vol_dtype, "vol_out")
+        P = ctypes.c_void_p * n
+        _check(self.lib.nufft3d_batch_forward_adjoint(
+            self._handle, P(*[v.data_ptr() for v in vols]), P(*[l.data_ptr() for l in lines]),
+            P(*[o.data_ptr() for o in vols_out]), _stream_ptr(stream, self.device)), "nufft3d_batch_forward_adjoint")
+
+    def close(self):
+        if getattr(self, "_handle", None) is not None and self._handle.value:
+            for it in self.items:
+                it._handle = ctypes.c_void_p()
+            self.lib.nufft3d_batch_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

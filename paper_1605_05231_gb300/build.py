@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnufft3d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cu", "fft_passes.cu", "interp.cu", "noalloc.cu"]
+SOURCES = ["plan.cu", "fft_passes.cu", "interp.cu", "noalloc.cu", "batch.cu"]
 
 
 def nvcc_path() -> str:

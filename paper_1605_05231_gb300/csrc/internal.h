@@ -50,6 +50,9 @@ cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, co
                           float2* grid, cudaStream_t st);
 size_t interp_smem_bytes(int T, int J);
 bool v2_supported(int T, int J, int L);
+// enqueue a plan's forward / adjoint on a stream (no argument checks; used by batches)
+int plan_forward_enqueue(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st);
+int plan_adjoint_enqueue(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st);
 bool v3_supported(int T, int J, int S);
 
 }  // namespace nufft

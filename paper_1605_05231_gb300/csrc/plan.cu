@@ -450,6 +450,17 @@ int adjoint_impl(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st)
 
 }  // namespace
 
+namespace nufft {
+int plan_forward_enqueue(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st) {
+  pl->last_stream = st;
+  return forward_impl(pl, vol, lines, st);
+}
+int plan_adjoint_enqueue(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st) {
+  pl->last_stream = st;
+  return adjoint_impl(pl, lines, vol, st);
+}
+}  // namespace nufft
+
 extern "C" {
 
 int nufft3d_plan_create(nufft3d_plan* out, const nufft3d_params* p, void* cuda_stream) {

@@ -1,0 +1,106 @@
+"""Batched path: 24 problems of mixed sizes (8 each at 64^3, 128^3 and 192^3,
+K = 2N, M = 2N, azimuth counts from {90, 180, 360} and polar counts from
+{64, 128}) run as one CUDA-graph replay, tiles chosen by the autotuner.
+
+Per item the graph result equals the plan's direct forward/adjoint (same
+kernels), the forward matches the FP64 oracle on sampled lines for one item of
+each size, and the adjoint passes the dot-product identity for every item.
+"""
+import numpy as np
+import pytest
+
+from oracle import nufft3d_oracle as O
+from paper_1605_05231_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _items(works):
+    return [dict(n=w.n, dirs=w.directions(), m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp) for w in works]
+
+
+def _rel(a, b):
+    import torch
+
+    return float(torch.linalg.norm((a - b).to(torch.complex128)) / torch.linalg.norm(b.to(torch.complex128)))
+
+
+@pytest.fixture(scope="module")
+def batch_run(cuda_lib, tmp_path_factory):
+    import torch
+
+    from paper_1605_05231_gb300 import autotune
+
+    works = I.batched_workloads()
+    assert len(works) == 24 and sorted({w.n for w in works}) == [64, 128, 192]
+    b = cuda_lib.Batch(_items(works))
+    cache = str(tmp_path_factory.mktemp("tune") / "tune.json")
+    chosen = autotune.tune_batch(b, candidates=((3, 2, 512, 8), (3, 2, 1024, 8), (2, 2, 1024, 8)),
+                                 reps=1, cache=cache)
+    assert len(chosen) == len({autotune.signature(p) for p in b.items})
+    vols = [torch.from_numpy(w.volume(np.float32)).cuda() for w in works]
+    lines = [torch.empty((p.n_dirs, p.m), dtype=torch.complex64, device="cuda") for p in b.items]
+    outs = [torch.empty_like(v) for v in vols]
+    b.forward_adjoint(vols, lines, outs)
+    first = [o.clone() for o in outs]
+    b.forward_adjoint(vols, lines, outs)  # graph replay
+    torch.cuda.synchronize()
+    yield b, works, vols, lines, outs, first
+    b.close()
+
+
+def test_batch_replay_matches_direct_path(cuda_lib, batch_run):
+    import torch
+
+    b, works, vols, lines, outs, first = batch_run
+    for p, v, l, o, f in zip(b.items, vols, lines, outs, first):
+        assert p.sync_status() == 0
+        ref_l = p.forward(v)
+        ref_o = p.adjoint(ref_l)
+        assert _rel(l, ref_l) < 1e-6
+        assert _rel(o, ref_o) < 1e-6
+        assert _rel(f, ref_o) < 1e-6
+
+
+def test_batch_items_forward_match_oracle(cuda_lib, batch_run):
+    b, works, vols, lines, outs, first = batch_run
+    for n in (64, 128, 192):
+        i = next(k for k, w in enumerate(works) if w.n == n)
+        w = works[i]
+        dirs = w.directions()
+        sel = np.sort(np.random.default_rng(n).choice(dirs.shape[0], 24, replace=False))
+        op = O.OraclePlan(w.n, w.k, w.j, w.table_oversamp, dirs, w.m)
+        ref = O.nufft_forward(vols[i].cpu().numpy().astype(np.float64), op, lines=sel)
+        assert O.rel_l2(lines[i].cpu().numpy()[sel], ref) < TOL, n
+
+
+def test_batch_items_adjoint_dot_product(cuda_lib, batch_run):
+    import torch
+
+    b, works, vols, lines, outs, first = batch_run
+    for i, p in enumerate(b.items):
+        y = torch.from_numpy(I.random_lines(p.n_dirs, p.m, 100 + i).astype(np.complex64)).cuda()
+        Ax = lines[i].to(torch.complex128)
+        Ahy = p.adjoint(y).to(torch.float64)
+        lhs = torch.sum(torch.conj(y.to(torch.complex128)) * Ax).real
+        rhs = torch.sum(Ahy * vols[i].to(torch.float64))
+        rel = abs(float(lhs - rhs)) / float(torch.linalg.norm(Ax) * torch.linalg.norm(y.to(torch.complex128)))
+        assert rel < 1e-6, (i, rel)
+
+
+def test_batch_recaptures_on_new_buffers(cuda_lib):
+    import torch
+
+    works = I.batched_workloads()[:3]
+    b = cuda_lib.Batch(_items(works))
+    vols = [torch.from_numpy(w.volume(np.float32)).cuda() for w in works]
+    lines = [torch.empty((p.n_dirs, p.m), dtype=torch.complex64, device="cuda") for p in b.items]
+    outs = [torch.empty_like(v) for v in vols]
+    b.forward_adjoint(vols, lines, outs)
+    outs2 = [torch.empty_like(v) for v in vols]
+    b.forward_adjoint(vols, lines, outs2)
+    torch.cuda.synchronize()
+    for o, o2 in zip(outs, outs2):
+        assert _rel(o2, o) < 1e-6
+    b.close()

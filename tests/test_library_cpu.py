@@ -94,3 +94,10 @@ def test_null_arguments_rejected(lib):
     assert out.value is None
     assert lib.nufft3d_plan_info(None, None) == -1
     assert lib.nufft3d_plan_sync_status(None, None) == -1
+    assert lib.nufft3d_adjoint_noalloc(None, None, None, None) == -1
+    bout = ctypes.c_void_p(1)
+    assert lib.nufft3d_batch_create(ctypes.byref(bout), None, 0, None) == -1
+    assert bout.value is None
+    assert lib.nufft3d_batch_forward_adjoint(None, None, None, None, None) == -1
+    assert lib.nufft3d_batch_item(None, 0, None) == -1
+    assert lib.nufft3d_batch_destroy(None) == 0
