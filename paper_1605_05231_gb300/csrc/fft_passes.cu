@@ -13,6 +13,9 @@ namespace nufft {
 constexpr int FFT_W = 16;    // columns (rows) per CTA: 16 complex64 = 128 B segments
 constexpr int FFT_NT = 256;  // threads per CTA
 constexpr int FFT_PITCH = FFT_W + 1;
+// shared memory bounds residency to 3 CTAs per SM at L = 512; ask for the
+// register budget that allows the same (65536 / (3 * 256) = 85 per thread)
+constexpr int FFT_MIN_CTAS = 3;
 
 __device__ __forceinline__ int centred_to_grid(int i, int half, int L) {
   int k = i - half;
@@ -24,13 +27,14 @@ __device__ __forceinline__ int centred_to_grid(int i, int half, int L) {
 // out[(z N + y) K + kx]
 // ----------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(FFT_NT) k_row_fwd(const void* __restrict__ vol, int cplx,
+__global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_fwd(const void* __restrict__ vol, int cplx,
                                                     float2* __restrict__ out, const float* __restrict__ s,
                                                     int N, const float2* __restrict__ tw) {
   extern __shared__ float2 buf[];
   const int nrows = N * N;
   const int row0 = blockIdx.x * FFT_W;
   const int half = N / 2;
+#pragma unroll 8
   for (int idx = threadIdx.x; idx < FFT_W * N; idx += FFT_NT) {
     const int c = idx / N, x = idx - c * N;
     const int r = row0 + c;
@@ -67,7 +71,7 @@ __global__ void __launch_bounds__(FFT_NT) k_row_fwd(const void* __restrict__ vol
 // element (i, c) of the input at in[o in_outer + i in_stride + ch W + c]
 // ----------------------------------------------------------------------------
 template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT>
-__global__ void __launch_bounds__(FFT_NT) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
+__global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
                                                 int N, int n_chunks, long long in_outer, long long in_stride,
                                                 long long out_outer, long long out_stride,
                                                 const float2* __restrict__ tw, const float* __restrict__ bound) {
@@ -79,6 +83,7 @@ __global__ void __launch_bounds__(FFT_NT) k_col(const float2* __restrict__ in, O
   OutT* ob = out + o * out_outer + (long long)ch * FFT_W;
   const int half = N / 2;
   const int in_len = PAD_IN ? N : L;
+#pragma unroll 8
   for (int idx = threadIdx.x; idx < FFT_W * in_len; idx += FFT_NT) {
     const int c = idx % FFT_W, i = idx / FFT_W;
     const int k = PAD_IN ? centred_to_grid(i, half, L) : i;
@@ -114,13 +119,14 @@ __global__ void __launch_bounds__(FFT_NT) k_col(const float2* __restrict__ in, O
 // inverse x pass: rows of K -> inverse FFT -> crop to N, deapodise, real part
 // ----------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(FFT_NT) k_row_adj(const float2* __restrict__ in, void* __restrict__ vol,
+__global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_adj(const float2* __restrict__ in, void* __restrict__ vol,
                                                     int cplx, const float* __restrict__ s, int N,
                                                     const float2* __restrict__ tw) {
   extern __shared__ float2 buf[];
   const int nrows = N * N;
   const int row0 = blockIdx.x * FFT_W;
   const int half = N / 2;
+#pragma unroll 8
   for (int idx = threadIdx.x; idx < FFT_W * K; idx += FFT_NT) {
     const int c = idx / K, k = idx - c * K;
     const int r = row0 + c;
@@ -148,11 +154,12 @@ __global__ void __launch_bounds__(FFT_NT) k_row_adj(const float2* __restrict__ i
 // Rows are lines (l0 + c); in-place operation (in == out) is allowed.
 // ----------------------------------------------------------------------------
 template <int M, bool FWD>
-__global__ void __launch_bounds__(FFT_NT) k_line(const float2* in, float2* out, int D,
+__global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_line(const float2* in, float2* out, int D,
                                                  const float2* __restrict__ weight,
                                                  const float2* __restrict__ tw) {
   extern __shared__ float2 buf[];
   const int l0 = blockIdx.x * FFT_W;
+#pragma unroll 8
   for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
     const int c = idx / M, m = idx - c * M;
     const int l = l0 + c;
