@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--spread-variant", type=int, default=-1)
     ap.add_argument("--points-per-subproblem", type=int, default=0)
     ap.add_argument("--tile-edge", type=int, default=0)
+    ap.add_argument("--keep-duplicates", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-lines", type=int, default=1500)
@@ -112,24 +113,28 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # roofline bookkeeping: algorithmic work per stage
 # ----------------------------------------------------------------------------
-def stage_work(n, k, j, m, d):
-    """Algorithmic bytes and flops per launch of each stage."""
+def stage_work(n, k, j, m, d, p_eval=None):
+    """Algorithmic bytes and flops per launch of each stage: every stage moves
+    its input and output arrays once; the interpolation does 8 (J^3 + J^2 + J)
+    flops per evaluated point (coincident samples are evaluated once) and reads
+    the touched part of the grid (the ball |k| <= K/2 + J/2)."""
     P = d * m
+    Pe = P if p_eval is None else p_eval
     c8 = 8
     ball = min(1.0, 4.0 / 3.0 * 3.141592653589793 * (0.5 + (j / 2) / k) ** 3)
-    interp_flops = 8 * (j ** 3 + j ** 2 + j) * P
+    interp_flops = 8 * (j ** 3 + j ** 2 + j) * Pe
     return {
         "forward": {
             "x_pass": {"bytes": 4 * n ** 3 + c8 * n * n * k},
             "y_pass": {"bytes": c8 * n * n * k + c8 * n * k * k},
             "z_pass": {"bytes": c8 * n * k * k + c8 * k ** 3},
-            "gather": {"bytes": ball * c8 * k ** 3 + c8 * P + 4 * P, "flops": interp_flops},
+            "gather": {"bytes": ball * c8 * k ** 3 + c8 * P + 8 * Pe, "flops": interp_flops},
             "line_dft": {"bytes": 2 * c8 * P},
         },
         "adjoint": {
             "line_dft": {"bytes": 2 * c8 * P},
             "grid_clear": {"bytes": c8 * k ** 3},
-            "spread": {"bytes": 2 * ball * c8 * k ** 3 + c8 * P + 4 * P, "flops": interp_flops},
+            "spread": {"bytes": 2 * ball * c8 * k ** 3 + c8 * P + 8 * Pe, "flops": interp_flops},
             "z_pass": {"bytes": c8 * k ** 3 + c8 * n * k * k},
             "y_pass": {"bytes": c8 * n * k * k + c8 * n * n * k},
             "x_pass": {"bytes": c8 * n * n * k + 4 * n ** 3},
@@ -319,7 +324,8 @@ def run_ours(args):
     dirs = w.directions()
     x = w.volume(np.float32)
     t0 = time.perf_counter()
-    plan = Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp, grid_dtype=args.grid_dtype)
+    plan = Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp, grid_dtype=args.grid_dtype,
+                keep_duplicates=args.keep_duplicates)
     plan.tune(args.gather_variant, args.spread_variant, args.points_per_subproblem, args.tile_edge)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
@@ -391,7 +397,8 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel ---------------------------------
     peaks = load_peaks()
-    work = stage_work(w.n, w.k, w.j, w.m, plan.n_dirs)
+    info = plan.info()
+    work = stage_work(w.n, w.k, w.j, w.m, plan.n_dirs, info["evaluated_points"])
     per_call = {}
     for side in ("forward", "adjoint"):
         calls = max(1, stages[f"{side}_calls"])

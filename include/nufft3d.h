@@ -86,6 +86,10 @@ typedef struct {
   int complex_volume;     /* 0: float32 real volume in/out; 1: complex64              */
   int do_line_fft;        /* 1: plane integrals (line inverse DFT applied);
                              0: raw Fourier samples X^(omega) (no line DFT)            */
+  int keep_duplicates;    /* 0: a sample that coincides with another one (line l' =
+                             -line l within 1e-13, radius -r) is interpolated once and
+                             its value shared (the partner direction is snapped to the
+                             exact negation); 1: every sample separately           */
 } nufft3d_params;
 
 /* Create a plan.  Validates *p, computes in FP64 on the host the scaling
@@ -124,9 +128,10 @@ int nufft3d_plan_destroy(nufft3d_plan plan);
 /* Static description of a status code (never NULL). */
 const char* nufft3d_error_string(int status);
 
-/* Numbers of the plan; out must hold 8 ints: tile edge T, tiles per axis,
+/* Numbers of the plan; out must hold 10 ints: tile edge T, tiles per axis,
  * subproblems, gather variant, spread variant, points per subproblem,
- * non-empty tiles, most points in one tile.  For tests and tuning. */
+ * non-empty tiles, most points in one tile, evaluated points (samples after
+ * merging coincident ones), merged antipodal line pairs.  For tests and tuning. */
 int nufft3d_plan_info(nufft3d_plan plan, int* out);
 
 /* Select the gather and spread kernel variants, the number of points per

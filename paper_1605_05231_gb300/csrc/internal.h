@@ -11,13 +11,15 @@
 
 namespace nufft {
 
+constexpr uint32_t kNoTwin = 0xffffffffu;
+
 // point-to-tile binning and the interpolation kernels' view of a plan
 struct InterpGeom {
   int K, J, L, T, nT, M, D;
   const float2* dir;     // [D][3] (hi, lo) direction components
   const float2* rad;     // [M] (hi, lo) radius in grid units
   const float2* table;   // [(L + 1) * J] min-max coefficients
-  const uint32_t* sorted;  // point ids sorted by tile
+  const uint2* sorted;   // (point id, coincident twin id or kNoTwin), sorted by tile
   int* err;              // device check word
   int* counter;          // two work counters (gather, spread) for the persistent variants
   int S;                 // most points in one subproblem
@@ -42,7 +44,8 @@ cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_ou
 cudaError_t launch_line(int M, bool fwd, const float2* in, float2* out, int D, const float2* w,
                         const float2* tw, cudaStream_t st);
 
-cudaError_t launch_bin_points(const InterpGeom& g, uint32_t* bins, cudaStream_t st);
+cudaError_t launch_bin_points(const InterpGeom& g, const uint32_t* ids, long long count, uint32_t* bins,
+                              cudaStream_t st);
 // subs: int4 (bin, start, count, 0); variant 0 = thread per point, 1 = warp per point
 cudaError_t launch_gather(const InterpGeom& g, int variant, int grid_dtype, const void* grid, float inv_scale,
                           const int4* subs, int n_subs, float2* out, cudaStream_t st);
@@ -54,6 +57,7 @@ bool v2_supported(int T, int J, int L);
 int plan_forward_enqueue(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st);
 int plan_adjoint_enqueue(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st);
 bool v3_supported(int T, int J, int S);
+bool v4_supported(int T, int J, int S, int L);
 
 }  // namespace nufft
 
@@ -77,7 +81,12 @@ struct nufft3d_plan_s {
   float2* d_table = nullptr;
   float2* d_twK = nullptr;
   float2* d_twM = nullptr;
-  uint32_t* d_sorted = nullptr;
+  uint2* d_sorted = nullptr;      // (id, twin) per evaluated point, sorted by tile
+  uint32_t* d_unique = nullptr;   // ids of the evaluated points (plan time only)
+  std::vector<uint32_t> h_unique; // same, host copy
+  std::vector<uint32_t> h_twin;   // twin of each evaluated point (kNoTwin if none)
+  long long P_eval = 0;           // number of evaluated points
+  int n_pairs = 0;                // antipodal line pairs merged
   int4* d_sub = nullptr;
   int n_sub = 0;
   float2* d_grid = nullptr;   // K^3

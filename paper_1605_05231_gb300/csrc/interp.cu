@@ -31,31 +31,44 @@ __device__ __forceinline__ void decode_point(const InterpGeom& g, uint32_t id, i
   }
 }
 
+static int g_num_sms = 0;
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 152;
+  }
+  return g_num_sms;
+}
+
 template <int J>
-__global__ void k_bin_points(InterpGeom g, long long P, uint32_t* __restrict__ bins) {
+__global__ void k_bin_points(InterpGeom g, const uint32_t* __restrict__ ids, long long P, uint32_t* __restrict__ bins) {
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
     int w0[3];
     float f[3];
-    decode_point<J>(g, (uint32_t)p, w0, f);
+    decode_point<J>(g, ids[p], w0, f);
     bins[p] = (uint32_t)(((w0[2] / g.T) * g.nT + w0[1] / g.T) * g.nT + w0[0] / g.T);
   }
 }
 
 template <int J>
-static cudaError_t launch_bin_t(const InterpGeom& g, uint32_t* bins, cudaStream_t st) {
-  const long long P = (long long)g.D * g.M;
+static cudaError_t launch_bin_t(const InterpGeom& g, const uint32_t* ids, long long P, uint32_t* bins,
+                                cudaStream_t st) {
   long long blocks = (P + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  k_bin_points<J><<<(unsigned)blocks, 256, 0, st>>>(g, P, bins);
+  if (blocks < 1) blocks = 1;
+  k_bin_points<J><<<(unsigned)blocks, 256, 0, st>>>(g, ids, P, bins);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin_points(const InterpGeom& g, uint32_t* bins, cudaStream_t st) {
+cudaError_t launch_bin_points(const InterpGeom& g, const uint32_t* ids, long long count, uint32_t* bins,
+                              cudaStream_t st) {
   switch (g.J) {
-    case 2: return launch_bin_t<2>(g, bins, st);
-    case 4: return launch_bin_t<4>(g, bins, st);
-    case 6: return launch_bin_t<6>(g, bins, st);
-    case 8: return launch_bin_t<8>(g, bins, st);
+    case 2: return launch_bin_t<2>(g, ids, count, bins, st);
+    case 4: return launch_bin_t<4>(g, ids, count, bins, st);
+    case 6: return launch_bin_t<6>(g, ids, count, bins, st);
+    case 8: return launch_bin_t<8>(g, ids, count, bins, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -101,7 +114,8 @@ __global__ void __launch_bounds__(256) k_gather_v0(InterpGeom g, const typename 
   stage_tile_plain<G>(grid, inv_scale, g.K, E, x0, y0, z0, tile);
   __syncthreads();
   for (int i = threadIdx.x; i < sp.z; i += blockDim.x) {
-    const uint32_t id = g.sorted[sp.y + i];
+    const uint2 ent = g.sorted[sp.y + i];
+    const uint32_t id = ent.x;
     int w0[3];
     float f[3];
     decode_point<J>(g, id, w0, f);
@@ -129,6 +143,7 @@ __global__ void __launch_bounds__(256) k_gather_v0(InterpGeom g, const typename 
       cmac(acc, cz[jz], zacc);
     }
     out[id] = acc;
+    if (ent.y != kNoTwin) out[ent.y] = acc;
   }
 }
 
@@ -144,7 +159,8 @@ __global__ void __launch_bounds__(256) k_spread_v0(InterpGeom g, const float2* _
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) tile[idx] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int i = threadIdx.x; i < sp.z; i += blockDim.x) {
-    const uint32_t id = g.sorted[sp.y + i];
+    const uint2 ent = g.sorted[sp.y + i];
+    const uint32_t id = ent.x;
     int w0[3];
     float f[3];
     decode_point<J>(g, id, w0, f);
@@ -153,7 +169,8 @@ __global__ void __launch_bounds__(256) k_spread_v0(InterpGeom g, const float2* _
       atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
       continue;
     }
-    const float2 v = in[id];
+    float2 v = in[id];
+    if (ent.y != kNoTwin) v = cadd(v, in[ent.y]);
     float2 cx[J], cy[J], cz[J];
     table_coeffs<J>(g.table, g.L, f[0], cx);
     table_coeffs<J>(g.table, g.L, f[1], cy);
@@ -229,9 +246,12 @@ __host__ __device__ inline V1Layout v1_layout(int T, int L) {
 // Phase 1 for one lane: decode, locate in the tile, write coefficients.
 // Returns the tile offset of the first tap (or -1 when the lane has no point).
 __device__ __forceinline__ int v1_phase1(const InterpGeom& g, const float2* table, int pi, int cnt, int start,
-                                         int x0, int y0, int z0, int P, int PP, float2* cp, uint32_t& id) {
+                                         int x0, int y0, int z0, int P, int PP, float2* cp, uint32_t& id,
+                                         uint32_t& tw) {
   if (pi >= cnt) return -1;
-  id = g.sorted[start + pi];
+  const uint2 ent = g.sorted[start + pi];
+  id = ent.x;
+  tw = ent.y;
   int w0[3];
   float f[3];
   decode_point<6>(g, id, w0, f);
@@ -300,8 +320,8 @@ __global__ void __launch_bounds__(V1_THREADS, 1) k_gather_v1(InterpGeom g, const
     stage_tile_padded<G>(grid, inv_scale, g.K, E, P, PP, x0, y0, z0, tile);
     __syncthreads();
     for (int b0 = warp * 32; b0 < sp.z; b0 += V1_THREADS) {
-      uint32_t id = 0;
-      const int off = v1_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, P, PP, coef + lane * V1_CSTRIDE, id);
+      uint32_t id = 0, tw = kNoTwin;
+      const int off = v1_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, P, PP, coef + lane * V1_CSTRIDE, id, tw);
       meta[lane] = off;
       __syncwarp();
       float2 acc[32];
@@ -344,7 +364,10 @@ __global__ void __launch_bounds__(V1_THREADS, 1) k_gather_v1(InterpGeom g, const
           acc[i] = make_float2(keep.x + rx, keep.y + ry);
         }
       }
-      if (off >= 0) out[id] = acc[0];
+      if (off >= 0) {
+        out[id] = acc[0];
+        if (tw != kNoTwin) out[tw] = acc[0];
+      }
       __syncwarp();
     }
   }
@@ -373,10 +396,10 @@ __global__ void __launch_bounds__(V1_THREADS, 1) k_spread_v1(InterpGeom g, const
     const int x0 = bx * T, y0 = by * T, z0 = bz * T;
     __syncthreads();  // the tile is zero again
     for (int b0 = warp * 32; b0 < sp.z; b0 += V1_THREADS) {
-      uint32_t id = 0;
+      uint32_t id = 0, tw = kNoTwin;
       float2* mycp = coef + lane * V1_CSTRIDE;
-      const int off = v1_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, P, PP, mycp, id);
-      if (off >= 0) mycp[18] = in[id];
+      const int off = v1_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, P, PP, mycp, id, tw);
+      if (off >= 0) mycp[18] = tw != kNoTwin ? cadd(in[id], in[tw]) : in[id];
       meta[lane] = off;
       __syncwarp();
       for (int p = 0; p < 32; ++p) {
@@ -482,9 +505,11 @@ __device__ __forceinline__ V2Lanes v2_lanes(int E, int lane) {
 // Phase 1 (one point per lane): decode, locate in the tile, interpolate the 18
 // coefficients from the shared table and store them as nine float4.
 __device__ __forceinline__ int v2_phase1(const InterpGeom& g, const float2* table, int pi, int cnt, int start,
-                                         int x0, int y0, int z0, int E, float2* cp, uint32_t& id) {
+                                         int x0, int y0, int z0, int E, float2* cp, uint32_t& id, uint32_t& tw) {
   if (pi >= cnt) return -1;
-  id = g.sorted[start + pi];
+  const uint2 ent = g.sorted[start + pi];
+  id = ent.x;
+  tw = ent.y;
   int w0[3];
   float f[3];
   decode_point<6>(g, id, w0, f);
@@ -549,8 +574,8 @@ __global__ void __launch_bounds__(V2_WARPS * 32, 1) k_gather_v2(InterpGeom g, co
     }
     __syncwarp();
     for (int b0 = 0; b0 < sp.z; b0 += 32) {
-      uint32_t id = 0;
-      const int off = v2_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, E, coef + lane * V2_CSTRIDE, id);
+      uint32_t id = 0, tw = kNoTwin;
+      const int off = v2_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, E, coef + lane * V2_CSTRIDE, id, tw);
       meta[lane] = off;
       __syncwarp();
       float2 acc[32];
@@ -592,7 +617,10 @@ __global__ void __launch_bounds__(V2_WARPS * 32, 1) k_gather_v2(InterpGeom g, co
           acc[i] = make_float2(keep.x + rx, keep.y + ry);
         }
       }
-      if (off >= 0) out[id] = acc[0];
+      if (off >= 0) {
+        out[id] = acc[0];
+        if (tw != kNoTwin) out[tw] = acc[0];
+      }
       __syncwarp();
     }
   }
@@ -625,9 +653,9 @@ __global__ void __launch_bounds__(V2_WARPS * 32, 1) k_spread_v2(InterpGeom g, co
     const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
     const int x0 = bx * T, y0 = by * T, z0 = bz * T;
     for (int b0 = 0; b0 < sp.z; b0 += 32) {
-      uint32_t id = 0;
-      const int off = v2_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, E, coef + lane * V2_CSTRIDE, id);
-      vals[lane] = off >= 0 ? in[id] : make_float2(0.f, 0.f);
+      uint32_t id = 0, tw = kNoTwin;
+      const int off = v2_phase1(g, table, b0 + lane, sp.z, sp.y, x0, y0, z0, E, coef + lane * V2_CSTRIDE, id, tw);
+      vals[lane] = off >= 0 ? (tw != kNoTwin ? cadd(in[id], in[tw]) : in[id]) : make_float2(0.f, 0.f);
       meta[lane] = off;
       __syncwarp();
       for (int p = 0; p < 32; ++p) {
@@ -704,8 +732,8 @@ __host__ __device__ inline V3Layout v3_layout(int T, int J, int S, int elem) {
   V3Layout l;
   l.E = T + J - 1;
   l.tile_bytes = ((size_t)l.E * l.E * l.E * elem + 15) / 16 * 16;
-  // per point: id, tile offset, f[3] (5 words) + ordered index (1 word); class counts and cursors
-  l.bytes = l.tile_bytes + (size_t)S * 6 * sizeof(int) + 64 * sizeof(int);
+  // per point: id, twin, tile offset, f[3] (6 words) + ordered index (1 word); class counts and cursors
+  l.bytes = l.tile_bytes + (size_t)S * 7 * sizeof(int) + 64 * sizeof(int);
   return l;
 }
 
@@ -724,7 +752,8 @@ __global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const ty
   const int E = lay.E, PP = E * E;
   TT* tile = (TT*)smem_raw;
   int* p_id = (int*)(smem_raw + lay.tile_bytes);
-  int* p_off = p_id + S;
+  int* p_tw = p_id + S;
+  int* p_off = p_tw + S;
   float* p_f = (float*)(p_off + S);  // [3][S]
   int* order = (int*)(p_f + 3 * S);
   int* ncls = order + S;             // [kRes] counts, [kRes] cursors
@@ -749,7 +778,8 @@ __global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const ty
   __syncthreads();
   // decode every point of the subproblem once
   for (int i = threadIdx.x; i < cnt; i += V3_THREADS) {
-    const uint32_t id = g.sorted[sp.y + i];
+    const uint2 ent = g.sorted[sp.y + i];
+    const uint32_t id = ent.x;
     int w0[3];
     float f[3];
     decode_point<J>(g, id, w0, f);
@@ -761,6 +791,7 @@ __global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const ty
       atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
     }
     p_id[i] = (int)id;
+    p_tw[i] = (int)ent.y;
     p_off[i] = off;
     p_f[i] = f[0];
     p_f[S + i] = f[1];
@@ -804,8 +835,189 @@ __global__ void __launch_bounds__(V3_THREADS) k_gather_v3(InterpGeom g, const ty
       }
       cmac(acc, cz[jz], zacc);
     }
-    out[p_id[i]] = cscale(acc, inv_scale);
+    const float2 res = cscale(acc, inv_scale);
+    out[p_id[i]] = res;
+    if ((uint32_t)p_tw[i] != kNoTwin) out[p_tw[i]] = res;
   }
+}
+
+// ---------------------------------------------------------------------------
+// variant 4 (gather, any J): variant 3 with the coefficient table in shared
+// memory.  One persistent CTA per SM holds the table once and runs
+// V4_GROUPS independent groups of 256 threads; each group takes whole
+// subproblems from a device work counter and synchronises on its own named
+// barrier.  Table reads become shared-memory loads instead of L1 tag lookups.
+// ---------------------------------------------------------------------------
+constexpr int V4_GROUPS = 4;
+constexpr int V4_GT = 256;  // threads per group
+
+__host__ __device__ inline size_t v4_group_bytes(int T, int J, int S, int elem) {
+  return (v3_layout(T, J, S, elem).bytes + 16 + 15) / 16 * 16;
+}
+
+__host__ __device__ inline size_t v4_bytes(int T, int J, int S, int L, int elem) {
+  const size_t table = ((size_t)(L + 1) * J * sizeof(float2) + 15) / 16 * 16;
+  return table + V4_GROUPS * v4_group_bytes(T, J, S, elem);
+}
+
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(V4_GT) : "memory");
+}
+
+template <int J>
+__device__ __forceinline__ void smem_table_coeffs(const float2* table, int L, float f, float2 (&c)[J]) {
+  float fl = f * (float)L;
+  int i = (int)fl;
+  if (i > L - 1) i = L - 1;
+  const float t = fl - (float)i;
+  const float4* r = (const float4*)(table + (size_t)i * J);
+  float4 v[J];
+#pragma unroll
+  for (int q = 0; q < J; ++q) v[q] = r[q];
+#pragma unroll
+  for (int q = 0; q < J / 2; ++q) {
+    const float4 a = v[q], b = v[q + J / 2];
+    c[2 * q] = make_float2(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y));
+    c[2 * q + 1] = make_float2(fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
+  }
+}
+
+template <int J, typename G>
+__global__ void __launch_bounds__(V4_GROUPS * V4_GT, 1) k_gather_v4(InterpGeom g, const typename G::T* __restrict__ grid,
+                                                                   const int4* __restrict__ subs, int n_subs, int S,
+                                                                   int* __restrict__ counter, float2* __restrict__ out) {
+  typedef typename G::T TT;
+  constexpr int kRes = sizeof(TT) == 4 ? 32 : 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const float inv_scale = lp_inv_scale<G>(g);
+  const int T = g.T, nT = g.nT, K = g.K;
+  const V3Layout lay = v3_layout(T, J, S, (int)sizeof(TT));
+  const int E = lay.E, PP = E * E;
+  float2* table = (float2*)smem_raw;
+  const size_t table_bytes = ((size_t)(g.L + 1) * J * sizeof(float2) + 15) / 16 * 16;
+  for (int i = threadIdx.x; i < (g.L + 1) * J; i += blockDim.x) table[i] = __ldg(g.table + i);
+  __syncthreads();
+  const int grp = threadIdx.x / V4_GT, tid = threadIdx.x % V4_GT;
+  unsigned char* gb = smem_raw + table_bytes + grp * v4_group_bytes(T, J, S, (int)sizeof(TT));
+  TT* tile = (TT*)gb;
+  int* p_id = (int*)(gb + lay.tile_bytes);
+  int* p_tw = p_id + S;
+  int* p_off = p_tw + S;
+  float* p_f = (float*)(p_off + S);
+  int* order = (int*)(p_f + 3 * S);
+  int* ncls = order + S;
+  int* work = ncls + 64;
+  for (;;) {
+    if (tid == 0) *work = atomicAdd(counter, 1);
+    if (tid < 2 * kRes) ncls[tid] = 0;
+    group_sync(grp);
+    const int s = *work;
+    if (s >= n_subs) break;
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    const int cnt = sp.z;
+    {
+      const int n = E * E * E;
+      for (int idx = tid; idx < n; idx += V4_GT) {
+        const int ix = idx % E;
+        const int t = idx / E;
+        const int iy = t % E, iz = t / E;
+        int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+        gx -= gx >= K ? K : 0;
+        gy -= gy >= K ? K : 0;
+        gz -= gz >= K ? K : 0;
+        tile[idx] = grid[((size_t)gz * K + gy) * K + gx];
+      }
+    }
+    for (int i = tid; i < cnt; i += V4_GT) {
+      const uint2 ent = g.sorted[sp.y + i];
+      const uint32_t id = ent.x;
+      int w0[3];
+      float f[3];
+      decode_point<J>(g, id, w0, f);
+      const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+      int off = -1;
+      if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+        off = (lz * E + ly) * E + lx;
+      } else {
+        atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+      }
+      p_id[i] = (int)id;
+      p_tw[i] = (int)ent.y;
+      p_off[i] = off;
+      p_f[i] = f[0];
+      p_f[S + i] = f[1];
+      p_f[2 * S + i] = f[2];
+      atomicAdd(&ncls[off < 0 ? 0 : (off & (kRes - 1))], 1);
+    }
+    group_sync(grp);
+    for (int i = tid; i < cnt; i += V4_GT) {
+      const int c = p_off[i] < 0 ? 0 : (p_off[i] & (kRes - 1));
+      const int r = atomicAdd(&ncls[kRes + c], 1);
+      int pos = 0;
+#pragma unroll
+      for (int q = 0; q < kRes; ++q) {
+        const int n = ncls[q];
+        pos += n < r ? n : r;
+        pos += (q < c && n > r) ? 1 : 0;
+      }
+      order[pos] = i;
+    }
+    group_sync(grp);
+    for (int k = tid; k < cnt; k += V4_GT) {
+      const int i = order[k];
+      const int off = p_off[i];
+      if (off < 0) continue;
+      float2 cx[J], cy[J], cz[J];
+      smem_table_coeffs<J>(table, g.L, p_f[i], cx);
+      smem_table_coeffs<J>(table, g.L, p_f[S + i], cy);
+      smem_table_coeffs<J>(table, g.L, p_f[2 * S + i], cz);
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jz = 0; jz < J; ++jz) {
+        float2 zacc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jy = 0; jy < J; ++jy) {
+          const TT* tp = tile + off + jz * PP + jy * E;
+          float2 row = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int jx = 0; jx < J; ++jx) cmac(row, cx[jx], G::to_f2(tp[jx]));
+          cmac(zacc, cy[jy], row);
+        }
+        cmac(acc, cz[jz], zacc);
+      }
+      const float2 res = cscale(acc, inv_scale);
+      out[p_id[i]] = res;
+      if ((uint32_t)p_tw[i] != kNoTwin) out[p_tw[i]] = res;
+    }
+    group_sync(grp);
+  }
+}
+
+template <int J, typename G>
+static cudaError_t launch_gather_v4_t(const InterpGeom& g, const void* grid, const int4* subs, int n_subs, int S,
+                                      float2* out, cudaStream_t st) {
+  auto f = k_gather_v4<J, G>;
+  const size_t smem = v4_bytes(g.T, J, S, g.L, (int)sizeof(typename G::T));
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  e = cudaMemsetAsync(g.counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  f<<<num_sms(), V4_GROUPS * V4_GT, smem, st>>>(g, (const typename G::T*)grid, subs, n_subs, S, g.counter, out);
+  return cudaGetLastError();
+}
+
+template <int J>
+static cudaError_t launch_gather_v4_j(const InterpGeom& g, int dtype, const void* grid, const int4* subs, int n_subs,
+                                      int S, float2* out, cudaStream_t st) {
+  switch (dtype) {
+    case 0: return launch_gather_v4_t<J, GridC64>(g, grid, subs, n_subs, S, out, st);
+    case 1: return launch_gather_v4_t<J, GridBF16>(g, grid, subs, n_subs, S, out, st);
+    case 2: return launch_gather_v4_t<J, GridF16>(g, grid, subs, n_subs, S, out, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int J, typename G>
@@ -831,22 +1043,16 @@ static cudaError_t launch_gather_v3_j(const InterpGeom& g, int dtype, const void
   return cudaErrorInvalidValue;
 }
 
-static int g_num_sms = 0;
-static int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 152;
-  }
-  return g_num_sms;
-}
 
 static int max_optin_smem() {
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   return maxsm;
+}
+
+bool v4_supported(int T, int J, int S, int L) {
+  return v4_bytes(T, J, S, L, 8) <= (size_t)max_optin_smem();
 }
 
 bool v3_supported(int T, int J, int S) {
@@ -934,6 +1140,15 @@ static cudaError_t launch_gather_v2_t(const InterpGeom& g, const void* grid, flo
 
 cudaError_t launch_gather(const InterpGeom& g, int variant, int grid_dtype, const void* grid, float inv_scale,
                           const int4* subs, int n_subs, float2* out, cudaStream_t st) {
+  if (variant == 4) {
+    switch (g.J) {
+      case 2: return launch_gather_v4_j<2>(g, grid_dtype, grid, subs, n_subs, g.S, out, st);
+      case 4: return launch_gather_v4_j<4>(g, grid_dtype, grid, subs, n_subs, g.S, out, st);
+      case 6: return launch_gather_v4_j<6>(g, grid_dtype, grid, subs, n_subs, g.S, out, st);
+      case 8: return launch_gather_v4_j<8>(g, grid_dtype, grid, subs, n_subs, g.S, out, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (variant == 3) {
     switch (g.J) {
       case 2: return launch_gather_v3_j<2>(g, grid_dtype, grid, inv_scale, subs, n_subs, g.S, out, st);

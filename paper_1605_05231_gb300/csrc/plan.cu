@@ -4,10 +4,12 @@
 // tile, workspace management and the orchestration of the forward and adjoint
 // passes.  Every entry point of include/nufft3d.h is defined here.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -18,7 +20,7 @@ typedef std::complex<double> cd;
 namespace {
 
 struct Resolved {
-  int N, K, J, L, D, M, grid_dtype, cplx, line_fft;
+  int N, K, J, L, D, M, grid_dtype, cplx, line_fft, keep_dup;
   long long P;
   int T, nT;
 };
@@ -38,6 +40,7 @@ int resolve(const nufft3d_params* p, Resolved& r) {
   r.grid_dtype = p->grid_dtype;
   r.cplx = p->complex_volume ? 1 : 0;
   r.line_fft = p->do_line_fft ? 1 : 0;
+  r.keep_dup = p->keep_duplicates ? 1 : 0;
   if (r.N < 8 || r.N > kMaxEdge || (r.N & 1)) return NUFFT3D_ERR_ARG;
   if (r.K < r.N || r.K > kMaxEdge) return NUFFT3D_ERR_ARG;
   if (r.J < 2 || r.J > 8) return NUFFT3D_ERR_ARG;
@@ -199,6 +202,71 @@ bool build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
   return true;
 }
 
+// Coincident samples.  If line l2 runs opposite to line l (d_l2 = -d_l within
+// 1e-13 per component) and the radii are symmetric (r[M - m] = -r[m]), sample
+// (l2, M - m) is the same Fourier point as (l, m) for m >= 1.  Such pairs are
+// interpolated once: l2 keeps only its sample m = 0 (whose partner radius is
+// not sampled), and (l, m) carries (l2, M - m) as its twin.  The direction of
+// l2 is snapped to the exact negation of d_l so both decode bit-identically.
+void pair_lines(const nufft3d_params* p, const Resolved& r, HostTables& h, std::vector<uint32_t>& ids,
+                std::vector<uint32_t>& twin, int& n_pairs) {
+  const int D = r.D, M = r.M;
+  ids.clear();
+  twin.clear();
+  n_pairs = 0;
+  std::vector<int> partner(D, -1), role(D, 0);  // role 1: keeps all samples, 2: keeps m = 0 only
+  bool symmetric = !r.keep_dup && (M % 2 == 0);
+  if (symmetric) {
+    std::vector<double> rad(M);
+    for (int m = 0; m < M; ++m)
+      rad[m] = p->omega ? p->omega[m] * r.K / (2.0 * M_PI) : (double)(m - M / 2) * r.K / M;
+    for (int m = 1; m < M && symmetric; ++m) symmetric = rad[M - m] == -rad[m];
+  }
+  if (symmetric) {
+    struct KeyHash {
+      size_t operator()(const std::array<long long, 3>& k) const {
+        return (size_t)(k[0] * 73856093ll ^ k[1] * 19349663ll ^ k[2] * 83492791ll);
+      }
+    };
+    auto key = [](const double* d, double sgn) {
+      return std::array<long long, 3>{std::llround(sgn * d[0] * 1e9), std::llround(sgn * d[1] * 1e9),
+                                      std::llround(sgn * d[2] * 1e9)};
+    };
+    std::unordered_map<std::array<long long, 3>, std::vector<int>, KeyHash> by_dir;
+    for (int l = 0; l < D; ++l) by_dir[key(p->dirs + 3 * l, 1.0)].push_back(l);
+    for (int l = 0; l < D; ++l) {
+      if (role[l]) continue;
+      auto it = by_dir.find(key(p->dirs + 3 * l, -1.0));
+      if (it == by_dir.end()) continue;
+      for (int l2 : it->second) {
+        if (l2 <= l || role[l2]) continue;
+        const double* a = p->dirs + 3 * l;
+        const double* b = p->dirs + 3 * l2;
+        if (std::fabs(a[0] + b[0]) <= 1e-13 && std::fabs(a[1] + b[1]) <= 1e-13 && std::fabs(a[2] + b[2]) <= 1e-13) {
+          role[l] = 1;
+          role[l2] = 2;
+          partner[l] = l2;
+          for (int c = 0; c < 3; ++c) h.dir[(size_t)l2 * 3 + c] = split(-a[c]);
+          ++n_pairs;
+          break;
+        }
+      }
+    }
+  }
+  for (int l = 0; l < D; ++l) {
+    const uint32_t base = (uint32_t)l * (uint32_t)M;
+    if (role[l] == 2) {
+      ids.push_back(base);
+      twin.push_back(nufft::kNoTwin);
+      continue;
+    }
+    for (int m = 0; m < M; ++m) {
+      ids.push_back(base + (uint32_t)m);
+      twin.push_back(role[l] == 1 && m >= 1 ? (uint32_t)partner[l] * (uint32_t)M + (uint32_t)(M - m) : nufft::kNoTwin);
+    }
+  }
+}
+
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return NUFFT3D_OK;
   if (e == cudaErrorMemoryAllocation) return NUFFT3D_ERR_NOMEM;
@@ -285,23 +353,27 @@ int build_subproblems(nufft3d_plan pl, int S, cudaStream_t st) {
 }
 
 int sort_points(nufft3d_plan pl, cudaStream_t st) {
-  const long long P = pl->P;
+  const long long P = pl->P_eval;
   uint32_t* d_bins = nullptr;
   CK(dalloc(&d_bins, (size_t)P));
+  uint32_t* d_ids = nullptr;
+  cudaError_t e = upload(&d_ids, pl->h_unique, st);
   InterpGeom g = geom(pl);
-  cudaError_t e = nufft::launch_bin_points(g, d_bins, st);
+  if (e == cudaSuccess) e = nufft::launch_bin_points(g, d_ids, P, d_bins, st);
   std::vector<uint32_t> bins;
   if (e == cudaSuccess) {
     try {
       bins.resize((size_t)P);
     } catch (...) {
       cudaFree(d_bins);
+      cudaFree(d_ids);
       return NUFFT3D_ERR_NOMEM;
     }
     e = cudaMemcpyAsync(bins.data(), d_bins, (size_t)P * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
   cudaFree(d_bins);
+  if (d_ids) cudaFree(d_ids);
   if (e != cudaSuccess) return cuda_status(e);
   // stable counting sort by bin
   const size_t nb = (size_t)pl->nT * pl->nT * pl->nT;
@@ -311,10 +383,10 @@ int sort_points(nufft3d_plan pl, cudaStream_t st) {
     off[bins[i] + 1]++;
   }
   for (size_t b = 0; b < nb; ++b) off[b + 1] += off[b];
-  std::vector<uint32_t> sorted((size_t)P);
+  std::vector<uint2> sorted((size_t)P);
   {
     std::vector<long long> pos(off.begin(), off.end() - 1);
-    for (long long i = 0; i < P; ++i) sorted[pos[bins[i]]++] = (uint32_t)i;
+    for (long long i = 0; i < P; ++i) sorted[pos[bins[i]]++] = make_uint2(pl->h_unique[i], pl->h_twin[i]);
   }
   pl->bin_offsets.swap(off);
   CK(upload(&pl->d_sorted, sorted, st));
@@ -328,6 +400,9 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   if (rc != NUFFT3D_OK) return rc;
   HostTables h;
   if (!build_tables(p, r, h)) return NUFFT3D_ERR_ARG;
+  std::vector<uint32_t> ids, twin;
+  int n_pairs = 0;
+  pair_lines(p, r, h, ids, twin, n_pairs);
   nufft3d_plan pl = new (std::nothrow) nufft3d_plan_s();
   if (!pl) return NUFFT3D_ERR_NOMEM;
   *out = pl;  // freed by the caller on failure
@@ -343,6 +418,10 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->grid_dtype = r.grid_dtype;
   pl->T = r.T;
   pl->nT = r.nT;
+  pl->h_unique.swap(ids);
+  pl->h_twin.swap(twin);
+  pl->P_eval = (long long)pl->h_unique.size();
+  pl->n_pairs = n_pairs;
   pl->spread_variant = nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0;
   pl->gather_variant = nufft::v3_supported(r.T, r.J, 1024) ? 3 : 0;
   CK(cudaGetDevice(&pl->device));
@@ -514,7 +593,7 @@ int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes) {
   b += (size_t)r.N * r.N * r.K * sizeof(float2);
   b += (size_t)r.N * r.K * r.K * sizeof(float2);
   if (r.line_fft) b += (size_t)r.P * sizeof(float2);
-  b += (size_t)r.P * sizeof(uint32_t);                                   // point sort
+  b += (size_t)r.P * sizeof(uint2);                                      // point sort (upper bound)
   b += (size_t)(r.L + 1) * r.J * sizeof(float2);                         // table
   b += (size_t)r.D * 3 * sizeof(float2) + (size_t)r.M * 2 * sizeof(float2) + r.N * sizeof(float);
   b += (size_t)(r.K + r.M) * sizeof(float2);
@@ -572,13 +651,15 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
   out[5] = plan->pts_per_sub;
   out[6] = nonempty;
   out[7] = (int)std::min<long long>(maxc, 0x7fffffff);
+  out[8] = (int)std::min<long long>(plan->P_eval, 0x7fffffff);
+  out[9] = plan->n_pairs;
   return NUFFT3D_OK;
 }
 
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 3 || spread_variant < -1 || spread_variant > 2) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 4 || spread_variant < -1 || spread_variant > 2) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -589,6 +670,7 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   if ((gv == 1 || sv == 1) && plan->J != 6) return NUFFT3D_ERR_UNSUPPORTED;
   const int S_new = points_per_subproblem > 0 ? points_per_subproblem : plan->pts_per_sub;
   if (gv == 3 && !nufft::v3_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
+  if (gv == 4 && !nufft::v4_supported(T, plan->J, S_new, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
   int rc = ensure_device(plan);
   if (rc != NUFFT3D_OK) return rc;
   CK(cudaStreamSynchronize(plan->last_stream));

@@ -80,7 +80,7 @@ def test_full_size_reduced_precision_grid(cuda_lib, problem, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp16"])
-@pytest.mark.parametrize("gv", [0, 2, 3])
+@pytest.mark.parametrize("gv", [0, 2, 3, 4])
 def test_reduced_precision_small_all_variants(cuda_lib, dtype, gv):
     """Every gather variant reads the reduced-precision grid with the same scale;
     the adjoint keeps FP32 accumulation and stays at the FP32 bar."""
@@ -91,7 +91,7 @@ def test_reduced_precision_small_all_variants(cuda_lib, dtype, gv):
     x = w.volume(np.float32)
     y = I.random_lines(dirs.shape[0], w.m, 3).astype(np.complex64)
     plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, grid_dtype=dtype)
-    plan.tune(gv)
+    plan.tune(gv, -1, 512 if gv == 4 else 0)
     p = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     a = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
     op = O.OraclePlan(w.n, w.k, w.j, w.table_oversamp, dirs, w.m)
