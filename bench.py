@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--keep-duplicates", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-lines", type=int, default=1500)
+    ap.add_argument("--cpu-sample-lines", type=int, default=4000)
     return ap.parse_args()
 
 
@@ -128,13 +128,15 @@ def stage_work(n, k, j, m, d, p_eval=None):
             "x_pass": {"bytes": 4 * n ** 3 + c8 * n * n * k},
             "y_pass": {"bytes": c8 * n * n * k + c8 * n * k * k},
             "z_pass": {"bytes": c8 * n * k * k + c8 * k ** 3},
-            "gather": {"bytes": ball * c8 * k ** 3 + c8 * P + 8 * Pe, "flops": interp_flops},
+            "gather": {"bytes": ball * c8 * k ** 3 + c8 * P + 8 * Pe, "flops": interp_flops,
+                       "smem_bytes": j ** 3 * 8 * Pe},
             "line_dft": {"bytes": 2 * c8 * P},
         },
         "adjoint": {
             "line_dft": {"bytes": 2 * c8 * P},
             "grid_clear": {"bytes": c8 * k ** 3},
-            "spread": {"bytes": 2 * ball * c8 * k ** 3 + c8 * P + 8 * Pe, "flops": interp_flops},
+            "spread": {"bytes": 2 * ball * c8 * k ** 3 + c8 * P + 8 * Pe, "flops": interp_flops,
+                       "smem_bytes": j ** 3 * 16 * Pe},
             "z_pass": {"bytes": c8 * k ** 3 + c8 * n * k * k},
             "y_pass": {"bytes": c8 * n * k * k + c8 * n * n * k},
             "x_pass": {"bytes": c8 * n * n * k + 4 * n ** 3},
@@ -419,6 +421,11 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "kernel": f"{dom[0]}.{dom[1]}"}
     roof["peak_source"] = peaks["source"]
+    if "smem_bytes" in wk:
+        smem_peak = SMS * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        roof["smem_frac"] = wk["smem_bytes"] / t_dom / 1e12 / smem_peak
+        roof["smem_basis"] = (f"shared-memory data path: {SMS} SMs x 128 B/clk x {peaks['sm_max_mhz']:.0f} MHz = "
+                              f"{smem_peak:.1f} TB/s; per evaluated point J^3 x 8 B (gather) or x 16 B (spread)")
     roof["algorithmic_bytes"] = wk["bytes"]
     roof["hbm_frac"] = wk["bytes"] / t_dom / 1e9 / peaks["hbm_gbs"]
     roof["traffic"] = ncu_traffic(f"{dom[0]}.{dom[1]}")

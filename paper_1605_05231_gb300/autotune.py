@@ -16,12 +16,13 @@ from .binding import NufftError
 
 # (gather variant, spread variant, points per subproblem, tile edge)
 CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
-    (3, 2, 256, 8),
+    (3, 3, 256, 8),
+    (3, 3, 512, 8),
+    (3, 3, 1024, 8),
+    (4, 3, 512, 8),
     (3, 2, 512, 8),
-    (3, 2, 1024, 8),
-    (3, 2, 2048, 8),
     (2, 2, 1024, 8),
-    (0, 2, 1024, 8),
+    (0, 3, 512, 8),
     (3, 0, 1024, 16),
     (3, 1, 1024, 16),
 )

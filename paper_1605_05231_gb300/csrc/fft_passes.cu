@@ -34,21 +34,33 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_fwd(const void* __
   const int nrows = N * N;
   const int row0 = blockIdx.x * FFT_W;
   const int half = N / 2;
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < FFT_W * N; idx += FFT_NT) {
-    const int c = idx / N, x = idx - c * N;
-    const int r = row0 + c;
-    float2 v = make_float2(0.f, 0.f);
-    if (r < nrows) {
-      const int z = r / N, y = r - z * N;
-      const float sc = __ldg(s + x) * __ldg(s + y) * __ldg(s + z);
-      if (cplx) {
-        v = cscale(((const float2*)vol)[(size_t)r * N + x], sc);
-      } else {
-        v = make_float2(((const float*)vol)[(size_t)r * N + x] * sc, 0.f);
+  // loads of a chunk are issued before its shared stores (batched in flight)
+  for (int base = threadIdx.x; base < FFT_W * N; base += 8 * FFT_NT) {
+    float2 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * FFT_NT;
+      t[u] = make_float2(0.f, 0.f);
+      if (idx < FFT_W * N) {
+        const int c = idx / N, x = idx - c * N;
+        const int r = row0 + c;
+        if (r < nrows) {
+          if (cplx) t[u] = ((const float2*)vol)[(size_t)r * N + x];
+          else t[u] = make_float2(((const float*)vol)[(size_t)r * N + x], 0.f);
+        }
       }
     }
-    buf[centred_to_grid(x, half, K) * FFT_PITCH + c] = v;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * FFT_NT;
+      if (idx < FFT_W * N) {
+        const int c = idx / N, x = idx - c * N;
+        const int r = row0 + c;
+        const int z = r / N, y = r - z * N;
+        const float sc = r < nrows ? __ldg(s + x) * __ldg(s + y) * __ldg(s + z) : 0.f;
+        buf[centred_to_grid(x, half, K) * FFT_PITCH + c] = cscale(t[u], sc);
+      }
+    }
   }
   for (int idx = threadIdx.x; idx < FFT_W * (K - N); idx += FFT_NT) {
     const int c = idx % FFT_W, i = idx / FFT_W + (N - half);
@@ -83,11 +95,22 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_col(const float2* __re
   OutT* ob = out + o * out_outer + (long long)ch * FFT_W;
   const int half = N / 2;
   const int in_len = PAD_IN ? N : L;
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < FFT_W * in_len; idx += FFT_NT) {
-    const int c = idx % FFT_W, i = idx / FFT_W;
-    const int k = PAD_IN ? centred_to_grid(i, half, L) : i;
-    buf[k * FFT_PITCH + c] = ib[(long long)i * in_stride + c];
+  for (int base = threadIdx.x; base < FFT_W * in_len; base += 8 * FFT_NT) {
+    float2 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * FFT_NT;
+      if (idx < FFT_W * in_len) t[u] = ib[(long long)(idx / FFT_W) * in_stride + idx % FFT_W];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * FFT_NT;
+      if (idx < FFT_W * in_len) {
+        const int c = idx % FFT_W, i = idx / FFT_W;
+        const int k = PAD_IN ? centred_to_grid(i, half, L) : i;
+        buf[k * FFT_PITCH + c] = t[u];
+      }
+    }
   }
   if (PAD_IN) {
     for (int idx = threadIdx.x; idx < FFT_W * (L - N); idx += FFT_NT) {
@@ -126,11 +149,23 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_adj(const float2* 
   const int nrows = N * N;
   const int row0 = blockIdx.x * FFT_W;
   const int half = N / 2;
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < FFT_W * K; idx += FFT_NT) {
-    const int c = idx / K, k = idx - c * K;
-    const int r = row0 + c;
-    buf[k * FFT_PITCH + c] = r < nrows ? in[(size_t)r * K + k] : make_float2(0.f, 0.f);
+  for (int base = threadIdx.x; base < FFT_W * K; base += 8 * FFT_NT) {
+    float2 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * FFT_NT;
+      const int c = idx / K, k = idx - c * K;
+      const int r = row0 + c;
+      t[u] = (idx < FFT_W * K && r < nrows) ? in[(size_t)r * K + k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * FFT_NT;
+      if (idx < FFT_W * K) {
+        const int c = idx / K, k = idx - c * K;
+        buf[k * FFT_PITCH + c] = t[u];
+      }
+    }
   }
   __syncthreads();
   smem_fft<K, FFT_W, FFT_NT, true>(buf, FFT_PITCH, tw);
@@ -159,17 +194,26 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_line(const float2* in,
                                                  const float2* __restrict__ tw) {
   extern __shared__ float2 buf[];
   const int l0 = blockIdx.x * FFT_W;
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
-    const int c = idx / M, m = idx - c * M;
-    const int l = l0 + c;
-    float2 v = make_float2(0.f, 0.f);
-    if (l < D) {
-      v = in[(size_t)l * M + m];
-      if (FWD && weight) v = cmul(v, __ldg(weight + m));
-      if (m & 1) v = make_float2(-v.x, -v.y);
+  for (int base = threadIdx.x; base < FFT_W * M; base += 8 * FFT_NT) {
+    float2 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * FFT_NT;
+      const int c = idx / M, m = idx - c * M;
+      const int l = l0 + c;
+      t[u] = (idx < FFT_W * M && l < D) ? in[(size_t)l * M + m] : make_float2(0.f, 0.f);
     }
-    buf[m * FFT_PITCH + c] = v;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * FFT_NT;
+      if (idx < FFT_W * M) {
+        const int c = idx / M, m = idx - c * M;
+        float2 v = t[u];
+        if (FWD && weight) v = cmul(v, __ldg(weight + m));
+        if (m & 1) v = make_float2(-v.x, -v.y);
+        buf[m * FFT_PITCH + c] = v;
+      }
+    }
   }
   __syncthreads();
   smem_fft<M, FFT_W, FFT_NT, FWD>(buf, FFT_PITCH, tw);

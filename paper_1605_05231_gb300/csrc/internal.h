@@ -58,6 +58,7 @@ int plan_forward_enqueue(nufft3d_plan pl, const void* vol, void* lines, cudaStre
 int plan_adjoint_enqueue(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st);
 bool v3_supported(int T, int J, int S);
 bool v4_supported(int T, int J, int S, int L);
+bool v3s_supported(int T, int J);
 
 }  // namespace nufft
 

@@ -708,6 +708,151 @@ __global__ void __launch_bounds__(V2_WARPS * 32, 1) k_spread_v2(InterpGeom g, co
 }
 
 // ---------------------------------------------------------------------------
+// spread variant 3 (J = 6, T = 8): variant 2 with more warps per SM and less
+// shared-memory traffic per point.  The coefficient table is read through L1
+// in phase 1 (freeing its 49 KB of shared memory for two more warps per SM),
+// a point's tile offset and value travel as one float4, and the coefficients
+// of the next point are loaded into registers while the current point's
+// read-modify-writes drain.
+// ---------------------------------------------------------------------------
+constexpr int V3S_WARPS = 10;
+
+__host__ __device__ inline size_t v3s_warp_bytes(int T) {
+  const int E = T + 5;
+  const size_t w = (size_t)32 * V2_CSTRIDE * sizeof(float2) + 32 * sizeof(float4) +
+                   (size_t)E * E * E * sizeof(float2);
+  return (w + 15) / 16 * 16;
+}
+
+__host__ __device__ inline size_t v3s_bytes(int T) { return V3S_WARPS * v3s_warp_bytes(T); }
+
+struct V3SCoef {
+  float2 cx, cy, ox, oy, oz;
+  float4 z01, z23, z45;
+  float4 mv;  // tile offset (int bits), value
+};
+
+__device__ __forceinline__ void v3s_load(const float2* coef, const float4* mvs, int p, const V2Lanes& ln,
+                                         V3SCoef& c) {
+  const float2* cp = coef + p * V2_CSTRIDE;
+  c.mv = mvs[p];
+  c.cx = cp[ln.mjx];
+  c.cy = cp[6 + ln.mjy];
+  c.z01 = *(const float4*)(cp + 12);
+  c.z23 = *(const float4*)(cp + 14);
+  c.z45 = *(const float4*)(cp + 16);
+  c.ox = cp[ln.ojx];
+  c.oy = cp[6 + ln.ojy];
+  c.oz = cp[12 + ln.ojz];
+}
+
+__global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, const float2* __restrict__ in,
+                                                                 const int4* __restrict__ subs, int n_subs,
+                                                                 int* __restrict__ counter,
+                                                                 float2* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int T = g.T, nT = g.nT, K = g.K;
+  const int E = T + 5, E3 = E * E * E, PP = E * E;
+  float2* coef = (float2*)(smem_raw + warp * v3s_warp_bytes(T));
+  float4* mvs = (float4*)(coef + 32 * V2_CSTRIDE);
+  float2* tile = (float2*)(mvs + 32);
+  for (int i = lane; i < E3; i += 32) tile[i] = make_float2(0.f, 0.f);
+  __syncwarp();
+  const V2Lanes ln = v2_lanes(E, lane);
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(counter, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= n_subs) break;
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    for (int b0 = 0; b0 < sp.z; b0 += 32) {
+      // phase 1: one point per lane
+      int off = -1;
+      float2 val = make_float2(0.f, 0.f);
+      const int pi = b0 + lane;
+      if (pi < sp.z) {
+        const uint2 ent = g.sorted[sp.y + pi];
+        int w0[3];
+        float f[3];
+        decode_point<6>(g, ent.x, w0, f);
+        const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+        if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+          off = (lz * E + ly) * E + lx;
+          val = in[ent.x];
+          if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+          float4* c4 = (float4*)(coef + lane * V2_CSTRIDE);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            float2 c[6];
+            table_coeffs_v4<6>(g.table, g.L, f[a], c);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) c4[a * 3 + q] = make_float4(c[2 * q].x, c[2 * q].y, c[2 * q + 1].x, c[2 * q + 1].y);
+          }
+        } else {
+          atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+        }
+      }
+      mvs[lane] = make_float4(__int_as_float(off), val.x, val.y, 0.f);
+      __syncwarp();
+      const int np = min(32, sp.z - b0);
+      V3SCoef cur;
+      v3s_load(coef, mvs, 0, ln, cur);
+      for (int p = 0; p < np; ++p) {
+        V3SCoef nxt;
+        if (p + 1 < np) v3s_load(coef, mvs, p + 1, ln, nxt);
+        const int mo = __float_as_int(cur.mv.x);
+        if (mo >= 0) {
+          const float2 v = make_float2(cur.mv.y, cur.mv.z);
+          const float2 a = cmulc(v, cmul(cur.cx, cur.cy));  // v conj(cx cy)
+          float2* tp = tile + mo + ln.main_off;
+          float2 t[6];
+#pragma unroll
+          for (int jz = 0; jz < 6; ++jz) t[jz] = tp[jz * PP];
+          const float2 cz[6] = {make_float2(cur.z01.x, cur.z01.y), make_float2(cur.z01.z, cur.z01.w),
+                                make_float2(cur.z23.x, cur.z23.y), make_float2(cur.z23.z, cur.z23.w),
+                                make_float2(cur.z45.x, cur.z45.y), make_float2(cur.z45.z, cur.z45.w)};
+#pragma unroll
+          for (int jz = 0; jz < 6; ++jz) {
+            t[jz].x = fmaf(a.x, cz[jz].x, fmaf(a.y, cz[jz].y, t[jz].x));
+            t[jz].y = fmaf(a.y, cz[jz].x, fmaf(-a.x, cz[jz].y, t[jz].y));
+          }
+#pragma unroll
+          for (int jz = 0; jz < 6; ++jz) tp[jz * PP] = t[jz];
+          if (lane < 24) {
+            const float2 w = cmulc(v, cmul(cmul(cur.ox, cur.oy), cur.oz));
+            float2* q = tile + mo + ln.ovf_off;
+            float2 u = *q;
+            u.x += w.x;
+            u.y += w.y;
+            *q = u;
+          }
+        }
+        __syncwarp();
+        cur = nxt;
+      }
+      __syncwarp();
+    }
+    for (int idx = lane; idx < E3; idx += 32) {
+      const float2 v = tile[idx];
+      if (v.x == 0.f && v.y == 0.f) continue;
+      tile[idx] = make_float2(0.f, 0.f);
+      const int ix = idx % E;
+      const int t = idx / E;
+      const int iy = t % E, iz = t / E;
+      int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      gz -= gz >= K ? K : 0;
+      atomicAdd(&grid[((size_t)gz * K + gy) * K + gx], v);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // variant 3 (gather, any J): one thread per point, with the points of a
 // subproblem reordered so that the 16 lanes of every half-warp hold points
 // whose first-tap offsets in the unpadded tile differ modulo 16 float2.  All
@@ -1051,6 +1196,10 @@ static int max_optin_smem() {
   return maxsm;
 }
 
+bool v3s_supported(int T, int J) {
+  return J == 6 && T == 8 && v3s_bytes(T) <= (size_t)max_optin_smem();
+}
+
 bool v4_supported(int T, int J, int S, int L) {
   return v4_bytes(T, J, S, L, 8) <= (size_t)max_optin_smem();
 }
@@ -1197,6 +1346,17 @@ static cudaError_t launch_spread_v0_t(const InterpGeom& g, const float2* in, con
 
 cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, const int4* subs, int n_subs,
                           float2* grid, cudaStream_t st) {
+  if (variant == 3 && v3s_supported(g.T, g.J)) {
+    auto f = k_spread_v3;
+    const size_t smem = v3s_bytes(g.T);
+    cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (n_subs == 0) return cudaSuccess;
+    e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    f<<<num_sms(), V3S_WARPS * 32, smem, st>>>(g, in, subs, n_subs, g.counter + 1, grid);
+    return cudaGetLastError();
+  }
   if (variant == 2 && v2_supported(g.T, g.J, g.L)) {
     auto f = k_spread_v2;
     const size_t smem = v2_layout(g.T, g.L).bytes;

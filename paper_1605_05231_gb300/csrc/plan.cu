@@ -422,8 +422,8 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->h_twin.swap(twin);
   pl->P_eval = (long long)pl->h_unique.size();
   pl->n_pairs = n_pairs;
-  pl->spread_variant = nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0;
-  pl->gather_variant = nufft::v3_supported(r.T, r.J, 1024) ? 3 : 0;
+  pl->spread_variant = nufft::v3s_supported(r.T, r.J) ? 3 : (nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0);
+  pl->gather_variant = nufft::v3_supported(r.T, r.J, 512) ? 3 : 0;
   CK(cudaGetDevice(&pl->device));
   CK(upload(&pl->d_s, h.s, st));
   CK(upload(&pl->d_table, h.table, st));
@@ -438,7 +438,7 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   CK(cudaStreamSynchronize(st));
   rc = sort_points(pl, st);
   if (rc != NUFFT3D_OK) return rc;
-  rc = build_subproblems(pl, 1024, st);
+  rc = build_subproblems(pl, 512, st);
   if (rc != NUFFT3D_OK) return rc;
   const size_t K3 = (size_t)r.K * r.K * r.K;
   CK(dalloc(&pl->d_grid, K3));
@@ -659,7 +659,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 4 || spread_variant < -1 || spread_variant > 2) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 4 || spread_variant < -1 || spread_variant > 3) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -671,6 +671,7 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   const int S_new = points_per_subproblem > 0 ? points_per_subproblem : plan->pts_per_sub;
   if (gv == 3 && !nufft::v3_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   if (gv == 4 && !nufft::v4_supported(T, plan->J, S_new, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
+  if (sv == 3 && !nufft::v3s_supported(T, plan->J)) return NUFFT3D_ERR_UNSUPPORTED;
   int rc = ensure_device(plan);
   if (rc != NUFFT3D_OK) return rc;
   CK(cudaStreamSynchronize(plan->last_stream));

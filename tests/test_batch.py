@@ -36,7 +36,7 @@ def batch_run(cuda_lib, tmp_path_factory):
     assert len(works) == 24 and sorted({w.n for w in works}) == [64, 128, 192]
     b = cuda_lib.Batch(_items(works))
     cache = str(tmp_path_factory.mktemp("tune") / "tune.json")
-    chosen = autotune.tune_batch(b, candidates=((3, 2, 512, 8), (3, 2, 1024, 8), (2, 2, 1024, 8)),
+    chosen = autotune.tune_batch(b, candidates=((3, 3, 512, 8), (3, 2, 1024, 8), (2, 2, 1024, 8)),
                                  reps=1, cache=cache)
     assert len(chosen) == len({autotune.signature(p) for p in b.items})
     vols = [torch.from_numpy(w.volume(np.float32)).cuda() for w in works]

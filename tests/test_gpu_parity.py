@@ -178,7 +178,7 @@ def test_mid_workload_sampled_lines(cuda_lib):
 
 @pytest.mark.parametrize("gv,sv,pps,tile", [(0, 0, 1024, 8), (0, 0, 700, 16), (1, 1, 1024, 16), (1, 1, 300, 8),
                                             (2, 2, 1024, 8), (2, 2, 64, 8), (2, 2, 5000, 8), (3, 2, 1024, 8),
-                                            (3, 0, 2048, 16), (3, 2, 37, 8), (4, 2, 512, 8), (4, 2, 400, 8),
+                                            (3, 0, 2048, 16), (3, 2, 37, 8), (4, 2, 512, 8), (4, 2, 400, 8), (3, 3, 1024, 8), (4, 3, 512, 8), (0, 3, 77, 8),
                                             (4, 0, 300, 8)])
 def test_kernel_variants_and_subproblem_split(cuda_lib, gv, sv, pps, tile):
     """Every gather/spread variant, tile edge and subproblem size gives the same operator."""
@@ -222,7 +222,7 @@ def test_variant1_dense_center_and_repeat_calls(cuda_lib):
     dirs = I.umbrella_directions(90, 64)
     x = torch.from_numpy(I.random_volume(n, 14).astype(np.float32)).cuda()
     plan = cuda_lib.Plan(n, dirs)
-    assert plan.info()["spread_variant"] == 2  # the default for J = 6
+    assert plan.info()["spread_variant"] == 3  # the default for J = 6
     plan.tune(-1, -1, 2048)
     p1 = plan.forward(x).clone()
     p2 = plan.forward(x)
