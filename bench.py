@@ -378,31 +378,28 @@ def run_ours(args):
     # ---- end to end through pinned host buffers -------------------------
     e2e = None
     if not args.no_e2e:
+        from paper_1605_05231_gb300 import HostPipeline
+
         xh = torch.from_numpy(x).pin_memory()
         lh = torch.empty((plan.n_dirs, plan.m), dtype=torch.complex64).pin_memory()
         vh = torch.empty_like(xh).pin_memory()
-
-        def step_e2e():
-            xd.copy_(xh, non_blocking=True)
-            plan.forward(xd, out=lines)
-            lh.copy_(lines, non_blocking=True)
-            plan.adjoint(lines, out=vout)
-            vh.copy_(vout, non_blocking=True)
-
+        pipe = HostPipeline(plan)
         for _ in range(3):
-            step_e2e()
+            pipe.run(xh, lh, vh)
+        pipe.synchronize()
         n_e2e = max(3, min(args.steps, 20))
         barrier(world)
         torch.cuda.synchronize()
-        ev0.record(stream)
+        t0 = time.perf_counter()
         for _ in range(n_e2e):
-            step_e2e()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms_e2e = max_over_ranks(world, ev0.elapsed_time(ev1) / n_e2e)
+            pipe.run(xh, lh, vh)
+        pipe.synchronize()
+        ms_e2e = max_over_ranks(world, (time.perf_counter() - t0) * 1e3 / n_e2e)
         e2e = {"value": world * P / (ms_e2e * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(xh.numel() * 4),
-               "d2h_bytes_per_step": int(lh.numel() * 8 + vh.numel() * 4), "ms_per_step": ms_e2e}
+               "d2h_bytes_per_step": int(lh.numel() * 8 + vh.numel() * 4), "ms_per_step": ms_e2e,
+               "copies": "pinned host buffers; uploads and downloads on their own streams, overlapped with the kernels",
+               "timer": "host wall clock around the enqueue loop and the final synchronize"}
     if plan.sync_status() != 0:
         raise RuntimeError("device check failed")
 

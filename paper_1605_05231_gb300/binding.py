@@ -389,3 +389,60 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class HostPipeline:
+    """Forward + adjoint of volumes that live in (pinned) host memory, with the
+    host<->device copies overlapped with the projector's kernels.
+
+    Per call: the volume is copied in on an upload stream, forward runs on the
+    compute stream, the projections are copied out on a download stream while
+    the adjoint runs (both only read them), and the adjoint volume is copied out.
+    Double-buffered device inputs let the next call's upload overlap the
+    current call's kernels.  run() returns immediately; results are valid after
+    synchronize().
+    """
+
+    def __init__(self, plan: "Plan"):
+        import torch
+
+        self.plan = plan
+        dev = plan.device
+        self.compute = torch.cuda.Stream(dev)
+        self.upload = torch.cuda.Stream(dev)
+        self.download = torch.cuda.Stream(dev)
+        self.vol = [torch.empty((plan.n,) * 3, dtype=plan.vol_dtype, device=dev) for _ in range(2)]
+        self.lines = [torch.empty((plan.n_dirs, plan.m), dtype=torch.complex64, device=dev) for _ in range(2)]
+        self.vout = [torch.empty((plan.n,) * 3, dtype=plan.vol_dtype, device=dev) for _ in range(2)]
+        self.ev_free = [torch.cuda.Event() for _ in range(2)]
+        self.k = 0
+
+    def run(self, vol_host, lines_host, vout_host):
+        """Enqueue one forward + adjoint: vol_host -> lines_host, vout_host."""
+        import torch
+
+        b = self.k % 2
+        self.k += 1
+        up = torch.cuda.Event()
+        fwd_done = torch.cuda.Event()
+        adj_done = torch.cuda.Event()
+        with torch.cuda.stream(self.upload):
+            self.upload.wait_event(self.ev_free[b])
+            self.vol[b].copy_(vol_host, non_blocking=True)
+            up.record(self.upload)
+        self.compute.wait_event(up)
+        self.plan.forward(self.vol[b], out=self.lines[b], stream=self.compute)
+        fwd_done.record(self.compute)
+        self.plan.adjoint(self.lines[b], out=self.vout[b], stream=self.compute)
+        adj_done.record(self.compute)
+        with torch.cuda.stream(self.download):
+            self.download.wait_event(fwd_done)
+            lines_host.copy_(self.lines[b], non_blocking=True)
+            self.download.wait_event(adj_done)
+            vout_host.copy_(self.vout[b], non_blocking=True)
+            self.ev_free[b].record(self.download)
+
+    def synchronize(self):
+        self.compute.synchronize()
+        self.upload.synchronize()
+        self.download.synchronize()

@@ -59,6 +59,7 @@ int plan_adjoint_enqueue(nufft3d_plan pl, const void* lines, void* vol, cudaStre
 bool v3_supported(int T, int J, int S);
 bool v4_supported(int T, int J, int S, int L);
 bool v3s_supported(int T, int J);
+bool v4s_supported(int T, int J, int S);
 
 }  // namespace nufft
 

@@ -11,6 +11,7 @@
 // line together, so the stores are mostly coalesced runs.
 #include "common.cuh"
 #include "internal.h"
+#include "spread_taps.inc"
 
 namespace nufft {
 
@@ -853,6 +854,148 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
 }
 
 // ---------------------------------------------------------------------------
+// spread variant 4 (J = 6): one thread per point without atomics.  Each warp
+// owns a private E^3 tile.  The points of a subproblem are bucketed by the
+// residue of their first-tap offset modulo 32; in round r lane l spreads the
+// r-th point of bucket l, so the 32 points of a round have pairwise distinct
+// residues.  Taps are visited in groups of equal offset residue (the order in
+// spread_taps.inc): inside one group no two lanes touch the same cell and the
+// warp's accesses hit 32 distinct banks, so plain read-modify-writes are safe;
+// a __syncwarp separates the groups.
+// ---------------------------------------------------------------------------
+constexpr int V4S_WARPS = 10;
+
+__host__ __device__ inline size_t v4s_warp_bytes(int T, int S) {
+  const int E = T + 5;
+  const size_t w = (size_t)E * E * E * sizeof(float2) + (size_t)S * 2 * sizeof(int) + 96 * sizeof(int);
+  return (w + 15) / 16 * 16;
+}
+
+__host__ __device__ inline size_t v4s_bytes(int T, int S) { return V4S_WARPS * v4s_warp_bytes(T, S); }
+
+template <int E>
+__global__ void __launch_bounds__(V4S_WARPS * 32, 1) k_spread_v4(InterpGeom g, const float2* __restrict__ in,
+                                                                 const int4* __restrict__ subs, int n_subs, int S,
+                                                                 int* __restrict__ counter,
+                                                                 float2* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int T = E - 5;
+  constexpr int E3 = E * E * E;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nT = g.nT, K = g.K;
+  unsigned char* wb = smem_raw + warp * v4s_warp_bytes(T, S);
+  float2* tile = (float2*)wb;
+  int* order = (int*)(tile + E3);
+  int* p_off = order + S;
+  int* ncls = p_off + S;   // [32] counts
+  int* cur = ncls + 32;    // [32] cursors
+  for (int i = lane; i < E3; i += 32) tile[i] = make_float2(0.f, 0.f);
+  __syncwarp();
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(counter, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= n_subs) break;
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    const int cnt = sp.z;
+    ncls[lane] = 0;
+    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) {
+      const uint2 ent = g.sorted[sp.y + i];
+      int w0[3];
+      float f[3];
+      decode_point<6>(g, ent.x, w0, f);
+      const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+      int off = -1;
+      if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+        off = (lz * E + ly) * E + lx;
+        atomicAdd(&ncls[off & 31], 1);
+      } else {
+        atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+      }
+      p_off[i] = off;
+    }
+    __syncwarp();
+    const int my_n = ncls[lane];
+    int incl = my_n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int my_start = incl - my_n;
+    int rounds = my_n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
+    cur[lane] = my_start;
+    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) {
+      const int off = p_off[i];
+      if (off >= 0) order[atomicAdd(&cur[off & 31], 1)] = i;
+    }
+    __syncwarp();
+    for (int r = 0; r < rounds; ++r) {
+      const bool act = r < my_n;
+      int off = 0;
+      float2 cx[6], vyz[6][6];
+      if (act) {
+        const int i = order[my_start + r];
+        const uint2 ent = g.sorted[sp.y + i];
+        int w0[3];
+        float f[3];
+        decode_point<6>(g, ent.x, w0, f);
+        off = p_off[i];
+        float2 v = in[ent.x];
+        if (ent.y != kNoTwin) v = cadd(v, in[ent.y]);
+        float2 cy[6], cz[6];
+        table_coeffs_v4<6>(g.table, g.L, f[0], cx);
+        table_coeffs_v4<6>(g.table, g.L, f[1], cy);
+        table_coeffs_v4<6>(g.table, g.L, f[2], cz);
+#pragma unroll
+        for (int jz = 0; jz < 6; ++jz) {
+          const float2 vz = cmulc(v, cz[jz]);
+#pragma unroll
+          for (int jy = 0; jy < 6; ++jy) vyz[jy][jz] = cmulc(vz, cy[jy]);
+        }
+      }
+      float2* base = tile + off;
+#define NUFFT_SPREAD_TAP(jx, jy, jz, end)                                               \
+  if (act) {                                                                            \
+    float2* q = base + ((jx) + E * (jy) + E * E * (jz));                                \
+    float2 t = *q;                                                                      \
+    t.x = fmaf(vyz[jy][jz].x, cx[jx].x, fmaf(vyz[jy][jz].y, cx[jx].y, t.x));            \
+    t.y = fmaf(vyz[jy][jz].y, cx[jx].x, fmaf(-vyz[jy][jz].x, cx[jx].y, t.y));           \
+    *q = t;                                                                             \
+  }                                                                                     \
+  if (end) __syncwarp();
+      if constexpr (E == 13) {
+        NUFFT_SPREAD_TAPS_E13(NUFFT_SPREAD_TAP)
+      } else {
+        NUFFT_SPREAD_TAPS_E21(NUFFT_SPREAD_TAP)
+      }
+#undef NUFFT_SPREAD_TAP
+    }
+    __syncwarp();
+    for (int idx = lane; idx < E3; idx += 32) {
+      const float2 v = tile[idx];
+      if (v.x == 0.f && v.y == 0.f) continue;
+      tile[idx] = make_float2(0.f, 0.f);
+      const int ix = idx % E;
+      const int t = idx / E;
+      const int iy = t % E, iz = t / E;
+      int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      gz -= gz >= K ? K : 0;
+      atomicAdd(&grid[((size_t)gz * K + gy) * K + gx], v);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // variant 3 (gather, any J): one thread per point, with the points of a
 // subproblem reordered so that the 16 lanes of every half-warp hold points
 // whose first-tap offsets in the unpadded tile differ modulo 16 float2.  All
@@ -1196,6 +1339,10 @@ static int max_optin_smem() {
   return maxsm;
 }
 
+bool v4s_supported(int T, int J, int S) {
+  return J == 6 && T == 8 && v4s_bytes(T, S) <= (size_t)max_optin_smem();
+}
+
 bool v3s_supported(int T, int J) {
   return J == 6 && T == 8 && v3s_bytes(T) <= (size_t)max_optin_smem();
 }
@@ -1346,6 +1493,17 @@ static cudaError_t launch_spread_v0_t(const InterpGeom& g, const float2* in, con
 
 cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, const int4* subs, int n_subs,
                           float2* grid, cudaStream_t st) {
+  if (variant == 4 && v4s_supported(g.T, g.J, g.S)) {
+    auto f = k_spread_v4<13>;
+    const size_t smem = v4s_bytes(g.T, g.S);
+    cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (n_subs == 0) return cudaSuccess;
+    e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    f<<<num_sms(), V4S_WARPS * 32, smem, st>>>(g, in, subs, n_subs, g.S, g.counter + 1, grid);
+    return cudaGetLastError();
+  }
   if (variant == 3 && v3s_supported(g.T, g.J)) {
     auto f = k_spread_v3;
     const size_t smem = v3s_bytes(g.T);
