@@ -747,14 +747,47 @@ __device__ __forceinline__ void v3s_load(const float2* coef, const float4* mvs, 
   c.oz = cp[12 + ln.ojz];
 }
 
+// read-modify-write of one point's taps held by this lane
+template <int PP>
+__device__ __forceinline__ void v3s_apply(float2* tile, const V3SCoef& c, const V2Lanes& ln, int lane) {
+  const int mo = __float_as_int(c.mv.x);
+  if (mo < 0) return;
+  const float2 v = make_float2(c.mv.y, c.mv.z);
+  const float2 a = cmulc(v, cmul(c.cx, c.cy));  // v conj(cx cy)
+  float2* tp = tile + mo + ln.main_off;
+  float2 t[6];
+#pragma unroll
+  for (int jz = 0; jz < 6; ++jz) t[jz] = tp[jz * PP];
+  const float2 cz[6] = {make_float2(c.z01.x, c.z01.y), make_float2(c.z01.z, c.z01.w),
+                        make_float2(c.z23.x, c.z23.y), make_float2(c.z23.z, c.z23.w),
+                        make_float2(c.z45.x, c.z45.y), make_float2(c.z45.z, c.z45.w)};
+#pragma unroll
+  for (int jz = 0; jz < 6; ++jz) {
+    t[jz].x = fmaf(a.x, cz[jz].x, fmaf(a.y, cz[jz].y, t[jz].x));
+    t[jz].y = fmaf(a.y, cz[jz].x, fmaf(-a.x, cz[jz].y, t[jz].y));
+  }
+#pragma unroll
+  for (int jz = 0; jz < 6; ++jz) tp[jz * PP] = t[jz];
+  if (lane < 24) {
+    const float2 w = cmulc(v, cmul(cmul(c.ox, c.oy), c.oz));
+    float2* q = tile + mo + ln.ovf_off;
+    float2 u = *q;
+    u.x += w.x;
+    u.y += w.y;
+    *q = u;
+  }
+}
+
+template <int T>
 __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, const float2* __restrict__ in,
                                                                  const int4* __restrict__ subs, int n_subs,
                                                                  int* __restrict__ counter,
                                                                  float2* __restrict__ grid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int E = T + 5, E2 = E * E, E3 = E2 * E, PP = E2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int T = g.T, nT = g.nT, K = g.K;
-  const int E = T + 5, E3 = E * E * E, PP = E * E;
+  const int nT = g.nT, K = g.K;
+  const size_t KK = (size_t)K * K;
   float2* coef = (float2*)(smem_raw + warp * v3s_warp_bytes(T));
   float4* mvs = (float4*)(coef + 32 * V2_CSTRIDE);
   float2* tile = (float2*)(mvs + 32);
@@ -799,55 +832,42 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
       mvs[lane] = make_float4(__int_as_float(off), val.x, val.y, 0.f);
       __syncwarp();
       const int np = min(32, sp.z - b0);
-      V3SCoef cur;
-      v3s_load(coef, mvs, 0, ln, cur);
-      for (int p = 0; p < np; ++p) {
-        V3SCoef nxt;
-        if (p + 1 < np) v3s_load(coef, mvs, p + 1, ln, nxt);
-        const int mo = __float_as_int(cur.mv.x);
-        if (mo >= 0) {
-          const float2 v = make_float2(cur.mv.y, cur.mv.z);
-          const float2 a = cmulc(v, cmul(cur.cx, cur.cy));  // v conj(cx cy)
-          float2* tp = tile + mo + ln.main_off;
-          float2 t[6];
-#pragma unroll
-          for (int jz = 0; jz < 6; ++jz) t[jz] = tp[jz * PP];
-          const float2 cz[6] = {make_float2(cur.z01.x, cur.z01.y), make_float2(cur.z01.z, cur.z01.w),
-                                make_float2(cur.z23.x, cur.z23.y), make_float2(cur.z23.z, cur.z23.w),
-                                make_float2(cur.z45.x, cur.z45.y), make_float2(cur.z45.z, cur.z45.w)};
-#pragma unroll
-          for (int jz = 0; jz < 6; ++jz) {
-            t[jz].x = fmaf(a.x, cz[jz].x, fmaf(a.y, cz[jz].y, t[jz].x));
-            t[jz].y = fmaf(a.y, cz[jz].x, fmaf(-a.x, cz[jz].y, t[jz].y));
-          }
-#pragma unroll
-          for (int jz = 0; jz < 6; ++jz) tp[jz * PP] = t[jz];
-          if (lane < 24) {
-            const float2 w = cmulc(v, cmul(cmul(cur.ox, cur.oy), cur.oz));
-            float2* q = tile + mo + ln.ovf_off;
-            float2 u = *q;
-            u.x += w.x;
-            u.y += w.y;
-            *q = u;
-          }
-        }
+      // two points per iteration: the second point's coefficients load while
+      // the first point's read-modify-writes drain
+      int p = 0;
+      for (; p + 1 < np; p += 2) {
+        V3SCoef c0, c1;
+        v3s_load(coef, mvs, p, ln, c0);
+        v3s_load(coef, mvs, p + 1, ln, c1);
+        v3s_apply<PP>(tile, c0, ln, lane);
         __syncwarp();
-        cur = nxt;
+        v3s_apply<PP>(tile, c1, ln, lane);
+        __syncwarp();
       }
-      __syncwarp();
+      if (p < np) {
+        V3SCoef c0;
+        v3s_load(coef, mvs, p, ln, c0);
+        v3s_apply<PP>(tile, c0, ln, lane);
+        __syncwarp();
+      }
     }
-    for (int idx = lane; idx < E3; idx += 32) {
-      const float2 v = tile[idx];
-      if (v.x == 0.f && v.y == 0.f) continue;
-      tile[idx] = make_float2(0.f, 0.f);
-      const int ix = idx % E;
-      const int t = idx / E;
-      const int iy = t % E, iz = t / E;
-      int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+    // add the tile to the grid: lanes walk (y, x) columns, each column along z
+    for (int c = lane; c < E2; c += 32) {
+      const int iy = c / E, ix = c - iy * E;
+      int gx = x0 + ix, gy = y0 + iy;
       gx -= gx >= K ? K : 0;
       gy -= gy >= K ? K : 0;
-      gz -= gz >= K ? K : 0;
-      atomicAdd(&grid[((size_t)gz * K + gy) * K + gx], v);
+      int gz = z0;
+      float2* cell = tile + c;
+#pragma unroll
+      for (int iz = 0; iz < E; ++iz) {
+        const float2 v = cell[iz * E2];
+        if (v.x != 0.f || v.y != 0.f) {
+          cell[iz * E2] = make_float2(0.f, 0.f);
+          atomicAdd(&grid[((size_t)(gz >= K ? gz - K : gz)) * KK + (size_t)gy * K + gx], v);
+        }
+        ++gz;
+      }
     }
     __syncwarp();
   }
@@ -1505,7 +1525,7 @@ cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, co
     return cudaGetLastError();
   }
   if (variant == 3 && v3s_supported(g.T, g.J)) {
-    auto f = k_spread_v3;
+    auto f = k_spread_v3<8>;
     const size_t smem = v3s_bytes(g.T);
     cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
