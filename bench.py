@@ -164,7 +164,7 @@ def load_peaks():
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("interp.cu", "common.cuh"):
+    for fn in ("interp_common.cuh", "interp_gather.cu", "interp_spread.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1605_05231_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

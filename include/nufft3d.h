@@ -141,7 +141,10 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
  * warp-private tile, no shared atomics (J = 6, T = 8; the default spread
  * when available); gather only: 3 one thread per point, points reordered so
  * that every half-warp's tile accesses fall in distinct banks (any J; the
- * default gather).  T is 4, 8 or 16; changing it re-sorts the points.
+ * default gather), 4 the same with the table in shared memory, 5 the same as 3
+ * with 128-thread CTAs; spread only: 3 variant 2 with ten warps per SM and
+ * the table read through L1 (the default spread), 4 one thread per point in
+ * rounds of pairwise distinct tile-offset residues (no atomics).  T is 4, 8 or 16; changing it re-sorts the points.
  * Synchronises the plan's last stream and works on cuda_stream.  Returns
  * NUFFT3D_ERR_UNSUPPORTED for a combination the plan cannot run.  Used by
  * the autotuner. */

@@ -17,7 +17,11 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnufft3d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cu", "fft_passes.cu", "interp.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["plan.cu", "fft_passes.cu", "interp_gather.cu", "interp_spread.cu", "noalloc.cu", "batch.cu"]
+# nvcc's whole-TU code generation (--split-compile=0) schedules the gather
+# kernels better and the shared-atomic spread kernels worse (both measured with
+# CUDA events at 256^3), so it is applied per translation unit.
+NO_SPLIT_COMPILE = {"interp_spread.cu"}
 
 
 def nvcc_path() -> str:
@@ -27,14 +31,16 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libnufft3d")
 
 
-def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
+def _flags(src: str, extra=()):
+    split = [] if src in NO_SPLIT_COMPILE or os.environ.get("NUFFT3D_SPLIT_COMPILE", "1") == "0" \
+        else ["--split-compile=0"]
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", *split, "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
                    "-I", os.path.join(ROOT, "include"), *extra]
 
 
 def _compile(src: str, extra=()) -> str:
     obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
-    cmd = [nvcc_path(), *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc_path(), *_flags(src, extra), "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -659,7 +659,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 4 || spread_variant < -1 || spread_variant > 4) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 5 || spread_variant < -1 || spread_variant > 4) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -669,7 +669,8 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   if ((gv == 2 || sv == 2) && !nufft::v2_supported(T, plan->J, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
   if ((gv == 1 || sv == 1) && plan->J != 6) return NUFFT3D_ERR_UNSUPPORTED;
   const int S_new = points_per_subproblem > 0 ? points_per_subproblem : plan->pts_per_sub;
-  if (gv == 3 && !nufft::v3_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
+  if ((gv == 3 || gv == 5) && !nufft::v3_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
+  if (gv == 5 && T != 8) return NUFFT3D_ERR_UNSUPPORTED;
   if (gv == 4 && !nufft::v4_supported(T, plan->J, S_new, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 3 && !nufft::v3s_supported(T, plan->J)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 4 && !nufft::v4s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;

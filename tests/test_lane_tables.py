@@ -7,7 +7,7 @@ import re
 import pytest
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1605_05231_gb300", "csrc",
-                   "interp.cu")
+                   "interp_common.cuh")
 
 
 def _table(name):
