@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--points-per-subproblem", type=int, default=0)
     ap.add_argument("--tile-edge", type=int, default=0)
     ap.add_argument("--keep-duplicates", action="store_true")
+    ap.add_argument("--coeffs", default="table", choices=["table", "exact"],
+                    help="min-max coefficients from the L = 1024 table, or exact per point (fitted polynomials)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-lines", type=int, default=4000)
@@ -230,6 +232,24 @@ def max_over_ranks(world, v: float) -> float:
 # ----------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------
+def bench_workload(args):
+    """The named workload; --coeffs exact selects exact per-point coefficients
+    (table_oversamp 0, the oracle's L = 0 variant)."""
+    import dataclasses
+
+    from paper_1605_05231_gb300 import inputs as I
+
+    w = I.workload(args.workload)
+    return dataclasses.replace(w, table_oversamp=0) if args.coeffs == "exact" else w
+
+
+def coeff_desc(w, info=None):
+    if w.table_oversamp:
+        return f"table, L = {w.table_oversamp}, linear interpolation"
+    err = f", fit error {info['coeff_fit_error']:.1e} of max|c|" if info else ""
+    return f"exact min-max per point (degree-8 polynomials fitted in FP64{err})"
+
+
 def oracle_fixed(w, x, dirs):
     """Time the oracle's size-fixed stages at full size: deapodise + pad + K^3
     FFT (forward) and K^3 inverse FFT + crop + deapodise (adjoint)."""
@@ -293,7 +313,7 @@ def run_reference(args):
 
     from paper_1605_05231_gb300 import inputs as I
 
-    w = I.workload(args.workload)
+    w = bench_workload(args)
     dirs = w.directions()
     x = w.volume(np.float32)
     op, Y, t_fixed = oracle_fixed(w, x, dirs)
@@ -313,7 +333,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "table_oversamp": w.table_oversamp,
+            "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "coefficients": coeff_desc(w),
                        "dirs": f"{w.n_az}x{w.n_pol}", "m": w.m, "points": P},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
@@ -331,11 +351,12 @@ def run_ours(args):
 
     world, rank, local = dist_setup(args)
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = I.workload(args.workload)
+    w = bench_workload(args)
     dirs = w.directions()
     x = w.volume(np.float32)
     t0 = time.perf_counter()
-    plan = Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp, grid_dtype=args.grid_dtype,
+    plan = Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp or 1024,
+                exact_coeffs=w.table_oversamp == 0, grid_dtype=args.grid_dtype,
                 keep_duplicates=args.keep_duplicates)
     plan.tune(args.gather_variant, args.spread_variant, args.points_per_subproblem, args.tile_edge)
     torch.cuda.synchronize()
@@ -451,7 +472,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.grid_dtype == "c64" else f"f32+{args.grid_dtype} grid",
                 "data": "synthetic",
-                "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "table_oversamp": w.table_oversamp,
+                "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "coefficients": coeff_desc(w, info),
                            "dirs": f"{w.n_az}x{w.n_pol}", "m": w.m, "points": P, "grid_dtype": args.grid_dtype,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "working set per step >> L2 (1.07 GB grid, 0.38 GB lines, 0.19 GB point ids)",
@@ -479,8 +500,8 @@ def run_batch(args):
     world, rank, local = dist_setup(args)
     dev = torch.device("cuda", torch.cuda.current_device())
     works = I.batched_workloads()
-    items = [dict(n=w.n, dirs=w.directions(), m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp)
-             for w in works]
+    items = [dict(n=w.n, dirs=w.directions(), m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp,
+                  exact_coeffs=args.coeffs == "exact") for w in works]
     t0 = time.perf_counter()
     b = Batch(items)
     tuned = autotune.tune_batch(b, reps=2, cache=None)
@@ -516,6 +537,7 @@ def run_batch(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "batch24", "items": [f"{w.n}^3 {w.n_az}x{w.n_pol}x{w.m}" for w in works],
+                           "coefficients": "exact min-max per point" if args.coeffs == "exact" else "table, L = 1024",
                            "points": P, "graph_launches_per_step": 1},
                 "clocks": clk, "autotune": {k: v["best"] for k, v in tuned.items()}, "plan_s": plan_s}
         print(json.dumps(line), flush=True)

@@ -90,6 +90,13 @@ typedef struct {
                              -line l within 1e-13, radius -r) is interpolated once and
                              its value shared (the partner direction is snapped to the
                              exact negation); 1: every sample separately           */
+  int exact_coeffs;       /* 0: coefficients linearly interpolated from the table of
+                             L + 1 rows c(i / L); 1: the exact min-max coefficients
+                             c(f) = T^-1 r(f) at each point's own f (table_oversamp is
+                             ignored).  The plan fits each c_j by a degree-8 Chebyshev
+                             interpolant in FP64 and evaluates it per point in FP32;
+                             a fit further than 1e-7 max|c| from c is refused with
+                             NUFFT3D_ERR_UNSUPPORTED (plan_info reports the error) */
 } nufft3d_params;
 
 /* Create a plan.  Validates *p, computes in FP64 on the host the scaling
@@ -128,10 +135,12 @@ int nufft3d_plan_destroy(nufft3d_plan plan);
 /* Static description of a status code (never NULL). */
 const char* nufft3d_error_string(int status);
 
-/* Numbers of the plan; out must hold 10 ints: tile edge T, tiles per axis,
+/* Numbers of the plan; out must hold 12 ints: tile edge T, tiles per axis,
  * subproblems, gather variant, spread variant, points per subproblem,
  * non-empty tiles, most points in one tile, evaluated points (samples after
- * merging coincident ones), merged antipodal line pairs.  For tests and tuning. */
+ * merging coincident ones), merged antipodal line pairs, exact_coeffs, and the
+ * coefficient polynomials' largest error relative to max|c| in units of 1e-12
+ * (rounded up; 0 with a table).  For tests and tuning. */
 int nufft3d_plan_info(nufft3d_plan plan, int* out);
 
 /* Select the gather and spread kernel variants, the number of points per

@@ -3,8 +3,8 @@
 For a plan it times forward + adjoint with CUDA events for each candidate
 (gather variant, spread variant, points per subproblem, tile edge), keeps the
 fastest, applies it with Plan.tune and caches the choice in a JSON file keyed
-by the problem signature (N, K, J, M, number of lines, grid dtype, volume type,
-GPU name).  Candidates a plan cannot run (NUFFT3D_ERR_UNSUPPORTED) are skipped.
+by the problem signature (N, K, J, M, number of lines, volume type, grid dtype,
+coefficient mode, GPU name).  Candidates a plan cannot run (NUFFT3D_ERR_UNSUPPORTED) are skipped.
 """
 from __future__ import annotations
 
@@ -39,7 +39,7 @@ def signature(plan) -> str:
     info = plan.info()
     name = torch.cuda.get_device_name(plan.device)
     return (f"N{plan.n}_K{plan.k}_J{plan.j}_M{plan.m}_D{plan.n_dirs}_"
-            f"{'c' if plan.complex_volume else 'r'}_{plan.grid_dtype}_{name}")
+            f"{'c' if plan.complex_volume else 'r'}_{plan.grid_dtype}_{'x' if plan.exact_coeffs else 't'}_{name}")
 
 
 def _load(path):

@@ -60,6 +60,7 @@ class Params(ctypes.Structure):
         ("complex_volume", ctypes.c_int),
         ("do_line_fft", ctypes.c_int),
         ("keep_duplicates", ctypes.c_int),
+        ("exact_coeffs", ctypes.c_int),
     ]
 
 
@@ -125,7 +126,7 @@ def _check(rc: int, what: str):
 
 
 def make_params(n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=None, grid_dtype="c64",
-                complex_volume=False, do_line_fft=True, keep_duplicates=False):
+                complex_volume=False, do_line_fft=True, keep_duplicates=False, exact_coeffs=False):
     """Build a Params struct plus the host arrays it points to (kept alive by the caller)."""
     dirs = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
     keep = [dirs]
@@ -150,6 +151,7 @@ def make_params(n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=
     p.complex_volume = 1 if complex_volume else 0
     p.do_line_fft = 1 if do_line_fft else 0
     p.keep_duplicates = 1 if keep_duplicates else 0
+    p.exact_coeffs = int(exact_coeffs)
     return p, keep
 
 
@@ -176,8 +178,8 @@ class Plan:
     """
 
     def __init__(self, n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=None,
-                 grid_dtype="c64", complex_volume=False, do_line_fft=True, keep_duplicates=False, device=None,
-                 stream=None, _handle=None):
+                 grid_dtype="c64", complex_volume=False, do_line_fft=True, keep_duplicates=False,
+                 exact_coeffs=False, device=None, stream=None, _handle=None):
         import torch
 
         self.lib = load_library()
@@ -185,7 +187,7 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         p, keep = make_params(n, dirs, m, k, j, table_oversamp, omega, weight, grid_dtype, complex_volume,
-                              do_line_fft, keep_duplicates)
+                              do_line_fft, keep_duplicates, exact_coeffs)
         self.n = int(n)
         self.n_dirs = p.n_dirs
         self.m = int(m) if m else 2 * int(n)
@@ -194,6 +196,7 @@ class Plan:
         self.complex_volume = bool(complex_volume)
         self.do_line_fft = bool(do_line_fft)
         self.grid_dtype = str(grid_dtype)
+        self.exact_coeffs = bool(exact_coeffs)
         self._handle = ctypes.c_void_p()
         if _handle is not None:
             self._handle = _handle
@@ -259,12 +262,14 @@ class Plan:
         return int(v.value)
 
     def info(self) -> dict:
-        a = (ctypes.c_int * 10)()
+        a = (ctypes.c_int * 12)()
         _check(self.lib.nufft3d_plan_info(self._handle, a), "nufft3d_plan_info")
         keys = ("tile", "tiles_per_axis", "subproblems", "gather_variant", "spread_variant",
                 "points_per_subproblem", "nonempty_tiles", "max_tile_points", "evaluated_points",
-                "merged_line_pairs")
-        return dict(zip(keys, list(a)))
+                "merged_line_pairs", "exact_coeffs")
+        d = dict(zip(keys, list(a)))
+        d["coeff_fit_error"] = a[11] * 1e-12
+        return d
 
     def tune(self, gather_variant=-1, spread_variant=-1, points_per_subproblem=0, tile_edge=0, stream=None):
         """Pick kernel variants (0, 1, 2), points per subproblem and tile edge (-1 / 0 keep)."""

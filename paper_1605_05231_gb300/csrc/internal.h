@@ -13,6 +13,17 @@ namespace nufft {
 
 constexpr uint32_t kNoTwin = 0xffffffffu;
 
+// Exact min-max coefficients without a table: each c_j(f), f in [0, 1], is
+// replaced by its degree-kPolyDeg Chebyshev interpolant (fitted in FP64 at plan
+// time), stored as monomials in t = 2 f - 1 and evaluated per point by Horner's
+// rule.  The coefficients travel in the kernel parameters, so every lane reads
+// them through the constant bank.
+constexpr int kPolyDeg = 8;
+constexpr int kPolyMaxJ = 8;
+struct CoefPoly {
+  float a[kPolyMaxJ][2][kPolyDeg + 1];  // [tap][re, im][power of t]
+};
+
 // point-to-tile binning and the interpolation kernels' view of a plan
 struct InterpGeom {
   int K, J, L, T, nT, M, D;
@@ -24,6 +35,7 @@ struct InterpGeom {
   int* counter;          // two work counters (gather, spread) for the persistent variants
   int S;                 // most points in one subproblem
   const float* lp_bound; // bound on |Y| for a reduced-precision grid (else null)
+  CoefPoly poly;         // coefficient polynomials (used when L == 0)
 };
 
 bool fft_length_supported(int L);
@@ -68,8 +80,10 @@ constexpr int ADJ_STAGES = 6;  // line DFT, grid clear, spread, z pass, y pass, 
 
 struct nufft3d_plan_s {
   // resolved parameters
-  int N, K, J, L, D, M;
+  int N, K, J, L, D, M;  // L = 0: exact coefficients from the fitted polynomials
   long long P;
+  nufft::CoefPoly poly{};
+  double poly_err = 0.0;  // max |fit - exact| / max |c| of the polynomials (0 with a table)
   int complex_volume, do_line_fft, grid_dtype;
   int T, nT;  // tile edge and tiles per axis
   int gather_variant, spread_variant, pts_per_sub;

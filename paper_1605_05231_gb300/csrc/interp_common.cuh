@@ -36,6 +36,34 @@ static inline int num_sms() {
   return g_num_sms;
 }
 
+// Min-max coefficients of the J taps of one axis at fractional offset f from
+// the fitted polynomials: Horner's rule in t = 2 f - 1, coefficients read from
+// the kernel parameters (uniform over the warp).
+template <int J>
+__device__ __forceinline__ void poly_coeffs(const CoefPoly& P, float f, float2 (&c)[J]) {
+  const float t = fmaf(2.f, f, -1.f);
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    float re = P.a[j][0][kPolyDeg], im = P.a[j][1][kPolyDeg];
+#pragma unroll
+    for (int q = kPolyDeg - 1; q >= 0; --q) {
+      re = fmaf(re, t, P.a[j][0][q]);
+      im = fmaf(im, t, P.a[j][1][q]);
+    }
+    c[j] = make_float2(re, im);
+  }
+}
+
+// Coefficients of one axis: the table's linear interpolation (L > 0) or the
+// exact coefficients' polynomials (L == 0); the branch is uniform per launch.
+template <int J>
+__device__ __forceinline__ void point_coeffs(const InterpGeom& g, float f, float2 (&c)[J]) {
+  if (g.L == 0)
+    poly_coeffs<J>(g.poly, f, c);
+  else
+    table_coeffs_v4<J>(g.table, g.L, f, c);
+}
+
 template <typename G>
 __device__ __forceinline__ float lp_inv_scale(const InterpGeom& g) {
   if constexpr (G::kLowPrecision) return 1.f / lp_scale_from_bound(*g.lp_bound);
@@ -251,7 +279,7 @@ static inline int max_optin_smem() {
 }
 
 static inline bool v1_fits(const InterpGeom& g) {
-  if (g.J != 6) return false;
+  if (g.J != 6 || g.L == 0) return false;
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

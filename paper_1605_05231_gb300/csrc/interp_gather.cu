@@ -41,9 +41,9 @@ __global__ void __launch_bounds__(256) k_gather_v0(InterpGeom g, const typename 
       continue;
     }
     float2 cx[J], cy[J], cz[J];
-    table_coeffs<J>(g.table, g.L, f[0], cx);
-    table_coeffs<J>(g.table, g.L, f[1], cy);
-    table_coeffs<J>(g.table, g.L, f[2], cz);
+    point_coeffs<J>(g, f[0], cx);
+    point_coeffs<J>(g, f[1], cy);
+    point_coeffs<J>(g, f[2], cz);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int jz = 0; jz < J; ++jz) {
@@ -263,7 +263,7 @@ __host__ __device__ inline V3Layout v3_layout(int T, int J, int S, int elem) {
 }
 
 template <int J, int T, int NT, typename G>
-__global__ void __launch_bounds__(NT) k_gather_v3(InterpGeom g, const typename G::T* __restrict__ grid,
+__global__ void __launch_bounds__(NT, J <= 6 ? 1024 / NT : 1) k_gather_v3(InterpGeom g, const typename G::T* __restrict__ grid,
                                                   float inv_scale, const int4* __restrict__ subs, int S,
                                                   float2* __restrict__ out) {
   typedef typename G::T TT;
@@ -339,9 +339,9 @@ __global__ void __launch_bounds__(NT) k_gather_v3(InterpGeom g, const typename G
     const int off = p_off[i];
     if (off < 0) continue;
     float2 cx[J], cy[J], cz[J];
-    table_coeffs_v4<J>(g.table, g.L, p_f[i], cx);
-    table_coeffs_v4<J>(g.table, g.L, p_f[S + i], cy);
-    table_coeffs_v4<J>(g.table, g.L, p_f[2 * S + i], cz);
+    point_coeffs<J>(g, p_f[i], cx);
+    point_coeffs<J>(g, p_f[S + i], cy);
+    point_coeffs<J>(g, p_f[2 * S + i], cz);
     float2 acc = make_float2(0.f, 0.f);
     const TT* base = tile + off;
 #pragma unroll
@@ -582,7 +582,7 @@ static cudaError_t launch_gather_v3_j(const InterpGeom& g, int nt, int dtype, co
 
 
 bool v4_supported(int T, int J, int S, int L) {
-  return v4_bytes(T, J, S, L, 8) <= (size_t)max_optin_smem();
+  return L > 0 && v4_bytes(T, J, S, L, 8) <= (size_t)max_optin_smem();
 }
 
 bool v3_supported(int T, int J, int S) {

@@ -64,9 +64,9 @@ __global__ void __launch_bounds__(256) k_spread_v0(InterpGeom g, const float2* _
     float2 v = in[id];
     if (ent.y != kNoTwin) v = cadd(v, in[ent.y]);
     float2 cx[J], cy[J], cz[J];
-    table_coeffs<J>(g.table, g.L, f[0], cx);
-    table_coeffs<J>(g.table, g.L, f[1], cy);
-    table_coeffs<J>(g.table, g.L, f[2], cz);
+    point_coeffs<J>(g, f[0], cx);
+    point_coeffs<J>(g, f[1], cy);
+    point_coeffs<J>(g, f[2], cz);
 #pragma unroll
     for (int jz = 0; jz < J; ++jz) {
       const float2 vz = cmulc(v, cz[jz]);
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             float2 c[6];
-            table_coeffs_v4<6>(g.table, g.L, f[a], c);
+            point_coeffs<6>(g, f[a], c);
 #pragma unroll
             for (int q = 0; q < 3; ++q) c4[a * 3 + q] = make_float4(c[2 * q].x, c[2 * q].y, c[2 * q + 1].x, c[2 * q + 1].y);
           }
@@ -510,9 +510,9 @@ __global__ void __launch_bounds__(V4S_WARPS * 32, 1) k_spread_v4(InterpGeom g, c
         float2 v = in[ent.x];
         if (ent.y != kNoTwin) v = cadd(v, in[ent.y]);
         float2 cy[6], cz[6];
-        table_coeffs_v4<6>(g.table, g.L, f[0], cx);
-        table_coeffs_v4<6>(g.table, g.L, f[1], cy);
-        table_coeffs_v4<6>(g.table, g.L, f[2], cz);
+        point_coeffs<6>(g, f[0], cx);
+        point_coeffs<6>(g, f[1], cy);
+        point_coeffs<6>(g, f[2], cz);
 #pragma unroll
         for (int jz = 0; jz < 6; ++jz) {
           const float2 vz = cmulc(v, cz[jz]);
@@ -564,7 +564,7 @@ bool v3s_supported(int T, int J) {
 }
 
 bool v2_supported(int T, int J, int L) {
-  return J == 6 && (T == 8 || T == 16) && v2_layout(T, L).bytes <= (size_t)max_optin_smem();
+  return L > 0 && J == 6 && (T == 8 || T == 16) && v2_layout(T, L).bytes <= (size_t)max_optin_smem();
 }
 
 static cudaError_t launch_spread_v1(const InterpGeom& g, const float2* in, const int4* subs, int n_subs,

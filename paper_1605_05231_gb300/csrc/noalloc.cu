@@ -93,6 +93,7 @@ extern "C" int nufft3d_adjoint_noalloc(nufft3d_plan pl, const void* lines_dev, v
   g.counter = counter;
   g.S = pl->pts_per_sub;
   g.lp_bound = pl->d_lp_bound;
+  g.poly = pl->poly;
 
   const float2* src = (const float2*)lines_dev;
   if (pl->do_line_fft) {

@@ -20,7 +20,7 @@ typedef std::complex<double> cd;
 namespace {
 
 struct Resolved {
-  int N, K, J, L, D, M, grid_dtype, cplx, line_fft, keep_dup;
+  int N, K, J, L, D, M, grid_dtype, cplx, line_fft, keep_dup, exact;
   long long P;
   int T, nT;
 };
@@ -41,11 +41,14 @@ int resolve(const nufft3d_params* p, Resolved& r) {
   r.cplx = p->complex_volume ? 1 : 0;
   r.line_fft = p->do_line_fft ? 1 : 0;
   r.keep_dup = p->keep_duplicates ? 1 : 0;
+  r.exact = p->exact_coeffs;
+  if (r.exact < 0 || r.exact > 1) return NUFFT3D_ERR_ARG;
   if (r.N < 8 || r.N > kMaxEdge || (r.N & 1)) return NUFFT3D_ERR_ARG;
   if (r.K < r.N || r.K > kMaxEdge) return NUFFT3D_ERR_ARG;
   if (r.J < 2 || r.J > 8) return NUFFT3D_ERR_ARG;
   if (r.J & 1) return NUFFT3D_ERR_UNSUPPORTED;
   if (!is_pow2(r.L) || r.L < 2 || r.L > 65536) return NUFFT3D_ERR_ARG;
+  if (r.exact) r.L = 0;  // no table: the kernels evaluate the fitted polynomials
   if (r.M < 2 || (r.M & 1) || r.M > 1 << 20) return NUFFT3D_ERR_ARG;
   if (r.D < 1) return NUFFT3D_ERR_ARG;
   if (!p->dirs) return NUFFT3D_ERR_ARG;
@@ -126,6 +129,8 @@ struct HostTables {
   std::vector<float2> dir;      // D * 3 (hi, lo)
   std::vector<float2> rad;      // M (hi, lo)
   std::vector<float2> weight;   // M or empty
+  nufft::CoefPoly poly{};       // exact-coefficient mode (L = 0)
+  double poly_err = 0.0;
 };
 
 float2 split(double v) {
@@ -134,7 +139,63 @@ float2 split(double v) {
   return make_float2(hi, lo);
 }
 
-bool build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
+// Degree-kPolyDeg Chebyshev interpolant of each c_j on f in [0, 1] (nodes
+// t_i = cos(pi (i + 1/2) / (D + 1)), f = (t + 1) / 2), converted to monomials in
+// t and rounded to FP32.  The FP32 coefficients are then checked against the
+// exact c on 1025 evenly spaced f; the largest error relative to max |c| is
+// kept for plan_info, and a fit above 1e-7 is refused.
+template <class F>
+int fit_coeff_polys(int J, F&& coeffs_at, HostTables& h) {
+  constexpr int D = nufft::kPolyDeg, n = D + 1;
+  std::vector<cd> cv((size_t)n * J);
+  for (int i = 0; i < n; ++i) {
+    const double t = std::cos(M_PI * (i + 0.5) / n);
+    coeffs_at(0.5 * (t + 1.0), cv.data() + (size_t)i * J);
+  }
+  // Chebyshev coefficients b_k = (2 - [k = 0]) / n sum_i c(t_i) T_k(t_i)
+  std::vector<cd> b((size_t)n * J, cd(0, 0));
+  for (int k = 0; k < n; ++k)
+    for (int i = 0; i < n; ++i) {
+      const double tk = std::cos(M_PI * k * (i + 0.5) / n);
+      for (int j = 0; j < J; ++j) b[(size_t)k * J + j] += cv[(size_t)i * J + j] * tk;
+    }
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < J; ++j) b[(size_t)k * J + j] *= (k == 0 ? 1.0 : 2.0) / n;
+  // monomial coefficients of T_k: T_0 = 1, T_1 = t, T_k = 2 t T_{k-1} - T_{k-2}
+  std::vector<double> Tm((size_t)n * n, 0.0);
+  Tm[0] = 1.0;
+  if (n > 1) Tm[(size_t)n + 1] = 1.0;
+  for (int k = 2; k < n; ++k)
+    for (int q = 0; q < n; ++q)
+      Tm[(size_t)k * n + q] = (q > 0 ? 2.0 * Tm[(size_t)(k - 1) * n + q - 1] : 0.0) - Tm[(size_t)(k - 2) * n + q];
+  h.poly = nufft::CoefPoly{};
+  for (int j = 0; j < J; ++j)
+    for (int q = 0; q < n; ++q) {
+      cd m = 0;
+      for (int k = q; k < n; ++k) m += b[(size_t)k * J + j] * Tm[(size_t)k * n + q];
+      h.poly.a[j][0][q] = (float)m.real();
+      h.poly.a[j][1][q] = (float)m.imag();
+    }
+  double err = 0.0, cmax = 0.0;
+  std::vector<cd> ce(J);
+  for (int i = 0; i <= 1024; ++i) {
+    const double f = i / 1024.0, t = 2.0 * f - 1.0;
+    coeffs_at(f, ce.data());
+    for (int j = 0; j < J; ++j) {
+      double re = h.poly.a[j][0][D], im = h.poly.a[j][1][D];
+      for (int q = D - 1; q >= 0; --q) {
+        re = re * t + h.poly.a[j][0][q];
+        im = im * t + h.poly.a[j][1][q];
+      }
+      err = std::max(err, std::abs(cd(re, im) - ce[j]));
+      cmax = std::max(cmax, std::abs(ce[j]));
+    }
+  }
+  h.poly_err = err / cmax;
+  return h.poly_err <= 1e-7 ? NUFFT3D_OK : NUFFT3D_ERR_UNSUPPORTED;
+}
+
+int build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
   const int N = r.N, K = r.K, J = r.J, L = r.L;
   const double alpha = 2.34 * J;
   const double gam = 2.0 * M_PI / K;
@@ -158,12 +219,10 @@ bool build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
       }
       T[a * J + b] = acc;
     }
-  if (!invert(T, J)) return false;
-  // table: c(f_i) = T^{-1} r(f_i), r_j(f) = sum_n s(n) e^{-i gam (f + J/2 - j) n}, j = 1..J
-  h.table.resize((size_t)(L + 1) * J);
+  if (!invert(T, J)) return NUFFT3D_ERR_ARG;
+  // c(f) = T^{-1} r(f), r_j(f) = sum_n s(n) e^{-i gam (f + J/2 - j) n}, j = 1..J
   std::vector<cd> rv(J);
-  for (int t = 0; t <= L; ++t) {
-    const double f = (double)t / L;
+  auto coeffs_at = [&](double f, cd* c) {
     for (int j = 1; j <= J; ++j) {
       cd acc = 0;
       const double dist = f + 0.5 * J - j;
@@ -174,10 +233,22 @@ bool build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
       rv[j - 1] = acc;
     }
     for (int a = 0; a < J; ++a) {
-      cd c = 0;
-      for (int b = 0; b < J; ++b) c += T[a * J + b] * rv[b];
-      h.table[(size_t)t * J + a] = make_float2((float)c.real(), (float)c.imag());
+      cd v = 0;
+      for (int b = 0; b < J; ++b) v += T[a * J + b] * rv[b];
+      c[a] = v;
     }
+  };
+  std::vector<cd> c(J);
+  if (L > 0) {
+    // table: c(f_i) at f_i = i / L, i = 0..L
+    h.table.resize((size_t)(L + 1) * J);
+    for (int t = 0; t <= L; ++t) {
+      coeffs_at((double)t / L, c.data());
+      for (int a = 0; a < J; ++a) h.table[(size_t)t * J + a] = make_float2((float)c[a].real(), (float)c[a].imag());
+    }
+  } else {
+    const int rc = fit_coeff_polys(J, coeffs_at, h);
+    if (rc != NUFFT3D_OK) return rc;
   }
   auto twiddles = [](int Lt, std::vector<float2>& out) {
     out.resize(Lt);
@@ -199,7 +270,7 @@ bool build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
     h.weight.resize(r.M);
     for (int m = 0; m < r.M; ++m) h.weight[m] = make_float2(p->weight[2 * m], p->weight[2 * m + 1]);
   }
-  return true;
+  return NUFFT3D_OK;
 }
 
 // Coincident samples.  If line l2 runs opposite to line l (d_l2 = -d_l within
@@ -322,6 +393,7 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.counter = pl->d_counter;
   g.S = pl->pts_per_sub;
   g.lp_bound = pl->d_lp_bound;
+  g.poly = pl->poly;
   return g;
 }
 
@@ -399,7 +471,8 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   int rc = resolve(p, r);
   if (rc != NUFFT3D_OK) return rc;
   HostTables h;
-  if (!build_tables(p, r, h)) return NUFFT3D_ERR_ARG;
+  rc = build_tables(p, r, h);
+  if (rc != NUFFT3D_OK) return rc;
   std::vector<uint32_t> ids, twin;
   int n_pairs = 0;
   pair_lines(p, r, h, ids, twin, n_pairs);
@@ -410,6 +483,8 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->K = r.K;
   pl->J = r.J;
   pl->L = r.L;
+  pl->poly = h.poly;
+  pl->poly_err = h.poly_err;
   pl->D = r.D;
   pl->M = r.M;
   pl->P = r.P;
@@ -594,7 +669,7 @@ int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes) {
   b += (size_t)r.N * r.K * r.K * sizeof(float2);
   if (r.line_fft) b += (size_t)r.P * sizeof(float2);
   b += (size_t)r.P * sizeof(uint2);                                      // point sort (upper bound)
-  b += (size_t)(r.L + 1) * r.J * sizeof(float2);                         // table
+  b += r.L ? (size_t)(r.L + 1) * r.J * sizeof(float2) : 0;               // table
   b += (size_t)r.D * 3 * sizeof(float2) + (size_t)r.M * 2 * sizeof(float2) + r.N * sizeof(float);
   b += (size_t)(r.K + r.M) * sizeof(float2);
   *bytes = b;
@@ -653,6 +728,8 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
   out[7] = (int)std::min<long long>(maxc, 0x7fffffff);
   out[8] = (int)std::min<long long>(plan->P_eval, 0x7fffffff);
   out[9] = plan->n_pairs;
+  out[10] = plan->L == 0 ? 1 : 0;
+  out[11] = (int)std::min(std::ceil(plan->poly_err * 1e12), 2147483647.0);
   return NUFFT3D_OK;
 }
 
@@ -667,7 +744,7 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   const int gv = gather_variant >= 0 ? gather_variant : plan->gather_variant;
   const int sv = spread_variant >= 0 ? spread_variant : plan->spread_variant;
   if ((gv == 2 || sv == 2) && !nufft::v2_supported(T, plan->J, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
-  if ((gv == 1 || sv == 1) && plan->J != 6) return NUFFT3D_ERR_UNSUPPORTED;
+  if ((gv == 1 || sv == 1) && (plan->J != 6 || plan->L == 0)) return NUFFT3D_ERR_UNSUPPORTED;
   const int S_new = points_per_subproblem > 0 ? points_per_subproblem : plan->pts_per_sub;
   if ((gv == 3 || gv == 5) && !nufft::v3_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   if (gv == 5 && T != 8) return NUFFT3D_ERR_UNSUPPORTED;

@@ -65,6 +65,31 @@ def test_full_size_adjoint_dot_product(cuda_lib, problem):
     plan.close()
 
 
+def test_full_size_forward_exact_coefficients(cuda_lib, problem):
+    """The 256^3 workload with exact per-point min-max coefficients (fitted
+    polynomials on the GPU) against the oracle's per-point FP64 solve."""
+    import torch
+
+    w, dirs, x, lines, _ = problem
+    plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, exact_coeffs=True)
+    p = plan.forward(torch.from_numpy(x).cuda())
+    assert plan.sync_status() == 0
+    op = O.OraclePlan(w.n, w.k, w.j, 0, dirs, w.m)
+    ref = O.nufft_forward(x.astype(np.float64), op, lines=lines)
+    err = O.rel_l2(p.cpu().numpy()[lines], ref)
+    print(f"full-size forward, exact coefficients, rel-L2 vs FP64 oracle (64 lines): {err:.3e}")
+    assert err < TOL
+    xr = torch.from_numpy(I.random_volume(w.n, 31).astype(np.float32)).cuda()
+    y = torch.from_numpy(I.random_lines(dirs.shape[0], w.m, 32).astype(np.complex64)).cuda()
+    Ax = plan.forward(xr).to(torch.complex128)
+    Ahy = plan.adjoint(y).to(torch.float64)
+    lhs = torch.sum(torch.conj(y.to(torch.complex128)) * Ax).real
+    rhs = torch.sum(Ahy * xr.to(torch.float64))
+    rel = abs(float(lhs - rhs)) / float(torch.linalg.norm(Ax) * torch.linalg.norm(y.to(torch.complex128)))
+    assert rel < 1e-6
+    plan.close()
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "fp16"])
 def test_full_size_reduced_precision_grid(cuda_lib, problem, dtype):
     import torch

@@ -58,6 +58,7 @@ def test_workspace_bytes_counts_grid_and_buffers(lib):
     assert expect <= b < expect + 200_000
     assert _ws(grid_dtype="bf16") == b + K ** 3 * 4 + 4
     assert _ws(do_line_fft=False) == b - D * M * 8
+    assert _ws(exact_coeffs=1) == b - 1025 * 6 * 8   # no table
 
 
 @pytest.mark.parametrize("kw,status", [
@@ -72,6 +73,7 @@ def test_workspace_bytes_counts_grid_and_buffers(lib):
     (dict(k=80), -4),                    # 80 = 16 * 5: not 2^a 3^b
     (dict(m=80), -4),
     (dict(grid_dtype=3), -1),
+    (dict(exact_coeffs=2), -1),
     (dict(dirs=np.array([[2.0, 0.0, 0.0]])), -1),   # |d| > 1
     (dict(dirs=np.array([[np.nan, 0.0, 0.0]])), -1),
     (dict(omega=np.full(64, 4.0)), -1),             # |omega| > pi
