@@ -147,13 +147,73 @@ __device__ __forceinline__ void stockham_stage(float2* buf, int pitch, const flo
   __syncthreads();
 }
 
-template <int L, int W, int NT, bool INV, int S = 0>
+template <int L, int W, int NT, bool INV, int S = 0, int SEND = fft_num_stages(L)>
 __device__ __forceinline__ void smem_fft(float2* buf, int pitch, const float2* __restrict__ tw) {
-  if constexpr (S < fft_num_stages(L)) {
+  if constexpr (S < SEND) {
     constexpr int R = fft_stage_radix(L, S);
     constexpr int NS = fft_span_before(L, S);
     stockham_stage<L, R, NS, W, NT, INV>(buf, pitch, tw);
-    smem_fft<L, W, NT, INV, S + 1>(buf, pitch, tw);
+    smem_fft<L, W, NT, INV, S + 1, SEND>(buf, pitch, tw);
+  }
+}
+
+// The same transform with the first stage fed from registers loaded straight
+// from global memory and the last stage written straight to global memory:
+// shared memory carries only the exchanges between stages (one write and one
+// read per element and exchange, instead of an extra staging write and read
+// at each end), and zero rows of a padded input are never touched.
+// load(i, c) returns input row i of column c; store(i, c, v) writes output row
+// i.  The first stage has span 1 (no twiddles); the last stage's butterfly j
+// writes rows j + r L / R.
+template <int L, int W, int NT, bool INV, class Load, class Store>
+__device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __restrict__ tw, Load&& load,
+                                        Store&& store) {
+  constexpr int S = fft_num_stages(L);
+  static_assert(S >= 2, "reg_fft needs at least two stages");
+  {
+    constexpr int R = fft_stage_radix(L, 0);
+    constexpr int NBF = W * (L / R);
+    constexpr int PER = (NBF + NT - 1) / NT;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int b = threadIdx.x + p * NT;
+      if (NBF % NT == 0 || b < NBF) {
+        const int c = b % W, j = b / W;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = load(j + r * (L / R), c);
+        small_dft<R, INV>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[(j * R + r) * pitch + c] = v[r];
+      }
+    }
+    __syncthreads();
+  }
+  smem_fft<L, W, NT, INV, 1, S - 1>(buf, pitch, tw);
+  {
+    constexpr int R = fft_stage_radix(L, S - 1);
+    constexpr int NS = L / R;
+    constexpr int NBF = W * NS;
+    constexpr int PER = (NBF + NT - 1) / NT;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int b = threadIdx.x + p * NT;
+      if (NBF % NT == 0 || b < NBF) {
+        const int c = b % W, j = b / W;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = buf[(j + r * NS) * pitch + c];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = __ldg(&tw[j * r]);
+          if (INV) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
+        small_dft<R, INV>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) store(j + r * NS, c, v[r]);
+      }
+    }
   }
 }
 

@@ -16,6 +16,10 @@ constexpr int FFT_PITCH = FFT_W + 1;
 // shared memory bounds residency to 3 CTAs per SM at L = 512; ask for the
 // register budget that allows the same (65536 / (3 * 256) = 85 per thread)
 constexpr int FFT_MIN_CTAS = 3;
+// column passes: 512 threads hold two radix-8 butterflies each between the
+// stages (two CTAs of 70 KB per SM, 64 registers per thread)
+constexpr int COL_NT = 512;
+constexpr int COL_MIN_CTAS = 2;
 
 __device__ __forceinline__ int centred_to_grid(int i, int half, int L) {
   int k = i - half;
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_fwd(const void* __
 // element (i, c) of the input at in[o in_outer + i in_stride + ch W + c]
 // ----------------------------------------------------------------------------
 template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT>
-__global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
+__global__ void __launch_bounds__(COL_NT, COL_MIN_CTAS) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
                                                 int N, int n_chunks, long long in_outer, long long in_stride,
                                                 long long out_outer, long long out_stride,
                                                 const float2* __restrict__ tw, const float* __restrict__ bound) {
@@ -94,48 +98,34 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_col(const float2* __re
   const float2* ib = in + o * in_outer + (long long)ch * FFT_W;
   OutT* ob = out + o * out_outer + (long long)ch * FFT_W;
   const int half = N / 2;
-  const int in_len = PAD_IN ? N : L;
-  for (int base = threadIdx.x; base < FFT_W * in_len; base += 8 * FFT_NT) {
-    float2 t[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * FFT_NT;
-      if (idx < FFT_W * in_len) t[u] = ib[(long long)(idx / FFT_W) * in_stride + idx % FFT_W];
+  // centred row i of an N-row input or output <-> grid row k of the L-point
+  // transform: k = i - N/2 (mod L); rows N/2 <= k < L - N/2 are the padding
+  auto load = [&](int k, int c) -> float2 {
+    int i = k;
+    if (PAD_IN) {
+      if (k < half) i = k + half;
+      else if (k >= L - half) i = k - (L - half);
+      else return make_float2(0.f, 0.f);
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * FFT_NT;
-      if (idx < FFT_W * in_len) {
-        const int c = idx % FFT_W, i = idx / FFT_W;
-        const int k = PAD_IN ? centred_to_grid(i, half, L) : i;
-        buf[k * FFT_PITCH + c] = t[u];
-      }
+    return ib[(long long)i * in_stride + c];
+  };
+  auto store = [&](int k, int c, float2 v) {
+    int i = k;
+    if (CROP_OUT) {
+      if (k < half) i = k + half;
+      else if (k >= L - half) i = k - (L - half);
+      else return;
     }
-  }
-  if (PAD_IN) {
-    for (int idx = threadIdx.x; idx < FFT_W * (L - N); idx += FFT_NT) {
-      const int c = idx % FFT_W, i = idx / FFT_W + (N - half);
-      buf[i * FFT_PITCH + c] = make_float2(0.f, 0.f);
-    }
-  }
-  __syncthreads();
-  smem_fft<L, FFT_W, FFT_NT, INV>(buf, FFT_PITCH, tw);
-  const int out_len = CROP_OUT ? N : L;
-  for (int idx = threadIdx.x; idx < FFT_W * out_len; idx += FFT_NT) {
-    const int c = idx % FFT_W, i = idx / FFT_W;
-    const int k = CROP_OUT ? centred_to_grid(i, half, L) : i;
     if constexpr (sizeof(OutT) == sizeof(float2)) {
-      ob[(long long)i * out_stride + c] = *(const OutT*)&buf[k * FFT_PITCH + c];
-    } else {
+      ob[(long long)i * out_stride + c] = *(const OutT*)&v;
+    } else if constexpr (std::is_same<OutT, __nv_bfloat162>::value) {
       // reduced-precision grid store (forward z pass only)
-      float2 v = buf[k * FFT_PITCH + c];
-      if constexpr (std::is_same<OutT, __nv_bfloat162>::value) {
-        ob[(long long)i * out_stride + c] = GridBF16::pack(v, out_scale);
-      } else {
-        ob[(long long)i * out_stride + c] = GridF16::pack(v, out_scale);
-      }
+      ob[(long long)i * out_stride + c] = GridBF16::pack(v, out_scale);
+    } else {
+      ob[(long long)i * out_stride + c] = GridF16::pack(v, out_scale);
     }
-  }
+  };
+  reg_fft<L, FFT_W, COL_NT, INV>(buf, FFT_PITCH, tw, load, store);
 }
 
 // ----------------------------------------------------------------------------
@@ -337,7 +327,7 @@ static cudaError_t launch_col_t(const float2* in, OutT* out, int N, int n_outer,
   if (e != cudaSuccess) return e;
   const int n_chunks = row_len / FFT_W;
   const long long grid = (long long)n_outer * n_chunks;
-  f<<<(unsigned)grid, FFT_NT, fft_smem(L), st>>>(in, out, N, n_chunks, in_outer, in_stride, out_outer,
+  f<<<(unsigned)grid, COL_NT, fft_smem(L), st>>>(in, out, N, n_chunks, in_outer, in_stride, out_outer,
                                                  out_stride, tw, out_scale);
   return cudaGetLastError();
 }
