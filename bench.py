@@ -2,10 +2,13 @@
 """Throughput of the radial-line 3D NUFFT projector (forward + adjoint).
 
 Metric: nonuniform points per second, P / (t_forward + t_adjoint), on the
-256^3 workload (K = 512, J = 6, L = 1024, 360 x 256 umbrella lines of 512
-samples: P = 47,185,920 points) with a seeded ellipsoid phantom plus
-N(0, 0.01^2) noise.  A step is one forward projection of the volume followed
-by the adjoint of the resulting lines.
+256^3 workload (K = 512, J = 6, 360 x 256 umbrella lines of 512 samples:
+P = 47,185,920 points) with a seeded ellipsoid phantom plus N(0, 0.01^2)
+noise.  A step is one forward projection of the volume followed by the
+adjoint of the resulting lines.  The min-max coefficients are the exact ones
+at every point (--coeffs exact, the default; the oracle's per-point solve is
+its reference) or linearly interpolated from the L = 1024 table
+(--coeffs table).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -49,7 +52,7 @@ def parse_args():
     ap.add_argument("--points-per-subproblem", type=int, default=0)
     ap.add_argument("--tile-edge", type=int, default=0)
     ap.add_argument("--keep-duplicates", action="store_true")
-    ap.add_argument("--coeffs", default="table", choices=["table", "exact"],
+    ap.add_argument("--coeffs", default="exact", choices=["table", "exact"],
                     help="min-max coefficients from the L = 1024 table, or exact per point (fitted polynomials)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -166,7 +169,7 @@ def load_peaks():
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("interp_common.cuh", "interp_gather.cu", "interp_spread.cu", "common.cuh"):
+    for fn in ("interp_common.cuh", "interp_gather.cu", "interp_spread.cu", "interp_tma.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1605_05231_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -150,8 +150,15 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
  * warp-private tile, no shared atomics (J = 6, T = 8; the default spread
  * when available); gather only: 3 one thread per point, points reordered so
  * that every half-warp's tile accesses fall in distinct banks (any J; the
- * default gather), 4 the same with the table in shared memory, 5 the same as 3
- * with 128-thread CTAs; spread only: 3 variant 2 with ten warps per SM and
+ * default gather with a table), 4 the same with the table in shared memory, 5
+ * the same as 3 with 128-thread CTAs (T = 8; the default with exact_coeffs,
+ * with 256 points per subproblem instead of 512), 6 and 7 the same as 3
+ * and 5 with two copies of the tile in shared memory, the second shifted by
+ * half the bank range, so that the points of two residue classes can be dealt
+ * evenly to both (J = 6, T = 8), 8 the same as 5 with persistent CTAs that
+ * copy the next subproblem's tile into shared memory with a TMA tensor copy
+ * while the current one is computed (J = 6, T = 8; needs the tensor map the
+ * plan encodes for its grid); spread only: 3 variant 2 with ten warps per SM and
  * the table read through L1 (the default spread), 4 one thread per point in
  * rounds of pairwise distinct tile-offset residues (no atomics).  T is 4, 8 or 16; changing it re-sorts the points.
  * Synchronises the plan's last stream and works on cuda_stream.  Returns

@@ -272,7 +272,7 @@ class Plan:
         return d
 
     def tune(self, gather_variant=-1, spread_variant=-1, points_per_subproblem=0, tile_edge=0, stream=None):
-        """Pick kernel variants (0, 1, 2), points per subproblem and tile edge (-1 / 0 keep)."""
+        """Pick the gather (0-7) and spread (0-4) variants, points per subproblem and tile edge (-1 / 0 keep)."""
         _check(self.lib.nufft3d_plan_tune(self._handle, int(gather_variant), int(spread_variant),
                                           int(points_per_subproblem), int(tile_edge),
                                           _stream_ptr(stream, self.device)), "nufft3d_plan_tune")

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libnufft3d.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,6 +37,7 @@ struct InterpGeom {
   int S;                 // most points in one subproblem
   const float* lp_bound; // bound on |Y| for a reduced-precision grid (else null)
   CoefPoly poly;         // coefficient polynomials (used when L == 0)
+  const CUtensorMap* tmap = nullptr;  // host copy of the grid's tensor map (gather variant 8), or null
 };
 
 bool fft_length_supported(int L);
@@ -69,6 +71,11 @@ bool v2_supported(int T, int J, int L);
 int plan_forward_enqueue(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st);
 int plan_adjoint_enqueue(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st);
 bool v3_supported(int T, int J, int S);
+bool v3_two_copy_supported(int T, int J, int S);
+bool v8_supported(int T, int J, int S, int elem);
+bool make_grid_tmap(CUtensorMap* map, const void* grid, int K, int elem);
+cudaError_t launch_gather_tma(const InterpGeom& g, int grid_dtype, const void* grid, const int4* subs, int n_subs,
+                              float2* out, cudaStream_t st);
 bool v4_supported(int T, int J, int S, int L);
 bool v3s_supported(int T, int J);
 bool v4s_supported(int T, int J, int S);
@@ -83,6 +90,8 @@ struct nufft3d_plan_s {
   int N, K, J, L, D, M;  // L = 0: exact coefficients from the fitted polynomials
   long long P;
   nufft::CoefPoly poly{};
+  CUtensorMap tmap_grid{};  // tensor map of the grid the gather reads (d_grid or d_grid_lp)
+  bool tmap_ok = false;
   double poly_err = 0.0;  // max |fit - exact| / max |c| of the polynomials (0 with a table)
   int complex_volume, do_line_fft, grid_dtype;
   int T, nT;  // tile edge and tiles per axis

@@ -249,20 +249,34 @@ constexpr int V3_THREADS = 256;
 
 struct V3Layout {
   int E;
+  int copy2;  // cell offset of the second tile copy (0: one copy)
   size_t tile_bytes, bytes;
 };
 
-// elem: bytes per grid cell in shared memory (8 for complex64, 4 for bf16/fp16 pairs)
-__host__ __device__ inline V3Layout v3_layout(int T, int J, int S, int elem) {
+// elem: bytes per grid cell in shared memory (8 for complex64, 4 for bf16/fp16
+// pairs).  With two copies the second starts at a cell offset congruent to
+// half the residue range (kRes / 2, kRes = 128 / elem), so that a point read
+// from it falls in the partner residue class.
+__host__ __device__ inline V3Layout v3_layout(int T, int J, int S, int elem, bool two = false) {
   V3Layout l;
   l.E = T + J - 1;
-  l.tile_bytes = ((size_t)l.E * l.E * l.E * elem + 15) / 16 * 16;
+  const int e3 = l.E * l.E * l.E;
+  const int kres = 128 / elem;
+  l.copy2 = two ? e3 + ((kres / 2 - e3 % kres) + kres) % kres : 0;
+  const int cells = two ? l.copy2 + e3 : e3;
+  l.tile_bytes = ((size_t)cells * elem + 15) / 16 * 16;
   // per point: id, twin, tile offset, f[3] (6 words) + ordered index (1 word); class counts and cursors
   l.bytes = l.tile_bytes + (size_t)S * 7 * sizeof(int) + 64 * sizeof(int);
   return l;
 }
 
-template <int J, int T, int NT, typename G>
+// TWO = false: one tile copy, points in round-robin order over their residue
+// classes.  TWO = true (variants 6 and 7): two copies of the tile; the points
+// of classes c and c + kRes/2 form one pool and are dealt alternately to the
+// two classes (a point dealt to its partner class reads the second copy), so
+// the classes of each pair hold equally many points and fewer half-warps
+// repeat a class.
+template <int J, int T, int NT, typename G, bool TWO = false>
 __global__ void __launch_bounds__(NT, J <= 6 ? 1024 / NT : 1) k_gather_v3(InterpGeom g, const typename G::T* __restrict__ grid,
                                                   float inv_scale, const int4* __restrict__ subs, int S,
                                                   float2* __restrict__ out) {
@@ -270,11 +284,12 @@ __global__ void __launch_bounds__(NT, J <= 6 ? 1024 / NT : 1) k_gather_v3(Interp
   // a warp access of 4-byte cells is conflict-free with 32 distinct residues,
   // of 8-byte cells with 16 distinct residues per half-warp
   constexpr int kRes = sizeof(TT) == 4 ? 32 : 16;
+  constexpr int kHalf = kRes / 2;
   constexpr int E = T + J - 1, E2 = E * E, PP = E2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   inv_scale = lp_inv_scale<G>(g);
   const int nT = g.nT, K = g.K;
-  const V3Layout lay = v3_layout(T, J, S, (int)sizeof(TT));
+  const V3Layout lay = v3_layout(T, J, S, (int)sizeof(TT), TWO);
   TT* tile = (TT*)smem_raw;
   int* p_id = (int*)(smem_raw + lay.tile_bytes);
   int* p_tw = p_id + S;
@@ -295,7 +310,9 @@ __global__ void __launch_bounds__(NT, J <= 6 ? 1024 / NT : 1) k_gather_v3(Interp
     gx -= gx >= K ? K : 0;
     gy -= gy >= K ? K : 0;
     gz -= gz >= K ? K : 0;
-    tile[r] = grid[((size_t)gz * K + gy) * K + gx];
+    const TT v = grid[((size_t)gz * K + gy) * K + gx];
+    tile[r] = v;
+    if (TWO) tile[lay.copy2 + r] = v;
   }
   __syncthreads();
   // decode every point of the subproblem once
@@ -317,13 +334,35 @@ __global__ void __launch_bounds__(NT, J <= 6 ? 1024 / NT : 1) k_gather_v3(Interp
     p_f[i] = f[0];
     p_f[S + i] = f[1];
     p_f[2 * S + i] = f[2];
-    atomicAdd(&ncls[off < 0 ? 0 : (off & (kRes - 1))], 1);
+    const int c = off < 0 ? 0 : (off & (kRes - 1));
+    atomicAdd(&ncls[TWO ? (c & (kHalf - 1)) : c], 1);
   }
   __syncthreads();
+  if (TWO) {
+    // class sizes after dealing each pool alternately: ceil to c, floor to c + kHalf
+    int pool = 0;
+    if (threadIdx.x < kHalf) pool = ncls[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < kHalf) {
+      ncls[threadIdx.x] = (pool + 1) >> 1;
+      ncls[threadIdx.x + kHalf] = pool >> 1;
+    }
+    __syncthreads();
+  }
   // rank within the class, then the round-robin position
   for (int i = threadIdx.x; i < cnt; i += NT) {
-    const int c = p_off[i] < 0 ? 0 : (p_off[i] & (kRes - 1));
-    const int r = atomicAdd(&ncls[kRes + c], 1);
+    int off = p_off[i];
+    const int c0 = off < 0 ? 0 : (off & (kRes - 1));
+    int c = c0, r;
+    if (TWO) {
+      const int pc = c0 & (kHalf - 1);
+      const int q = atomicAdd(&ncls[kRes + pc], 1);
+      c = pc + ((q & 1) ? kHalf : 0);
+      r = q >> 1;
+      if (c != c0 && off >= 0) p_off[i] = off + lay.copy2;  // read from the second copy
+    } else {
+      r = atomicAdd(&ncls[kRes + c], 1);
+    }
     int pos = 0;
 #pragma unroll
     for (int q = 0; q < kRes; ++q) {
@@ -542,11 +581,11 @@ static cudaError_t launch_gather_v4_j(const InterpGeom& g, int dtype, const void
   return cudaErrorInvalidValue;
 }
 
-template <int J, int T, int NT, typename G>
+template <int J, int T, int NT, typename G, bool TWO = false>
 static cudaError_t launch_gather_v3_tt(const InterpGeom& g, const void* grid, float inv_scale, const int4* subs,
                                        int n_subs, int S, float2* out, cudaStream_t st) {
-  auto f = k_gather_v3<J, T, NT, G>;
-  const size_t smem = v3_layout(T, J, S, (int)sizeof(typename G::T)).bytes;
+  auto f = k_gather_v3<J, T, NT, G, TWO>;
+  const size_t smem = v3_layout(T, J, S, (int)sizeof(typename G::T), TWO).bytes;
   cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (n_subs == 0) return cudaSuccess;
@@ -587,6 +626,18 @@ bool v4_supported(int T, int J, int S, int L) {
 
 bool v3_supported(int T, int J, int S) {
   return v3_layout(T, J, S, 8).bytes <= (size_t)max_optin_smem();
+}
+
+bool v3_two_copy_supported(int T, int J, int S) {
+  return T == 8 && J == 6 && v3_layout(T, J, S, 8, true).bytes <= (size_t)max_optin_smem();
+}
+
+// variants 6 (256 threads) and 7 (128 threads): two tile copies, J = 6, T = 8
+template <typename G>
+static cudaError_t launch_gather_v3_two(const InterpGeom& g, int nt, const void* grid, float inv_scale,
+                                        const int4* subs, int n_subs, int S, float2* out, cudaStream_t st) {
+  if (nt == 128) return launch_gather_v3_tt<6, 8, 128, G, true>(g, grid, inv_scale, subs, n_subs, S, out, st);
+  return launch_gather_v3_tt<6, 8, 256, G, true>(g, grid, inv_scale, subs, n_subs, S, out, st);
 }
 
 template <typename G>
@@ -647,6 +698,16 @@ cudaError_t launch_gather(const InterpGeom& g, int variant, int grid_dtype, cons
       case 4: return launch_gather_v4_j<4>(g, grid_dtype, grid, subs, n_subs, g.S, out, st);
       case 6: return launch_gather_v4_j<6>(g, grid_dtype, grid, subs, n_subs, g.S, out, st);
       case 8: return launch_gather_v4_j<8>(g, grid_dtype, grid, subs, n_subs, g.S, out, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+  if (variant == 8) return launch_gather_tma(g, grid_dtype, grid, subs, n_subs, out, st);
+  if ((variant == 6 || variant == 7) && g.J == 6 && g.T == 8) {
+    const int nt = variant == 7 ? 128 : 256;
+    switch (grid_dtype) {
+      case 0: return launch_gather_v3_two<GridC64>(g, nt, grid, inv_scale, subs, n_subs, g.S, out, st);
+      case 1: return launch_gather_v3_two<GridBF16>(g, nt, grid, inv_scale, subs, n_subs, g.S, out, st);
+      case 2: return launch_gather_v3_two<GridF16>(g, nt, grid, inv_scale, subs, n_subs, g.S, out, st);
     }
     return cudaErrorInvalidValue;
   }

@@ -394,6 +394,7 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.S = pl->pts_per_sub;
   g.lp_bound = pl->d_lp_bound;
   g.poly = pl->poly;
+  g.tmap = pl->tmap_ok ? &pl->tmap_grid : nullptr;
   return g;
 }
 
@@ -498,7 +499,11 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->P_eval = (long long)pl->h_unique.size();
   pl->n_pairs = n_pairs;
   pl->spread_variant = nufft::v3s_supported(r.T, r.J) ? 3 : (nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0);
-  pl->gather_variant = nufft::v3_supported(r.T, r.J, 512) ? 3 : 0;
+  // defaults measured at 256^3: with the table, 256-thread gather CTAs and 512
+  // points per subproblem; with exact coefficients (no table traffic), the
+  // 128-thread CTAs and 256 points per subproblem
+  const int S0 = r.L == 0 && r.T == 8 ? 256 : 512;
+  pl->gather_variant = nufft::v3_supported(r.T, r.J, S0) ? (r.L == 0 && r.T == 8 ? 5 : 3) : 0;
   CK(cudaGetDevice(&pl->device));
   CK(upload(&pl->d_s, h.s, st));
   CK(upload(&pl->d_table, h.table, st));
@@ -513,7 +518,7 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   CK(cudaStreamSynchronize(st));
   rc = sort_points(pl, st);
   if (rc != NUFFT3D_OK) return rc;
-  rc = build_subproblems(pl, 512, st);
+  rc = build_subproblems(pl, S0, st);
   if (rc != NUFFT3D_OK) return rc;
   const size_t K3 = (size_t)r.K * r.K * r.K;
   CK(dalloc(&pl->d_grid, K3));
@@ -521,6 +526,10 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
     CK(cudaMalloc(&pl->d_grid_lp, K3 * 4));
     CK(dalloc(&pl->d_lp_bound, 1));
   }
+  // tensor map of the grid the gather reads (TMA tile copies of gather variant 8)
+  pl->tmap_ok = nufft::make_grid_tmap(&pl->tmap_grid, r.grid_dtype == NUFFT3D_GRID_C64 ? (const void*)pl->d_grid
+                                                                                       : pl->d_grid_lp,
+                                      r.K, r.grid_dtype == NUFFT3D_GRID_C64 ? 8 : 4);
   CK(dalloc(&pl->d_bufA, (size_t)r.N * r.N * r.K));
   CK(dalloc(&pl->d_bufB, (size_t)r.N * r.K * r.K));
   if (r.line_fft) CK(dalloc(&pl->d_lines, (size_t)r.P));
@@ -736,7 +745,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 5 || spread_variant < -1 || spread_variant > 4) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 8 || spread_variant < -1 || spread_variant > 4) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -748,6 +757,10 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   const int S_new = points_per_subproblem > 0 ? points_per_subproblem : plan->pts_per_sub;
   if ((gv == 3 || gv == 5) && !nufft::v3_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   if (gv == 5 && T != 8) return NUFFT3D_ERR_UNSUPPORTED;
+  if ((gv == 6 || gv == 7) && !nufft::v3_two_copy_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
+  if (gv == 8 && (!plan->tmap_ok ||
+                  !nufft::v8_supported(T, plan->J, S_new, plan->grid_dtype == NUFFT3D_GRID_C64 ? 8 : 4)))
+    return NUFFT3D_ERR_UNSUPPORTED;
   if (gv == 4 && !nufft::v4_supported(T, plan->J, S_new, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 3 && !nufft::v3s_supported(T, plan->J)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 4 && !nufft::v4s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;

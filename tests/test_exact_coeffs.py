@@ -83,7 +83,9 @@ def test_shapes_and_taps(cuda_lib, n, k, m, ndir, j):
 
 
 @pytest.mark.parametrize("gv,sv,pps,tile", [(0, 0, 1024, 8), (3, 3, 512, 8), (3, 3, 37, 8), (5, 4, 512, 8),
-                                            (3, 4, 300, 8), (0, 3, 77, 8), (3, 0, 1024, 16), (5, 3, 2048, 8)])
+                                            (3, 4, 300, 8), (0, 3, 77, 8), (3, 0, 1024, 16), (5, 3, 2048, 8),
+                                            (6, 3, 512, 8), (7, 3, 256, 8), (7, 4, 100, 8), (8, 3, 256, 8),
+                                            (8, 3, 5, 8)])
 def test_variants_without_table(cuda_lib, gv, sv, pps, tile):
     n = 32
     dirs = I.umbrella_directions(35, 20)

@@ -73,6 +73,10 @@ def test_full_size_forward_exact_coefficients(cuda_lib, problem):
     w, dirs, x, lines, _ = problem
     plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, exact_coeffs=True)
     p = plan.forward(torch.from_numpy(x).cuda())
+    plan.tune(8, -1, 256, 8)
+    p8 = plan.forward(torch.from_numpy(x).cuda())
+    # same arithmetic per point; only the tile staging differs
+    assert float(torch.linalg.norm(p - p8) / torch.linalg.norm(p)) < 1e-6
     assert plan.sync_status() == 0
     op = O.OraclePlan(w.n, w.k, w.j, 0, dirs, w.m)
     ref = O.nufft_forward(x.astype(np.float64), op, lines=lines)
@@ -105,7 +109,7 @@ def test_full_size_reduced_precision_grid(cuda_lib, problem, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp16"])
-@pytest.mark.parametrize("gv", [0, 2, 3, 4])
+@pytest.mark.parametrize("gv", [0, 2, 3, 4, 7, 8])
 def test_reduced_precision_small_all_variants(cuda_lib, dtype, gv):
     """Every gather variant reads the reduced-precision grid with the same scale;
     the adjoint keeps FP32 accumulation and stays at the FP32 bar."""

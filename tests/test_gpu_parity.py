@@ -178,7 +178,8 @@ def test_mid_workload_sampled_lines(cuda_lib):
 
 @pytest.mark.parametrize("gv,sv,pps,tile", [(0, 0, 1024, 8), (0, 0, 700, 16), (1, 1, 1024, 16), (1, 1, 300, 8),
                                             (2, 2, 1024, 8), (2, 2, 64, 8), (2, 2, 5000, 8), (3, 2, 1024, 8),
-                                            (3, 0, 2048, 16), (3, 2, 37, 8), (4, 2, 512, 8), (4, 2, 400, 8), (3, 3, 1024, 8), (4, 3, 512, 8), (0, 3, 77, 8), (3, 4, 512, 8), (3, 4, 33, 8), (3, 4, 560, 8), (5, 3, 512, 8), (5, 0, 300, 8),
+                                            (3, 0, 2048, 16), (3, 2, 37, 8), (4, 2, 512, 8), (4, 2, 400, 8), (3, 3, 1024, 8), (4, 3, 512, 8), (0, 3, 77, 8), (3, 4, 512, 8), (3, 4, 33, 8), (3, 4, 560, 8), (5, 3, 512, 8), (5, 0, 300, 8), (6, 3, 512, 8), (7, 3, 256, 8), (7, 0, 37, 8), (6, 2, 2048, 8), (8, 3, 256, 8), (8, 0, 37, 8),
+                                            (8, 2, 1024, 8),
                                             (4, 0, 300, 8)])
 def test_kernel_variants_and_subproblem_split(cuda_lib, gv, sv, pps, tile):
     """Every gather/spread variant, tile edge and subproblem size gives the same operator."""
@@ -209,7 +210,7 @@ def test_unsupported_tuning_is_refused(cuda_lib):
         plan.tune(2, 2, 1024, 16)
     assert ei.value.status == -4
     with pytest.raises(cuda_lib.NufftError):
-        plan.tune(6, 0, 0, 0)
+        plan.tune(9, 0, 0, 0)
     assert plan.info()["gather_variant"] == 3 and plan.info()["tile"] == 8
 
 
