@@ -56,7 +56,8 @@ def parse_args():
                     help="min-max coefficients from the L = 1024 table, or exact per point (fitted polynomials)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-lines", type=int, default=4000)
+    ap.add_argument("--cpu-sample-lines", type=int, default=0,
+                    help="lines of the CPU oracle sample (0: sized for about 20 s of CPU work)")
     return ap.parse_args()
 
 
@@ -246,9 +247,11 @@ def bench_workload(args):
     return dataclasses.replace(w, table_oversamp=0) if args.coeffs == "exact" else w
 
 
-def coeff_desc(w, info=None):
+def coeff_desc(w, info=None, oracle=False):
     if w.table_oversamp:
         return f"table, L = {w.table_oversamp}, linear interpolation"
+    if oracle:
+        return "exact min-max per point (FP64 solve of T c = r at every point)"
     err = f", fit error {info['coeff_fit_error']:.1e} of max|c|" if info else ""
     return f"exact min-max per point (degree-8 polynomials fitted in FP64{err})"
 
@@ -283,14 +286,20 @@ def oracle_points(op, Y, lines):
     return time.perf_counter() - t0
 
 
-def oracle_time(w, x, dirs, sample_lines: int, seed: int = 0):
+def oracle_time(w, x, dirs, sample_lines: int, seed: int = 0, target_s: float = 20.0):
     """Oracle time for the whole workload: the fixed stages at full size plus
-    the per-point stages on a sample of lines scaled to all points."""
+    the per-point stages on a sample of lines scaled to all points.  With
+    sample_lines = 0 the sample is sized from a 4-line pilot to take about
+    target_s seconds."""
     import numpy as np
 
     t0 = time.perf_counter()
     op, Y, t_fixed = oracle_fixed(w, x, dirs)
-    lines = np.sort(np.random.default_rng(seed).choice(dirs.shape[0], sample_lines, replace=False))
+    rng = np.random.default_rng(seed)
+    if sample_lines <= 0:
+        t_pilot = oracle_points(op, Y, np.sort(rng.choice(dirs.shape[0], 4, replace=False)))
+        sample_lines = int(min(dirs.shape[0], max(4, 4 * target_s / max(t_pilot, 1e-6))))
+    lines = np.sort(rng.choice(dirs.shape[0], sample_lines, replace=False))
     t_pts = oracle_points(op, Y, lines)
     P = dirs.shape[0] * w.m
     Ps = len(lines) * w.m
@@ -336,7 +345,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "coefficients": coeff_desc(w),
+            "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "coefficients": coeff_desc(w, oracle=True),
                        "dirs": f"{w.n_az}x{w.n_pol}", "m": w.m, "points": P},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},

@@ -16,9 +16,14 @@ from .binding import NufftError
 
 # (gather variant, spread variant, points per subproblem, tile edge)
 CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
+    (5, 3, 256, 8),
+    (5, 3, 512, 8),
     (3, 3, 256, 8),
     (3, 3, 512, 8),
     (3, 3, 1024, 8),
+    (8, 3, 256, 8),
+    (8, 3, 512, 8),
+    (7, 3, 256, 8),
     (4, 3, 512, 8),
     (3, 2, 512, 8),
     (2, 2, 1024, 8),

@@ -174,17 +174,26 @@ __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __
     constexpr int R = fft_stage_radix(L, 0);
     constexpr int NBF = W * (L / R);
     constexpr int PER = (NBF + NT - 1) / NT;
+    // all of this thread's loads are issued before the first butterfly (more
+    // bytes in flight per SM); two butterflies per thread at 512 threads
+    float2 v[PER][R];
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int b = threadIdx.x + p * NT;
       if (NBF % NT == 0 || b < NBF) {
         const int c = b % W, j = b / W;
-        float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = load(j + r * (L / R), c);
-        small_dft<R, INV>(v);
+        for (int r = 0; r < R; ++r) v[p][r] = load(j + r * (L / R), c);
+      }
+    }
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[(j * R + r) * pitch + c] = v[r];
+    for (int p = 0; p < PER; ++p) {
+      const int b = threadIdx.x + p * NT;
+      if (NBF % NT == 0 || b < NBF) {
+        const int c = b % W, j = b / W;
+        small_dft<R, INV>(v[p]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[(j * R + r) * pitch + c] = v[p][r];
       }
     }
     __syncthreads();
