@@ -56,6 +56,7 @@ def parse_args():
                     help="min-max coefficients from the L = 1024 table, or exact per point (fitted polynomials)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fft-compare", action="store_true", help="skip the cuFFT comparison")
     ap.add_argument("--cpu-sample-lines", type=int, default=0,
                     help="lines of the CPU oracle sample (0: sized for about 20 s of CPU work)")
     return ap.parse_args()
@@ -155,6 +156,30 @@ def stage_work(n, k, j, m, d, p_eval=None):
             "x_pass": {"bytes": c8 * n * n * k + 4 * n ** 3},
         },
     }
+
+
+def cufft_compare(K: int, dev, reps: int = 10):
+    """Milliseconds of cuFFT's complex-to-complex K^3 forward and inverse
+    transforms (through torch.fft) on a resident complex64 grid, event-timed."""
+    import torch
+
+    g = torch.randn((K, K, K), dtype=torch.complex64, device=dev)
+    s = torch.cuda.current_stream(dev)
+    out = {}
+    for name, fn in (("cufft_fftn_ms", torch.fft.fftn), ("cufft_ifftn_ms", torch.fft.ifftn)):
+        for _ in range(3):
+            fn(g)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            fn(g)
+        e1.record(s)
+        e1.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / reps, 4)
+    del g
+    torch.cuda.empty_cache()
+    return out
 
 
 def load_peaks():
@@ -470,6 +495,16 @@ def run_ours(args):
     roof["traffic"] = ncu_traffic(f"{dom[0]}.{dom[1]}")
     stage_ms = {f"{side}.{name}": round(per_call[(side, name)], 4) for (side, name) in per_call}
 
+    # ---- cuFFT on the same grid, timed only as a comparison --------------
+    fft_cmp = None
+    if not args.no_fft_compare:
+        fft_cmp = cufft_compare(w.k, dev)
+        fft_cmp["ours_forward_ms"] = round(sum(per_call[("forward", s)] for s in ("x_pass", "y_pass", "z_pass")), 4)
+        fft_cmp["ours_inverse_ms"] = round(sum(per_call[("adjoint", s)] for s in ("z_pass", "y_pass", "x_pass")), 4)
+        fft_cmp["note"] = ("ours: the pruned 3D transform with the zero padding / cropping and the deapodisation "
+                           "fused (x, y, z passes); cuFFT: a full complex-to-complex K^3 transform of a "
+                           "resident grid (torch.fft), nothing fused")
+
     # ---- CPU oracle baseline (rank 0, N = 1) ----------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -490,7 +525,7 @@ def run_ours(args):
                            "l2": "working set per step >> L2 (1.07 GB grid, 0.38 GB lines, 0.19 GB point ids)",
                            "variants": plan.info()},
                 "gpu_launches": 10 * args.steps, "clocks": clk, "e2e": e2e, "roofline": roof,
-                "cpu_baseline": cpu, "stage_ms": stage_ms, "plan_s": plan_s}
+                "cpu_baseline": cpu, "stage_ms": stage_ms, "plan_s": plan_s, "cufft_comparison": fft_cmp}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

@@ -121,7 +121,9 @@ int nufft3d_forward(nufft3d_plan plan, const void* vol_dev, void* lines_dev, voi
 int nufft3d_adjoint(nufft3d_plan plan, const void* lines_dev, void* vol_dev, void* cuda_stream);
 
 /* Bytes of device memory a plan with these parameters holds (tables, point
- * sort, workspace).  Host only: touches no device. */
+ * sort, workspace: the forward grid, a separate adjoint grid that the
+ * adjoint keeps clear between calls unless the forward grid is bf16/fp16,
+ * the FFT intermediates and the line buffer).  Host only: touches no device. */
 int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes);
 
 /* Synchronise the plan's last stream and return, in *device_status, the

@@ -165,9 +165,16 @@ __device__ __forceinline__ void smem_fft(float2* buf, int pitch, const float2* _
 // load(i, c) returns input row i of column c; store(i, c, v) writes output row
 // i.  The first stage has span 1 (no twiddles); the last stage's butterfly j
 // writes rows j + r L / R.
-template <int L, int W, int NT, bool INV, class Load, class Store>
+struct NoPostLoad {
+  __device__ __forceinline__ void operator()(int, int) const {}
+};
+
+// post_load(i, c) runs for every input row once all of the thread's first-stage
+// loads have been issued (a consumer that clears its input does it there, so
+// that no load waits behind a store to a possibly aliasing address).
+template <int L, int W, int NT, bool INV, class Load, class Store, class PostLoad = NoPostLoad>
 __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __restrict__ tw, Load&& load,
-                                        Store&& store) {
+                                        Store&& store, PostLoad&& post_load = PostLoad{}) {
   constexpr int S = fft_num_stages(L);
   static_assert(S >= 2, "reg_fft needs at least two stages");
   {
@@ -184,6 +191,15 @@ __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __
         const int c = b % W, j = b / W;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[p][r] = load(j + r * (L / R), c);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int b = threadIdx.x + p * NT;
+      if (NBF % NT == 0 || b < NBF) {
+        const int c = b % W, j = b / W;
+#pragma unroll
+        for (int r = 0; r < R; ++r) post_load(j + r * (L / R), c);
       }
     }
 #pragma unroll

@@ -90,7 +90,8 @@ template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT>
 __global__ void __launch_bounds__(COL_NT, COL_MIN_CTAS) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
                                                 int N, int n_chunks, long long in_outer, long long in_stride,
                                                 long long out_outer, long long out_stride,
-                                                const float2* __restrict__ tw, const float* __restrict__ bound) {
+                                                const float2* __restrict__ tw, const float* __restrict__ bound,
+                                                ColPrune pr) {
   extern __shared__ float2 buf[];
   const float out_scale = bound ? lp_scale_from_bound(*bound) : 1.f;
   const int ch = blockIdx.x % n_chunks;
@@ -98,6 +99,40 @@ __global__ void __launch_bounds__(COL_NT, COL_MIN_CTAS) k_col(const float2* __re
   const float2* ib = in + o * in_outer + (long long)ch * FFT_W;
   OutT* ob = out + o * out_outer + (long long)ch * FFT_W;
   const int half = N / 2;
+  // pruning to the ball of cells the interpolation touches: the column's grid
+  // frequency kx = ch W + c, and for z passes ky = o (centred)
+  const int hk = pr.K / 2;
+  auto cen = [&](int k) -> int { return k < hk ? k : k - pr.K; };
+  const int cy2 = pr.mode == 2 ? cen((int)o) * cen((int)o) : 0;
+  int mcx2 = 0;  // smallest kx^2 over the CTA's columns
+  if (pr.mode != 0) {
+    mcx2 = 0x7fffffff;
+    for (int c = 0; c < FFT_W; ++c) {
+      const int cx = cen(ch * FFT_W + c);
+      mcx2 = cx * cx < mcx2 ? cx * cx : mcx2;
+    }
+    // a z pass whose columns all lie outside the disk kx^2 + ky^2 <= r2 has nothing to do
+    if (pr.mode == 2 && (long long)mcx2 + cy2 > pr.r2) return;
+  }
+  // exact test of cell (k, column c): inverse passes read only cells inside the
+  // ball (the adjoint clears nothing outside it)
+  auto live = [&](int k, int c) -> bool {
+    if (pr.mode == 0) return true;
+    const int cx = cen(ch * FFT_W + c), ck = cen(k);
+    return (long long)cx * cx + cy2 + (long long)ck * ck <= pr.r2;
+  };
+  // row test shared by the CTA's columns: forward passes write whole 128-byte
+  // rows whenever one of the 16 columns needs the row (no partial lines)
+  auto row_live = [&](int k) -> bool {
+    if (pr.mode == 0) return true;
+    const int ck = cen(k);
+    return (long long)mcx2 + cy2 + (long long)ck * ck <= pr.r2;
+  };
+  auto col_live = [&](int c) -> bool {
+    if (pr.mode != 2) return true;
+    const int cx = cen(ch * FFT_W + c);
+    return (long long)cx * cx + cy2 <= pr.r2;
+  };
   // centred row i of an N-row input or output <-> grid row k of the L-point
   // transform: k = i - N/2 (mod L); rows N/2 <= k < L - N/2 are the padding
   auto load = [&](int k, int c) -> float2 {
@@ -106,6 +141,13 @@ __global__ void __launch_bounds__(COL_NT, COL_MIN_CTAS) k_col(const float2* __re
       if (k < half) i = k + half;
       else if (k >= L - half) i = k - (L - half);
       else return make_float2(0.f, 0.f);
+      if (!col_live(c)) return make_float2(0.f, 0.f);
+    } else if (INV && pr.consume) {
+      // the adjoint grid is zero outside the ball: whole rows are read when a
+      // column of the CTA needs them (and cleared after the loads, below)
+      if (!row_live(k)) return make_float2(0.f, 0.f);
+    } else if (INV && !live(k, c)) {
+      return make_float2(0.f, 0.f);  // cells outside the touched ball are zero
     }
     return ib[(long long)i * in_stride + c];
   };
@@ -115,6 +157,8 @@ __global__ void __launch_bounds__(COL_NT, COL_MIN_CTAS) k_col(const float2* __re
       if (k < half) i = k + half;
       else if (k >= L - half) i = k - (L - half);
       else return;
+    } else if (!INV && !row_live(k)) {
+      return;  // no column of this CTA has the row in the touched region
     }
     if constexpr (sizeof(OutT) == sizeof(float2)) {
       ob[(long long)i * out_stride + c] = *(const OutT*)&v;
@@ -125,7 +169,12 @@ __global__ void __launch_bounds__(COL_NT, COL_MIN_CTAS) k_col(const float2* __re
       ob[(long long)i * out_stride + c] = GridF16::pack(v, out_scale);
     }
   };
-  reg_fft<L, FFT_W, COL_NT, INV>(buf, FFT_PITCH, tw, load, store);
+  // consume: every adjoint-grid row read is cleared for the next adjoint call
+  auto clear_read = [&](int k, int c) {
+    if (INV && !PAD_IN && pr.consume && row_live(k))
+      const_cast<float2*>(ib)[(long long)k * in_stride + c] = make_float2(0.f, 0.f);
+  };
+  reg_fft<L, FFT_W, COL_NT, INV>(buf, FFT_PITCH, tw, load, store, clear_read);
 }
 
 // ----------------------------------------------------------------------------
@@ -321,22 +370,23 @@ cudaError_t launch_row_adj(int K, const float2* in, void* vol, int cplx, const f
 template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT>
 static cudaError_t launch_col_t(const float2* in, OutT* out, int N, int n_outer, int row_len,
                                 long long in_outer, long long in_stride, long long out_outer,
-                                long long out_stride, const float2* tw, const float* out_scale, cudaStream_t st) {
+                                long long out_stride, const float2* tw, const float* out_scale, ColPrune pr,
+                                cudaStream_t st) {
   auto f = k_col<L, INV, PAD_IN, CROP_OUT, OutT>;
   cudaError_t e = set_smem(f, fft_smem(L));
   if (e != cudaSuccess) return e;
   const int n_chunks = row_len / FFT_W;
   const long long grid = (long long)n_outer * n_chunks;
   f<<<(unsigned)grid, COL_NT, fft_smem(L), st>>>(in, out, N, n_chunks, in_outer, in_stride, out_outer,
-                                                 out_stride, tw, out_scale);
+                                                 out_stride, tw, out_scale, pr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
                            long long in_outer, long long in_stride, long long out_outer, long long out_stride,
-                           const float2* tw, cudaStream_t st) {
+                           const float2* tw, cudaStream_t st, ColPrune pr) {
   switch (L) {
-#define CASE_L(V) case V: return launch_col_t<V, false, true, false, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, nullptr, st);
+#define CASE_L(V) case V: return launch_col_t<V, false, true, false, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, nullptr, pr, st);
     NUFFT_FFT_SIZES(CASE_L)
 #undef CASE_L
   }
@@ -345,16 +395,17 @@ cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_ou
 
 cudaError_t launch_col_fwd_lp(int L, int dtype, const float2* in, void* out, int N, int n_outer, int row_len,
                               long long in_outer, long long in_stride, long long out_outer,
-                              long long out_stride, const float2* tw, const float* scale, cudaStream_t st) {
+                              long long out_stride, const float2* tw, const float* scale, cudaStream_t st,
+                              ColPrune pr) {
   if (dtype == 1) {
     switch (L) {
-#define CASE_L(V) case V: return launch_col_t<V, false, true, false, __nv_bfloat162>(in, (__nv_bfloat162*)out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, scale, st);
+#define CASE_L(V) case V: return launch_col_t<V, false, true, false, __nv_bfloat162>(in, (__nv_bfloat162*)out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, scale, pr, st);
       NUFFT_FFT_SIZES(CASE_L)
 #undef CASE_L
     }
   } else {
     switch (L) {
-#define CASE_L(V) case V: return launch_col_t<V, false, true, false, __half2>(in, (__half2*)out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, scale, st);
+#define CASE_L(V) case V: return launch_col_t<V, false, true, false, __half2>(in, (__half2*)out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, scale, pr, st);
       NUFFT_FFT_SIZES(CASE_L)
 #undef CASE_L
     }
@@ -364,9 +415,9 @@ cudaError_t launch_col_fwd_lp(int L, int dtype, const float2* in, void* out, int
 
 cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
                            long long in_outer, long long in_stride, long long out_outer, long long out_stride,
-                           const float2* tw, cudaStream_t st) {
+                           const float2* tw, cudaStream_t st, ColPrune pr) {
   switch (L) {
-#define CASE_L(V) case V: return launch_col_t<V, true, false, true, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, nullptr, st);
+#define CASE_L(V) case V: return launch_col_t<V, true, false, true, float2>(in, out, N, n_outer, row_len, in_outer, in_stride, out_outer, out_stride, tw, nullptr, pr, st);
     NUFFT_FFT_SIZES(CASE_L)
 #undef CASE_L
   }

@@ -40,6 +40,20 @@ struct InterpGeom {
   const CUtensorMap* tmap = nullptr;  // host copy of the grid's tensor map (gather variant 8), or null
 };
 
+// Pruning of the column FFT passes to the cells the interpolation touches:
+// the ball |k| <= R in centred grid frequencies (R = K/2 + (J/2) sqrt 3 + 1
+// covers every tap of every point with |u| <= K/2).  mode 1: y passes (rows
+// ky, column kx; test kx^2 + ky^2 <= r2); mode 2: z passes (rows kz, columns
+// (kx, ky = outer index); columns outside the disk skipped, rows tested with
+// the ball).  Forward passes skip whole-row stores no column needs, inverse
+// passes skip the loads of cells outside the ball (which are not cleared).
+struct ColPrune {
+  int mode = 0;
+  int K = 0;
+  long long r2 = 0;
+  int consume = 0;  // inverse z pass: zero every grid row it reads (the adjoint grid is left clear)
+};
+
 bool fft_length_supported(int L);
 cudaError_t launch_row_fwd(int K, const void* vol, int cplx, float2* out, const float* s, int N,
                            const float2* tw, cudaStream_t st);
@@ -47,14 +61,15 @@ cudaError_t launch_row_adj(int K, const float2* in, void* vol, int cplx, const f
                            const float2* tw, cudaStream_t st);
 cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
                            long long in_outer, long long in_stride, long long out_outer, long long out_stride,
-                           const float2* tw, cudaStream_t st);
+                           const float2* tw, cudaStream_t st, ColPrune pr = ColPrune{});
 cudaError_t launch_col_fwd_lp(int L, int dtype, const float2* in, void* out, int N, int n_outer, int row_len,
                               long long in_outer, long long in_stride, long long out_outer,
-                              long long out_stride, const float2* tw, const float* bound, cudaStream_t st);
+                              long long out_stride, const float2* tw, const float* bound, cudaStream_t st,
+                              ColPrune pr = ColPrune{});
 cudaError_t launch_abs_bound(const void* vol, int cplx, const float* s, int N, float* bound, cudaStream_t st);
 cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_outer, int row_len,
                            long long in_outer, long long in_stride, long long out_outer, long long out_stride,
-                           const float2* tw, cudaStream_t st);
+                           const float2* tw, cudaStream_t st, ColPrune pr = ColPrune{});
 cudaError_t launch_line(int M, bool fwd, const float2* in, float2* out, int D, const float2* w,
                         const float2* tw, cudaStream_t st);
 
@@ -93,6 +108,7 @@ struct nufft3d_plan_s {
   CUtensorMap tmap_grid{};  // tensor map of the grid the gather reads (d_grid or d_grid_lp)
   bool tmap_ok = false;
   double poly_err = 0.0;  // max |fit - exact| / max |c| of the polynomials (0 with a table)
+  long long ball_r2 = 0;  // squared radius of the ball of grid cells the interpolation touches
   int complex_volume, do_line_fft, grid_dtype;
   int T, nT;  // tile edge and tiles per axis
   int gather_variant, spread_variant, pts_per_sub;
@@ -114,7 +130,9 @@ struct nufft3d_plan_s {
   int n_pairs = 0;                // antipodal line pairs merged
   int4* d_sub = nullptr;
   int n_sub = 0;
-  float2* d_grid = nullptr;   // K^3
+  float2* d_grid = nullptr;   // K^3 (forward grid; also the adjoint grid with a reduced-precision forward grid)
+  float2* d_grid_adj = nullptr;  // K^3 adjoint grid with a complex64 forward grid (kept clear between calls)
+  bool adj_dirty = false;        // the adjoint grid may hold values (a call stopped before the z pass)
   void* d_grid_lp = nullptr;  // K^3 reduced precision (grid_dtype != 0)
   float2* d_bufA = nullptr;   // N * N * K
   float2* d_bufB = nullptr;   // N * K * K

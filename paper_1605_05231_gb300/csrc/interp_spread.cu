@@ -252,15 +252,16 @@ __global__ void __launch_bounds__(V2_WARPS * 32, 1) k_spread_v2(InterpGeom g, co
 // spread variant 3 (J = 6, T = 8): variant 2 with more warps per SM and less
 // shared-memory traffic per point.  The coefficient table is read through L1
 // in phase 1 (freeing its 49 KB of shared memory for two more warps per SM),
-// a point's tile offset and value travel as one float4, and the coefficients
-// of the next point are loaded into registers while the current point's
-// read-modify-writes drain.
+// phase 1 folds the point's value into its z coefficients (v conj(cz)) so that
+// phase 2 reads only the tile offset besides the coefficients, and the
+// coefficients of the next point are loaded into registers while the current
+// point's read-modify-writes drain.
 // ---------------------------------------------------------------------------
 constexpr int V3S_WARPS = 10;
 
 __host__ __device__ inline size_t v3s_warp_bytes(int T) {
   const int E = T + 5;
-  const size_t w = (size_t)32 * V2_CSTRIDE * sizeof(float2) + 32 * sizeof(float4) +
+  const size_t w = (size_t)32 * V2_CSTRIDE * sizeof(float2) + 32 * sizeof(int) +
                    (size_t)E * E * E * sizeof(float2);
   return (w + 15) / 16 * 16;
 }
@@ -268,15 +269,15 @@ __host__ __device__ inline size_t v3s_warp_bytes(int T) {
 __host__ __device__ inline size_t v3s_bytes(int T) { return V3S_WARPS * v3s_warp_bytes(T); }
 
 struct V3SCoef {
-  float2 cx, cy, ox, oy, oz;
-  float4 z01, z23, z45;
-  float4 mv;  // tile offset (int bits), value
+  float2 cx, cy, ox, oy;
+  float4 z01, z23, z45;  // v conj(cz[0..5])
+  int mo;                // tile offset, or -1
 };
 
-__device__ __forceinline__ void v3s_load(const float2* coef, const float4* mvs, int p, const V2Lanes& ln,
+__device__ __forceinline__ void v3s_load(const float2* coef, const int* mos, int p, const V2Lanes& ln,
                                          V3SCoef& c) {
   const float2* cp = coef + p * V2_CSTRIDE;
-  c.mv = mvs[p];
+  c.mo = mos[p];
   c.cx = cp[ln.mjx];
   c.cy = cp[6 + ln.mjy];
   c.z01 = *(const float4*)(cp + 12);
@@ -284,37 +285,39 @@ __device__ __forceinline__ void v3s_load(const float2* coef, const float4* mvs, 
   c.z45 = *(const float4*)(cp + 16);
   c.ox = cp[ln.ojx];
   c.oy = cp[6 + ln.ojy];
-  c.oz = cp[12 + ln.ojz];
 }
 
 // read-modify-write of one point's taps held by this lane
 template <int PP>
 __device__ __forceinline__ void v3s_apply(float2* tile, const V3SCoef& c, const V2Lanes& ln, int lane) {
-  const int mo = __float_as_int(c.mv.x);
-  if (mo < 0) return;
-  const float2 v = make_float2(c.mv.y, c.mv.z);
-  const float2 a = cmulc(v, cmul(c.cx, c.cy));  // v conj(cx cy)
-  float2* tp = tile + mo + ln.main_off;
+  if (c.mo < 0) return;
+  // contribution conj(cx cy) (v conj(cz)) = v conj(cx cy cz)
+  const float2 p = cmul(c.cx, c.cy);
+  float2* tp = tile + c.mo + ln.main_off;
   float2 t[6];
 #pragma unroll
   for (int jz = 0; jz < 6; ++jz) t[jz] = tp[jz * PP];
-  const float2 cz[6] = {make_float2(c.z01.x, c.z01.y), make_float2(c.z01.z, c.z01.w),
+  const float2 zv[6] = {make_float2(c.z01.x, c.z01.y), make_float2(c.z01.z, c.z01.w),
                         make_float2(c.z23.x, c.z23.y), make_float2(c.z23.z, c.z23.w),
                         make_float2(c.z45.x, c.z45.y), make_float2(c.z45.z, c.z45.w)};
 #pragma unroll
   for (int jz = 0; jz < 6; ++jz) {
-    t[jz].x = fmaf(a.x, cz[jz].x, fmaf(a.y, cz[jz].y, t[jz].x));
-    t[jz].y = fmaf(a.y, cz[jz].x, fmaf(-a.x, cz[jz].y, t[jz].y));
+    t[jz].x = fmaf(p.x, zv[jz].x, fmaf(p.y, zv[jz].y, t[jz].x));
+    t[jz].y = fmaf(p.x, zv[jz].y, fmaf(-p.y, zv[jz].x, t[jz].y));
   }
 #pragma unroll
   for (int jz = 0; jz < 6; ++jz) tp[jz * PP] = t[jz];
   if (lane < 24) {
-    const float2 w = cmulc(v, cmul(cmul(c.ox, c.oy), c.oz));
-    float2* q = tile + mo + ln.ovf_off;
-    float2 u = *q;
-    u.x += w.x;
-    u.y += w.y;
-    *q = u;
+    // the lane's overflow tap takes v conj(cz) of its own jz (a register select)
+    float2 z = zv[0];
+#pragma unroll
+    for (int jz = 1; jz < 6; ++jz) z = ln.ojz == jz ? zv[jz] : z;
+    const float2 q = cmul(c.ox, c.oy);
+    float2* r = tile + c.mo + ln.ovf_off;
+    float2 u = *r;
+    u.x = fmaf(q.x, z.x, fmaf(q.y, z.y, u.x));
+    u.y = fmaf(q.x, z.y, fmaf(-q.y, z.x, u.y));
+    *r = u;
   }
 }
 
@@ -329,8 +332,8 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
   const int nT = g.nT, K = g.K;
   const size_t KK = (size_t)K * K;
   float2* coef = (float2*)(smem_raw + warp * v3s_warp_bytes(T));
-  float4* mvs = (float4*)(coef + 32 * V2_CSTRIDE);
-  float2* tile = (float2*)(mvs + 32);
+  int* mos = (int*)(coef + 32 * V2_CSTRIDE);
+  float2* tile = (float2*)(mos + 32);
   for (int i = lane; i < E3; i += 32) tile[i] = make_float2(0.f, 0.f);
   __syncwarp();
   const V2Lanes ln = v2_lanes(E, lane);
@@ -362,6 +365,10 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
           for (int a = 0; a < 3; ++a) {
             float2 c[6];
             point_coeffs<6>(g, f[a], c);
+            if (a == 2) {
+#pragma unroll
+              for (int q = 0; q < 6; ++q) c[q] = cmulc(val, c[q]);  // v conj(cz)
+            }
 #pragma unroll
             for (int q = 0; q < 3; ++q) c4[a * 3 + q] = make_float4(c[2 * q].x, c[2 * q].y, c[2 * q + 1].x, c[2 * q + 1].y);
           }
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
           atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
         }
       }
-      mvs[lane] = make_float4(__int_as_float(off), val.x, val.y, 0.f);
+      mos[lane] = off;
       __syncwarp();
       const int np = min(32, sp.z - b0);
       // two points per iteration: the second point's coefficients load while
@@ -377,8 +384,8 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
       int p = 0;
       for (; p + 1 < np; p += 2) {
         V3SCoef c0, c1;
-        v3s_load(coef, mvs, p, ln, c0);
-        v3s_load(coef, mvs, p + 1, ln, c1);
+        v3s_load(coef, mos, p, ln, c0);
+        v3s_load(coef, mos, p + 1, ln, c1);
         v3s_apply<PP>(tile, c0, ln, lane);
         __syncwarp();
         v3s_apply<PP>(tile, c1, ln, lane);
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
       }
       if (p < np) {
         V3SCoef c0;
-        v3s_load(coef, mvs, p, ln, c0);
+        v3s_load(coef, mos, p, ln, c0);
         v3s_apply<PP>(tile, c0, ln, lane);
         __syncwarp();
       }

@@ -367,7 +367,7 @@ cudaError_t upload(T** p, const std::vector<T>& v, cudaStream_t st) {
 void free_plan(nufft3d_plan pl) {
   if (!pl) return;
   void* ptrs[] = {pl->d_dir, pl->d_rad, pl->d_weight, pl->d_s, pl->d_table, pl->d_twK, pl->d_twM,
-                  pl->d_sorted, pl->d_sub, pl->d_grid, pl->d_grid_lp, pl->d_bufA, pl->d_bufB,
+                  pl->d_sorted, pl->d_sub, pl->d_grid, pl->d_grid_adj, pl->d_grid_lp, pl->d_bufA, pl->d_bufB,
                   pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -485,6 +485,12 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->J = r.J;
   pl->L = r.L;
   pl->poly = h.poly;
+  {
+    // every tap of a point with |u| <= K/2 lies within (J/2) sqrt 3 of it; one
+    // more cell covers a rounding of the tap base
+    const double R = 0.5 * r.K + 0.5 * r.J * std::sqrt(3.0) + 1.0;
+    pl->ball_r2 = (long long)std::ceil(R * R);
+  }
   pl->poly_err = h.poly_err;
   pl->D = r.D;
   pl->M = r.M;
@@ -522,6 +528,13 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   if (rc != NUFFT3D_OK) return rc;
   const size_t K3 = (size_t)r.K * r.K * r.K;
   CK(dalloc(&pl->d_grid, K3));
+  if (r.grid_dtype == NUFFT3D_GRID_C64) {
+    CK(dalloc(&pl->d_grid_adj, K3));
+    CK(cudaMemsetAsync(pl->d_grid_adj, 0, K3 * sizeof(float2), st));
+  } else {
+    CK(cudaMemsetAsync(pl->d_grid, 0, K3 * sizeof(float2), st));  // the adjoint grid
+  }
+  pl->adj_dirty = false;
   if (r.grid_dtype != NUFFT3D_GRID_C64) {
     CK(cudaMalloc(&pl->d_grid_lp, K3 * 4));
     CK(dalloc(&pl->d_lp_bound, 1));
@@ -555,6 +568,14 @@ struct StageClock {
   cudaError_t mark(int stage) { return ev ? cudaEventRecord(ev[stage + 1], st) : cudaSuccess; }
 };
 
+nufft::ColPrune prune(const nufft3d_plan pl, int mode) {
+  nufft::ColPrune p;
+  p.mode = mode;
+  p.K = pl->K;
+  p.r2 = pl->ball_r2;
+  return p;
+}
+
 int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st) {
   const int N = pl->N, K = pl->K;
   const long long KK = (long long)K * K;
@@ -569,10 +590,10 @@ int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st)
   const void* grid = pl->d_grid;
   float inv_scale = 1.f;
   if (pl->grid_dtype == NUFFT3D_GRID_C64) {
-    CK(nufft::launch_col_fwd(K, pl->d_bufB, pl->d_grid, N, K, K, K, KK, K, KK, pl->d_twK, st));
+    CK(nufft::launch_col_fwd(K, pl->d_bufB, pl->d_grid, N, K, K, K, KK, K, KK, pl->d_twK, st, prune(pl, 2)));
   } else {
     CK(nufft::launch_col_fwd_lp(K, pl->grid_dtype, pl->d_bufB, pl->d_grid_lp, N, K, K, K, KK, K, KK, pl->d_twK,
-                                pl->d_lp_bound, st));
+                                pl->d_lp_bound, st, prune(pl, 2)));
     grid = pl->d_grid_lp;
   }
   CK(clk.mark(2));
@@ -597,14 +618,23 @@ int adjoint_impl(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st)
     src = pl->d_lines;
   }
   CK(clk.mark(0));
-  CK(cudaMemsetAsync(pl->d_grid, 0, (size_t)K * KK * sizeof(float2), st));
+  // the adjoint grid is clear between calls: the inverse z pass zeroes every
+  // cell it reads, and nothing outside the touched ball is ever written.  A
+  // call that stopped between the spread and that pass left it dirty.
+  float2* ag = pl->d_grid_adj ? pl->d_grid_adj : pl->d_grid;
+  if (pl->adj_dirty) CK(cudaMemsetAsync(ag, 0, (size_t)K * KK * sizeof(float2), st));
   CK(clk.mark(1));
   InterpGeom g = geom(pl);
-  CK(nufft::launch_spread(g, pl->spread_variant, src, pl->d_sub, pl->n_sub, pl->d_grid, st));
+  pl->adj_dirty = true;
+  CK(nufft::launch_spread(g, pl->spread_variant, src, pl->d_sub, pl->n_sub, ag, st));
   CK(clk.mark(2));
-  CK(nufft::launch_col_inv(K, pl->d_grid, pl->d_bufB, N, K, K, K, KK, K, KK, pl->d_twK, st));
+  nufft::ColPrune pz = prune(pl, 2);
+  pz.consume = 1;
+  CK(nufft::launch_col_inv(K, ag, pl->d_bufB, N, K, K, K, KK, K, KK, pl->d_twK, st, pz));
+  pl->adj_dirty = false;
   CK(clk.mark(3));
-  CK(nufft::launch_col_inv(K, pl->d_bufB, pl->d_bufA, N, N, K, KK, K, (long long)N * K, K, pl->d_twK, st));
+  CK(nufft::launch_col_inv(K, pl->d_bufB, pl->d_bufA, N, N, K, KK, K, (long long)N * K, K, pl->d_twK, st,
+                           prune(pl, 1)));
   CK(clk.mark(4));
   CK(nufft::launch_row_adj(K, pl->d_bufA, vol, pl->complex_volume, pl->d_s, N, pl->d_twK, st));
   CK(clk.mark(5));
@@ -674,6 +704,7 @@ int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes) {
   size_t b = 0;
   b += K3 * sizeof(float2);
   if (r.grid_dtype != NUFFT3D_GRID_C64) b += K3 * 4 + sizeof(float);
+  else b += K3 * sizeof(float2);  // separate adjoint grid
   b += (size_t)r.N * r.N * r.K * sizeof(float2);
   b += (size_t)r.N * r.K * r.K * sizeof(float2);
   if (r.line_fft) b += (size_t)r.P * sizeof(float2);

@@ -291,3 +291,24 @@ def test_host_pipeline_matches_device_path(cuda_lib):
         ref_o = plan.adjoint(ref_l)
         assert torch.allclose(l, ref_l.cpu(), rtol=0, atol=1e-5 * float(ref_l.abs().max()))
         assert torch.allclose(o, ref_o.cpu(), rtol=0, atol=1e-5 * float(ref_o.abs().max()))
+
+
+@pytest.mark.parametrize("grid_dtype", ["c64", "bf16"])
+def test_adjoint_grid_left_clear_between_calls(cuda_lib, grid_dtype):
+    """The inverse z pass clears the adjoint grid as it reads it, so repeated
+    adjoints, with forward calls in between, must keep agreeing with the
+    oracle (a leftover value would add to the next call)."""
+    import torch
+
+    n, ndir = 32, 300
+    dirs = I.random_directions(ndir, 91)
+    x = torch.from_numpy(I.random_volume(n, 92).astype(np.float32)).cuda()
+    ys = [I.random_lines(ndir, 2 * n, 93 + i).astype(np.complex64) for i in range(3)]
+    plan = cuda_lib.Plan(n, dirs, grid_dtype=grid_dtype)
+    op = _oplan(n, dirs)
+    for rep in range(2):
+        for y in ys:
+            a = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+            plan.forward(x)
+            assert O.rel_l2(a, O.nufft_adjoint(y.astype(np.complex128), op)) < TOL, rep
+    assert plan.sync_status() == 0

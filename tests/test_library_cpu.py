@@ -54,9 +54,11 @@ def _ws(**kw):
 def test_workspace_bytes_counts_grid_and_buffers(lib):
     b = _ws()
     K, N, D, M = 64, 32, 3, 64
-    expect = K ** 3 * 8 + N * N * K * 8 + N * K * K * 8 + D * M * 8 + D * M * 4
+    # forward grid + adjoint grid + FFT intermediates + line buffer + point sort
+    expect = 2 * K ** 3 * 8 + N * N * K * 8 + N * K * K * 8 + D * M * 8 + D * M * 4
     assert expect <= b < expect + 200_000
-    assert _ws(grid_dtype="bf16") == b + K ** 3 * 4 + 4
+    # a reduced-precision forward grid replaces the separate adjoint grid
+    assert _ws(grid_dtype="bf16") == b - K ** 3 * 8 + K ** 3 * 4 + 4
     assert _ws(do_line_fft=False) == b - D * M * 8
     assert _ws(exact_coeffs=1) == b - 1025 * 6 * 8   # no table
 
