@@ -158,26 +158,34 @@ def stage_work(n, k, j, m, d, p_eval=None):
     }
 
 
-def cufft_compare(K: int, dev, reps: int = 10):
-    """Milliseconds of cuFFT's complex-to-complex K^3 forward and inverse
-    transforms (through torch.fft) on a resident complex64 grid, event-timed."""
+def cufft_compare(K: int, D: int, M: int, dev, reps: int = 10):
+    """Milliseconds of cuFFT (through torch.fft) on resident complex64 data of
+    the workload's shapes, event-timed: the K^3 forward and inverse transforms
+    and the batch of D line transforms of length M."""
     import torch
 
-    g = torch.randn((K, K, K), dtype=torch.complex64, device=dev)
     s = torch.cuda.current_stream(dev)
     out = {}
-    for name, fn in (("cufft_fftn_ms", torch.fft.fftn), ("cufft_ifftn_ms", torch.fft.ifftn)):
+
+    def timed(fn, x):
         for _ in range(3):
-            fn(g)
+            fn(x)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(s)
         for _ in range(reps):
-            fn(g)
+            fn(x)
         e1.record(s)
         e1.synchronize()
-        out[name] = round(e0.elapsed_time(e1) / reps, 4)
+        return round(e0.elapsed_time(e1) / reps, 4)
+
+    g = torch.randn((K, K, K), dtype=torch.complex64, device=dev)
+    out["cufft_fftn_ms"] = timed(torch.fft.fftn, g)
+    out["cufft_ifftn_ms"] = timed(torch.fft.ifftn, g)
     del g
+    lines = torch.randn((D, M), dtype=torch.complex64, device=dev)
+    out["cufft_lines_ifft_ms"] = timed(lambda x: torch.fft.ifft(x, dim=1), lines)
+    del lines
     torch.cuda.empty_cache()
     return out
 
@@ -498,12 +506,14 @@ def run_ours(args):
     # ---- cuFFT on the same grid, timed only as a comparison --------------
     fft_cmp = None
     if not args.no_fft_compare:
-        fft_cmp = cufft_compare(w.k, dev)
+        fft_cmp = cufft_compare(w.k, plan.n_dirs, w.m, dev)
         fft_cmp["ours_forward_ms"] = round(sum(per_call[("forward", s)] for s in ("x_pass", "y_pass", "z_pass")), 4)
         fft_cmp["ours_inverse_ms"] = round(sum(per_call[("adjoint", s)] for s in ("z_pass", "y_pass", "x_pass")), 4)
+        fft_cmp["ours_line_dft_ms"] = round(per_call[("forward", "line_dft")], 4)
         fft_cmp["note"] = ("ours: the pruned 3D transform with the zero padding / cropping and the deapodisation "
-                           "fused (x, y, z passes); cuFFT: a full complex-to-complex K^3 transform of a "
-                           "resident grid (torch.fft), nothing fused")
+                           "fused (x, y, z passes), and the centred weighted line DFT; cuFFT: a full "
+                           "complex-to-complex K^3 transform of a resident grid and a plain batched line "
+                           "transform (torch.fft), nothing fused")
 
     # ---- CPU oracle baseline (rank 0, N = 1) ----------------------------
     cpu = None
