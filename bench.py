@@ -313,8 +313,8 @@ def oracle_points(op, Y, lines):
     t0 = time.perf_counter()
     u = op.point_u(lines).reshape(-1, 3)
     Xh = O.interp_gather(Y, u, op).reshape(len(lines), op.M)
-    p = O.radial_idft(Xh, op)
-    Yh = O.radial_idft_adjoint(p, op)
+    p = O.radial_idft(Xh, op, lines)
+    Yh = O.radial_idft_adjoint(p, op, lines)
     O.interp_spread(Yh.reshape(-1), u, op)
     return time.perf_counter() - t0
 

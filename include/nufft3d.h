@@ -97,6 +97,11 @@ typedef struct {
                              interpolant in FP64 and evaluates it per point in FP32;
                              a fit further than 1e-7 max|c| from c is refused with
                              NUFFT3D_ERR_UNSUPPORTED (plan_info reports the error) */
+  const float* line_weight; /* host, D real per-line weights lw[l], or NULL for 1; the
+                             line DFTs use lw[l] w[q] (forward) and lw[l] conj(w[q])
+                             (adjoint); copied.  With the weights of
+                             nufft3d_fourier_slice_weights the adjoint is the
+                             direct reconstruction of Sec. 2.3 */
 } nufft3d_params;
 
 /* Create a plan.  Validates *p, computes in FP64 on the host the scaling
@@ -133,6 +138,25 @@ int nufft3d_plan_sync_status(nufft3d_plan plan, int* device_status);
 
 /* Free a plan and everything it owns (NULL is accepted). */
 int nufft3d_plan_destroy(nufft3d_plan plan);
+
+/* Weights that turn the adjoint into the direct (Fourier-slice) reconstruction
+ * that inverts the image-to-Radon step (Sec. 2.3: ramp filtering in the
+ * Fourier domain, then the NUFFT transpose; Sec. 1: the 3D parallel-beam
+ * ramp filter is R^2).  The reconstruction is a quadrature of the inverse 3D
+ * Fourier transform in spherical coordinates, x[n] ~ (2 pi)^-3 sum |w|^2 dw
+ * dOmega X(w) e^{i w.n}, over the umbrella directions of Eq. 2.1 (phi_a = 2 pi
+ * a / n_az, theta_p = c + (pi - 2c)(p + 1/2) / n_pol, c = cone_half_angle,
+ * azimuth-major l = a n_pol + p).  Every Fourier point lies on two antipodal
+ * lines, and the adjoint's line DFT carries a factor 1/M, so:
+ *   line_weight[l]  = sin(theta_p) (pi - 2c)/n_pol (2 pi/n_az) / 2  (half the solid-angle cell)
+ *   radial_weight[q] = q^2 / M^2 for q != 0 (complex, imaginary part 0),
+ *   radial_weight[0] = pi / (6 M^2 sum_l line_weight[l])   (the ball |w| < pi/M around the origin)
+ * for q = m - M/2.  radial_weight holds 2 M floats (interleaved complex),
+ * line_weight n_az n_pol floats.  Pass them as weight and line_weight of a plan
+ * over those directions with do_line_fft = 1 and M samples per line; its
+ * adjoint of plane integrals is the reconstruction.  Host only. */
+int nufft3d_fourier_slice_weights(int n_az, int n_pol, double cone_half_angle, int m, float* radial_weight,
+                                  float* line_weight);
 
 /* Static description of a status code (never NULL). */
 const char* nufft3d_error_string(int status);

@@ -164,6 +164,7 @@ class OraclePlan:
     weight: Optional[np.ndarray] = None  # (M,) complex; None -> 1
     complex_volume: bool = False
     do_line_fft: bool = True
+    line_weight: Optional[np.ndarray] = None  # (D,) real per-line weights; None -> 1
 
     def __post_init__(self):
         self.dirs = np.asarray(self.dirs, dtype=np.float64).reshape(-1, 3)
@@ -174,6 +175,11 @@ class OraclePlan:
         w = np.ones(self.M, dtype=np.complex128) if self.weight is None else \
             np.asarray(self.weight, dtype=np.complex128)
         self.w = w
+        self.lw = (np.ones(self.dirs.shape[0]) if self.line_weight is None else
+                   np.asarray(self.line_weight, dtype=np.float64).reshape(-1))
+
+    def line_weights(self, lines=None) -> np.ndarray:
+        return self.lw if lines is None else self.lw[np.asarray(lines)]
 
     @property
     def D(self) -> int:
@@ -290,17 +296,19 @@ def line_exponent(M: int) -> np.ndarray:
     return np.exp(2j * np.pi * np.outer(q, q) / M)
 
 
-def radial_idft(Xhat: np.ndarray, plan: OraclePlan) -> np.ndarray:
-    """p[l][s] = (1/M) sum_q w[q] X^[l][q] exp(+2 pi i q s / M)  (Fourier Slice
-    Theorem, Sec. 2.2.1; Eqs. 2.2-2.7 in the radial coordinate)."""
+def radial_idft(Xhat: np.ndarray, plan: OraclePlan, lines=None) -> np.ndarray:
+    """p[l][s] = (1/M) lw[l] sum_q w[q] X^[l][q] exp(+2 pi i q s / M)  (Fourier
+    Slice Theorem, Sec. 2.2.1; Eqs. 2.2-2.7 in the radial coordinate)."""
     M = plan.M
-    return ((Xhat * plan.w[None, :]) @ line_exponent(M)) / M
+    lw = plan.line_weights(lines)[:, None]
+    return ((Xhat * plan.w[None, :] * lw) @ line_exponent(M)) / M
 
 
-def radial_idft_adjoint(y: np.ndarray, plan: OraclePlan) -> np.ndarray:
-    """Y^[l][q] = (1/M) conj(w[q]) sum_s y[l][s] exp(-2 pi i q s / M)."""
+def radial_idft_adjoint(y: np.ndarray, plan: OraclePlan, lines=None) -> np.ndarray:
+    """Y^[l][q] = (1/M) lw[l] conj(w[q]) sum_s y[l][s] exp(-2 pi i q s / M)."""
     M = plan.M
-    return (y @ np.conj(line_exponent(M)).T) * np.conj(plan.w)[None, :] / M
+    lw = plan.line_weights(lines)[:, None]
+    return (y @ np.conj(line_exponent(M)).T) * np.conj(plan.w)[None, :] * lw / M
 
 
 # -----------------------------------------------------------------------------
@@ -316,12 +324,12 @@ def nufft_forward(x: np.ndarray, plan: OraclePlan, lines=None, return_samples: b
     Xhat = interp_gather(Y, u.reshape(-1, 3), plan).reshape(nl, plan.M)
     if return_samples or not plan.do_line_fft:
         return Xhat
-    return radial_idft(Xhat, plan)
+    return radial_idft(Xhat, plan, lines)
 
 
 def nufft_adjoint(y: np.ndarray, plan: OraclePlan, lines=None) -> np.ndarray:
     """Adjoint of nufft_forward: line data (D, M) (or the selected lines) -> volume."""
-    Yhat = radial_idft_adjoint(y, plan) if plan.do_line_fft else y
+    Yhat = radial_idft_adjoint(y, plan, lines) if plan.do_line_fft else y
     u = plan.point_u(lines)
     G = interp_spread(Yhat.reshape(-1), u.reshape(-1, 3), plan)
     return crop_deapodize(grid_ifft_unnormalised(G), plan)
@@ -357,7 +365,7 @@ def forward_exact(x: np.ndarray, plan: OraclePlan, lines=None, return_samples: b
     X = nudft_type2(x, om.reshape(-1, 3)).reshape(d.shape[0], plan.M)
     if return_samples:
         return X
-    return radial_idft(X, plan)
+    return radial_idft(X, plan, lines)
 
 
 def dirichlet_kernel(t: np.ndarray, M: int) -> np.ndarray:

@@ -35,6 +35,7 @@ EXPORTS = (
     "nufft3d_batch_forward_adjoint",
     "nufft3d_batch_invalidate",
     "nufft3d_batch_destroy",
+    "nufft3d_fourier_slice_weights",
 )
 
 FWD_STAGES = ("x_pass", "y_pass", "z_pass", "gather", "line_dft")
@@ -61,6 +62,7 @@ class Params(ctypes.Structure):
         ("do_line_fft", ctypes.c_int),
         ("keep_duplicates", ctypes.c_int),
         ("exact_coeffs", ctypes.c_int),
+        ("line_weight", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -105,6 +107,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     fp = ctypes.POINTER(ctypes.c_float)
     lib.nufft3d_plan_set_timing.argtypes = [vp, i]
     lib.nufft3d_plan_stage_times.argtypes = [vp, fp, fp, ip]
+    lib.nufft3d_fourier_slice_weights.argtypes = [i, i, ctypes.c_double, i, fp, fp]
     for name in EXPORTS:
         if name != "nufft3d_error_string":
             getattr(lib, name).restype = ctypes.c_int
@@ -126,7 +129,8 @@ def _check(rc: int, what: str):
 
 
 def make_params(n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=None, grid_dtype="c64",
-                complex_volume=False, do_line_fft=True, keep_duplicates=False, exact_coeffs=False):
+                complex_volume=False, do_line_fft=True, keep_duplicates=False, exact_coeffs=False,
+                line_weight=None):
     """Build a Params struct plus the host arrays it points to (kept alive by the caller)."""
     dirs = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
     keep = [dirs]
@@ -152,7 +156,27 @@ def make_params(n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=
     p.do_line_fft = 1 if do_line_fft else 0
     p.keep_duplicates = 1 if keep_duplicates else 0
     p.exact_coeffs = int(exact_coeffs)
+    if line_weight is not None:
+        lw = np.ascontiguousarray(np.asarray(line_weight, dtype=np.float32).reshape(-1))
+        if lw.shape[0] != p.n_dirs:
+            raise ValueError(f"line_weight needs {p.n_dirs} values, got {lw.shape[0]}")
+        keep.append(lw)
+        p.line_weight = lw.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     return p, keep
+
+
+def fourier_slice_weights(n_az: int, n_pol: int, cone_half_angle: float, m: int):
+    """Radial (M,) complex64 and per-line (n_az n_pol,) float32 weights with which
+    the adjoint of plane integrals over the umbrella directions of Eq. 2.1 is the
+    direct Fourier-slice reconstruction (nufft3d_fourier_slice_weights).
+    cone_half_angle in radians."""
+    rw = np.zeros(2 * int(m), dtype=np.float32)
+    lw = np.zeros(int(n_az) * int(n_pol), dtype=np.float32)
+    _check(load_library().nufft3d_fourier_slice_weights(
+        int(n_az), int(n_pol), float(cone_half_angle), int(m),
+        rw.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), lw.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+        "nufft3d_fourier_slice_weights")
+    return (rw[0::2] + 1j * rw[1::2]).astype(np.complex64), lw
 
 
 def workspace_bytes(**kw) -> int:
@@ -179,7 +203,7 @@ class Plan:
 
     def __init__(self, n, dirs, m=0, k=0, j=6, table_oversamp=1024, omega=None, weight=None,
                  grid_dtype="c64", complex_volume=False, do_line_fft=True, keep_duplicates=False,
-                 exact_coeffs=False, device=None, stream=None, _handle=None):
+                 exact_coeffs=False, line_weight=None, device=None, stream=None, _handle=None):
         import torch
 
         self.lib = load_library()
@@ -187,7 +211,7 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         p, keep = make_params(n, dirs, m, k, j, table_oversamp, omega, weight, grid_dtype, complex_volume,
-                              do_line_fft, keep_duplicates, exact_coeffs)
+                              do_line_fft, keep_duplicates, exact_coeffs, line_weight)
         self.n = int(n)
         self.n_dirs = p.n_dirs
         self.m = int(m) if m else 2 * int(n)

@@ -43,8 +43,11 @@ def _compile(src: str, extra=()) -> str:
     obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
     cmd = [nvcc_path(), *_flags(src, extra), "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0 and (r.returncode < 0 or "Segmentation fault" in r.stdout + r.stderr):
+        # a crashed compiler process (not a diagnostic): run it once more
+        r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        raise RuntimeError(f"nvcc failed for {src} (exit {r.returncode}):\n{r.stdout}\n{r.stderr}")
     return obj
 
 

@@ -222,14 +222,16 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_adj(const float2* 
 }
 
 // ----------------------------------------------------------------------------
-// per-line centred DFTs.  FWD (projection): a[m] = w[m] (-1)^m X[m];
+// per-line centred DFTs.  FWD (projection): a[m] = lw[l] w[m] (-1)^m X[m];
 // p[t] = (-1)^{M/2} (-1)^t / M * sum_m a[m] e^{+2 pi i m t / M}.
-// ADJ: a[t] = (-1)^t y[t]; Y[m] = (-1)^{M/2} (-1)^m conj(w[m]) / M * sum_t a[t] e^{-2 pi i m t / M}.
+// ADJ: a[t] = (-1)^t y[t]; Y[m] = (-1)^{M/2} (-1)^m lw[l] conj(w[m]) / M * sum_t a[t] e^{-2 pi i m t / M}.
+// w: radial weights (or null for 1), lw: real per-line weights (or null for 1).
 // Rows are lines (l0 + c); in-place operation (in == out) is allowed.
 // ----------------------------------------------------------------------------
 template <int M, bool FWD>
 __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_line(const float2* in, float2* out, int D,
                                                  const float2* __restrict__ weight,
+                                                 const float* __restrict__ line_weight,
                                                  const float2* __restrict__ tw) {
   extern __shared__ float2 buf[];
   const int l0 = blockIdx.x * FFT_W;
@@ -257,13 +259,27 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_line(const float2* in,
   __syncthreads();
   smem_fft<M, FFT_W, FFT_NT, FWD>(buf, FFT_PITCH, tw);
   const float sc = (((M / 2) & 1) ? -1.f : 1.f) / (float)M;
-  for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
-    const int c = idx / M, t = idx - c * M;
-    const int l = l0 + c;
-    if (l < D) {
-      float2 v = cscale(buf[t * FFT_PITCH + c], (t & 1) ? -sc : sc);
-      if (!FWD && weight) v = cmulc(v, __ldg(weight + t));
-      out[(size_t)l * M + t] = v;
+  if (!line_weight) {
+    for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
+      const int c = idx / M, t = idx - c * M;
+      const int l = l0 + c;
+      if (l < D) {
+        float2 v = cscale(buf[t * FFT_PITCH + c], (t & 1) ? -sc : sc);
+        if (!FWD && weight) v = cmulc(v, __ldg(weight + t));
+        out[(size_t)l * M + t] = v;
+      }
+    }
+  } else {
+    // the per-line weight is a scalar: applied with the output scale (both directions)
+    for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
+      const int c = idx / M, t = idx - c * M;
+      const int l = l0 + c;
+      if (l < D) {
+        const float s_l = sc * __ldg(line_weight + l);
+        float2 v = cscale(buf[t * FFT_PITCH + c], (t & 1) ? -s_l : s_l);
+        if (!FWD && weight) v = cmulc(v, __ldg(weight + t));
+        out[(size_t)l * M + t] = v;
+      }
     }
   }
 }
@@ -425,27 +441,27 @@ cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_ou
 }
 
 template <int M, bool FWD>
-static cudaError_t launch_line_t(const float2* in, float2* out, int D, const float2* w, const float2* tw,
-                                 cudaStream_t st) {
+static cudaError_t launch_line_t(const float2* in, float2* out, int D, const float2* w, const float* lw,
+                                 const float2* tw, cudaStream_t st) {
   auto f = k_line<M, FWD>;
   cudaError_t e = set_smem(f, fft_smem(M));
   if (e != cudaSuccess) return e;
   const int grid = (D + FFT_W - 1) / FFT_W;
-  f<<<grid, FFT_NT, fft_smem(M), st>>>(in, out, D, w, tw);
+  f<<<grid, FFT_NT, fft_smem(M), st>>>(in, out, D, w, lw, tw);
   return cudaGetLastError();
 }
 
 cudaError_t launch_line(int M, bool fwd, const float2* in, float2* out, int D, const float2* w,
-                        const float2* tw, cudaStream_t st) {
+                        const float2* tw, cudaStream_t st, const float* lw) {
   if (fwd) {
     switch (M) {
-#define CASE_L(V) case V: return launch_line_t<V, true>(in, out, D, w, tw, st);
+#define CASE_L(V) case V: return launch_line_t<V, true>(in, out, D, w, lw, tw, st);
       NUFFT_FFT_SIZES(CASE_L)
 #undef CASE_L
     }
   } else {
     switch (M) {
-#define CASE_L(V) case V: return launch_line_t<V, false>(in, out, D, w, tw, st);
+#define CASE_L(V) case V: return launch_line_t<V, false>(in, out, D, w, lw, tw, st);
       NUFFT_FFT_SIZES(CASE_L)
 #undef CASE_L
     }

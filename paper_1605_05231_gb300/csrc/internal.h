@@ -71,7 +71,7 @@ cudaError_t launch_col_inv(int L, const float2* in, float2* out, int N, int n_ou
                            long long in_outer, long long in_stride, long long out_outer, long long out_stride,
                            const float2* tw, cudaStream_t st, ColPrune pr = ColPrune{});
 cudaError_t launch_line(int M, bool fwd, const float2* in, float2* out, int D, const float2* w,
-                        const float2* tw, cudaStream_t st);
+                        const float2* tw, cudaStream_t st, const float* lw = nullptr);
 
 cudaError_t launch_bin_points(const InterpGeom& g, const uint32_t* ids, long long count, uint32_t* bins,
                               cudaStream_t st);
@@ -118,6 +118,7 @@ struct nufft3d_plan_s {
   float2* d_dir = nullptr;
   float2* d_rad = nullptr;
   float2* d_weight = nullptr;  // null when w = 1
+  float* d_line_weight = nullptr;  // D real per-line weights, null when 1
   float* d_s = nullptr;
   float2* d_table = nullptr;
   float2* d_twK = nullptr;

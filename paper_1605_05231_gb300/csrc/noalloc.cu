@@ -97,7 +97,7 @@ extern "C" int nufft3d_adjoint_noalloc(nufft3d_plan pl, const void* lines_dev, v
 
   const float2* src = (const float2*)lines_dev;
   if (pl->do_line_fft) {
-    e = nufft::launch_line(pl->M, false, src, lines_tmp, pl->D, pl->d_weight, pl->d_twM, st);
+    e = nufft::launch_line(pl->M, false, src, lines_tmp, pl->D, pl->d_weight, pl->d_twM, st, pl->d_line_weight);
     if (e != cudaSuccess) return status_of(e);
     src = lines_tmp;
   }

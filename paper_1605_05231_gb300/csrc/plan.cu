@@ -71,6 +71,10 @@ int resolve(const nufft3d_params* p, Resolved& r) {
     for (int m = 0; m < 2 * r.M; ++m)
       if (!std::isfinite(p->weight[m])) return NUFFT3D_ERR_ARG;
   }
+  if (p->line_weight) {
+    for (int l = 0; l < r.D; ++l)
+      if (!std::isfinite(p->line_weight[l])) return NUFFT3D_ERR_ARG;
+  }
   r.T = r.J == 6 ? 8 : 16;
   while (r.T > 4 && (r.K % r.T != 0 || r.T + r.J - 1 > r.K)) r.T /= 2;
   r.nT = r.K / r.T;
@@ -129,6 +133,7 @@ struct HostTables {
   std::vector<float2> dir;      // D * 3 (hi, lo)
   std::vector<float2> rad;      // M (hi, lo)
   std::vector<float2> weight;   // M or empty
+  std::vector<float> line_weight;  // D or empty
   nufft::CoefPoly poly{};       // exact-coefficient mode (L = 0)
   double poly_err = 0.0;
 };
@@ -266,6 +271,7 @@ int build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
     const double rad = p->omega ? p->omega[m] * K / (2.0 * M_PI) : (double)(m - r.M / 2) * K / r.M;
     h.rad[m] = split(rad);
   }
+  if (p->line_weight) h.line_weight.assign(p->line_weight, p->line_weight + r.D);
   if (p->weight) {
     h.weight.resize(r.M);
     for (int m = 0; m < r.M; ++m) h.weight[m] = make_float2(p->weight[2 * m], p->weight[2 * m + 1]);
@@ -366,7 +372,7 @@ cudaError_t upload(T** p, const std::vector<T>& v, cudaStream_t st) {
 
 void free_plan(nufft3d_plan pl) {
   if (!pl) return;
-  void* ptrs[] = {pl->d_dir, pl->d_rad, pl->d_weight, pl->d_s, pl->d_table, pl->d_twK, pl->d_twM,
+  void* ptrs[] = {pl->d_dir, pl->d_rad, pl->d_weight, pl->d_line_weight, pl->d_s, pl->d_table, pl->d_twK, pl->d_twM,
                   pl->d_sorted, pl->d_sub, pl->d_grid, pl->d_grid_adj, pl->d_grid_lp, pl->d_bufA, pl->d_bufB,
                   pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound};
   for (void* q : ptrs)
@@ -518,6 +524,7 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   CK(upload(&pl->d_dir, h.dir, st));
   CK(upload(&pl->d_rad, h.rad, st));
   CK(upload(&pl->d_weight, h.weight, st));
+  CK(upload(&pl->d_line_weight, h.line_weight, st));
   CK(dalloc(&pl->d_err, 1));
   CK(dalloc(&pl->d_counter, 2));
   CK(cudaMemsetAsync(pl->d_err, 0, sizeof(int), st));
@@ -602,7 +609,8 @@ int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st)
                           (float2*)lines, st));
   CK(clk.mark(3));
   if (pl->do_line_fft)
-    CK(nufft::launch_line(pl->M, true, (const float2*)lines, (float2*)lines, pl->D, pl->d_weight, pl->d_twM, st));
+    CK(nufft::launch_line(pl->M, true, (const float2*)lines, (float2*)lines, pl->D, pl->d_weight, pl->d_twM, st,
+                          pl->d_line_weight));
   CK(clk.mark(4));
   return NUFFT3D_OK;
 }
@@ -614,7 +622,8 @@ int adjoint_impl(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st)
   StageClock clk(pl->ev_adj, pl->timing_slots, pl->adj_calls, ADJ_STAGES, st);
   CK(clk.mark(-1));
   if (pl->do_line_fft) {
-    CK(nufft::launch_line(pl->M, false, src, pl->d_lines, pl->D, pl->d_weight, pl->d_twM, st));
+    CK(nufft::launch_line(pl->M, false, src, pl->d_lines, pl->D, pl->d_weight, pl->d_twM, st,
+                          pl->d_line_weight));
     src = pl->d_lines;
   }
   CK(clk.mark(0));
@@ -693,6 +702,30 @@ int nufft3d_adjoint(nufft3d_plan plan, const void* lines_dev, void* vol_dev, voi
   if (rc != NUFFT3D_OK) return rc;
   plan->last_stream = (cudaStream_t)cuda_stream;
   return adjoint_impl(plan, lines_dev, vol_dev, (cudaStream_t)cuda_stream);
+}
+
+int nufft3d_fourier_slice_weights(int n_az, int n_pol, double cone_half_angle, int m, float* radial_weight,
+                                  float* line_weight) {
+  if (n_az < 1 || n_pol < 1 || m < 2 || (m & 1) || !radial_weight || !line_weight) return NUFFT3D_ERR_ARG;
+  if (!std::isfinite(cone_half_angle) || cone_half_angle < 0.0 || cone_half_angle >= 0.5 * M_PI)
+    return NUFFT3D_ERR_ARG;
+  const double dth = (M_PI - 2.0 * cone_half_angle) / n_pol, dph = 2.0 * M_PI / n_az;
+  double sum = 0.0;
+  for (int a = 0; a < n_az; ++a)
+    for (int p = 0; p < n_pol; ++p) {
+      const double th = cone_half_angle + dth * (p + 0.5);
+      const double w = 0.5 * std::sin(th) * dth * dph;
+      line_weight[(size_t)a * n_pol + p] = (float)w;
+      sum += w;
+    }
+  const double mm = (double)m * m;
+  for (int i = 0; i < m; ++i) {
+    const double q = i - m / 2;
+    const double w = q != 0.0 ? q * q / mm : M_PI / (6.0 * mm * sum);
+    radial_weight[2 * i] = (float)w;
+    radial_weight[2 * i + 1] = 0.f;
+  }
+  return NUFFT3D_OK;
 }
 
 int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes) {

@@ -76,6 +76,7 @@ def test_workspace_bytes_counts_grid_and_buffers(lib):
     (dict(m=80), -4),
     (dict(grid_dtype=3), -1),
     (dict(exact_coeffs=2), -1),
+    (dict(line_weight=np.array([1.0, np.nan, 1.0])), -1),
     (dict(dirs=np.array([[2.0, 0.0, 0.0]])), -1),   # |d| > 1
     (dict(dirs=np.array([[np.nan, 0.0, 0.0]])), -1),
     (dict(omega=np.full(64, 4.0)), -1),             # |omega| > pi
