@@ -13,13 +13,17 @@ namespace nufft {
 constexpr int FFT_W = 16;    // columns (rows) per CTA: 16 complex64 = 128 B segments
 constexpr int FFT_NT = 256;  // threads per CTA
 constexpr int FFT_PITCH = FFT_W + 1;
-// shared memory bounds residency to 3 CTAs per SM at L = 512; ask for the
-// register budget that allows the same (65536 / (3 * 256) = 85 per thread)
-constexpr int FFT_MIN_CTAS = 3;
 // column passes: 512 threads hold two radix-8 butterflies each between the
 // stages (two CTAs of 70 KB per SM, 64 registers per thread)
 constexpr int COL_NT = 512;
 constexpr int COL_MIN_CTAS = 2;
+// row passes (x) and line DFTs: 8 rows per CTA (pitch 9: the Stockham writes
+// stay conflict-free), 37 KB of shared memory at L = 512, four CTAs per SM;
+// a thread's loads of a CTA's rows are issued in one batch of ROW_CHUNK
+constexpr int ROW_W = 8;
+constexpr int ROW_PITCH = ROW_W + 1;
+constexpr int ROW_MIN_CTAS = 4;
+constexpr int ROW_CHUNK = 16;
 
 __device__ __forceinline__ int centred_to_grid(int i, int half, int L) {
   int k = i - half;
@@ -31,21 +35,21 @@ __device__ __forceinline__ int centred_to_grid(int i, int half, int L) {
 // out[(z N + y) K + kx]
 // ----------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_fwd(const void* __restrict__ vol, int cplx,
+__global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_row_fwd(const void* __restrict__ vol, int cplx,
                                                     float2* __restrict__ out, const float* __restrict__ s,
                                                     int N, const float2* __restrict__ tw) {
   extern __shared__ float2 buf[];
   const int nrows = N * N;
-  const int row0 = blockIdx.x * FFT_W;
+  const int row0 = blockIdx.x * ROW_W;
   const int half = N / 2;
   // loads of a chunk are issued before its shared stores (batched in flight)
-  for (int base = threadIdx.x; base < FFT_W * N; base += 8 * FFT_NT) {
-    float2 t[8];
+  for (int base = threadIdx.x; base < ROW_W * N; base += ROW_CHUNK * FFT_NT) {
+    float2 t[ROW_CHUNK];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < ROW_CHUNK; ++u) {
       const int idx = base + u * FFT_NT;
       t[u] = make_float2(0.f, 0.f);
-      if (idx < FFT_W * N) {
+      if (idx < ROW_W * N) {
         const int c = idx / N, x = idx - c * N;
         const int r = row0 + c;
         if (r < nrows) {
@@ -55,27 +59,27 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_fwd(const void* __
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < ROW_CHUNK; ++u) {
       const int idx = base + u * FFT_NT;
-      if (idx < FFT_W * N) {
+      if (idx < ROW_W * N) {
         const int c = idx / N, x = idx - c * N;
         const int r = row0 + c;
         const int z = r / N, y = r - z * N;
         const float sc = r < nrows ? __ldg(s + x) * __ldg(s + y) * __ldg(s + z) : 0.f;
-        buf[centred_to_grid(x, half, K) * FFT_PITCH + c] = cscale(t[u], sc);
+        buf[centred_to_grid(x, half, K) * ROW_PITCH + c] = cscale(t[u], sc);
       }
     }
   }
-  for (int idx = threadIdx.x; idx < FFT_W * (K - N); idx += FFT_NT) {
-    const int c = idx % FFT_W, i = idx / FFT_W + (N - half);
-    buf[i * FFT_PITCH + c] = make_float2(0.f, 0.f);
+  for (int idx = threadIdx.x; idx < ROW_W * (K - N); idx += FFT_NT) {
+    const int c = idx % ROW_W, i = idx / ROW_W + (N - half);
+    buf[i * ROW_PITCH + c] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  smem_fft<K, FFT_W, FFT_NT, false>(buf, FFT_PITCH, tw);
-  for (int idx = threadIdx.x; idx < FFT_W * K; idx += FFT_NT) {
+  smem_fft<K, ROW_W, FFT_NT, false>(buf, ROW_PITCH, tw);
+  for (int idx = threadIdx.x; idx < ROW_W * K; idx += FFT_NT) {
     const int c = idx / K, k = idx - c * K;
     const int r = row0 + c;
-    if (r < nrows) out[(size_t)r * K + k] = buf[k * FFT_PITCH + c];
+    if (r < nrows) out[(size_t)r * K + k] = buf[k * ROW_PITCH + c];
   }
 }
 
@@ -181,40 +185,40 @@ __global__ void __launch_bounds__(COL_NT, COL_MIN_CTAS) k_col(const float2* __re
 // inverse x pass: rows of K -> inverse FFT -> crop to N, deapodise, real part
 // ----------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_adj(const float2* __restrict__ in, void* __restrict__ vol,
+__global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_row_adj(const float2* __restrict__ in, void* __restrict__ vol,
                                                     int cplx, const float* __restrict__ s, int N,
                                                     const float2* __restrict__ tw) {
   extern __shared__ float2 buf[];
   const int nrows = N * N;
-  const int row0 = blockIdx.x * FFT_W;
+  const int row0 = blockIdx.x * ROW_W;
   const int half = N / 2;
-  for (int base = threadIdx.x; base < FFT_W * K; base += 8 * FFT_NT) {
-    float2 t[8];
+  for (int base = threadIdx.x; base < ROW_W * K; base += ROW_CHUNK * FFT_NT) {
+    float2 t[ROW_CHUNK];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < ROW_CHUNK; ++u) {
       const int idx = base + u * FFT_NT;
       const int c = idx / K, k = idx - c * K;
       const int r = row0 + c;
-      t[u] = (idx < FFT_W * K && r < nrows) ? in[(size_t)r * K + k] : make_float2(0.f, 0.f);
+      t[u] = (idx < ROW_W * K && r < nrows) ? in[(size_t)r * K + k] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < ROW_CHUNK; ++u) {
       const int idx = base + u * FFT_NT;
-      if (idx < FFT_W * K) {
+      if (idx < ROW_W * K) {
         const int c = idx / K, k = idx - c * K;
-        buf[k * FFT_PITCH + c] = t[u];
+        buf[k * ROW_PITCH + c] = t[u];
       }
     }
   }
   __syncthreads();
-  smem_fft<K, FFT_W, FFT_NT, true>(buf, FFT_PITCH, tw);
-  for (int idx = threadIdx.x; idx < FFT_W * N; idx += FFT_NT) {
+  smem_fft<K, ROW_W, FFT_NT, true>(buf, ROW_PITCH, tw);
+  for (int idx = threadIdx.x; idx < ROW_W * N; idx += FFT_NT) {
     const int c = idx / N, x = idx - c * N;
     const int r = row0 + c;
     if (r < nrows) {
       const int z = r / N, y = r - z * N;
       const float sc = __ldg(s + x) * __ldg(s + y) * __ldg(s + z);
-      const float2 v = cscale(buf[centred_to_grid(x, half, K) * FFT_PITCH + c], sc);
+      const float2 v = cscale(buf[centred_to_grid(x, half, K) * ROW_PITCH + c], sc);
       if (cplx) ((float2*)vol)[(size_t)r * N + x] = v;
       else ((float*)vol)[(size_t)r * N + x] = v.x;
     }
@@ -229,54 +233,54 @@ __global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_row_adj(const float2* 
 // Rows are lines (l0 + c); in-place operation (in == out) is allowed.
 // ----------------------------------------------------------------------------
 template <int M, bool FWD>
-__global__ void __launch_bounds__(FFT_NT, FFT_MIN_CTAS) k_line(const float2* in, float2* out, int D,
+__global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_line(const float2* in, float2* out, int D,
                                                  const float2* __restrict__ weight,
                                                  const float* __restrict__ line_weight,
                                                  const float2* __restrict__ tw) {
   extern __shared__ float2 buf[];
-  const int l0 = blockIdx.x * FFT_W;
-  for (int base = threadIdx.x; base < FFT_W * M; base += 8 * FFT_NT) {
-    float2 t[8];
+  const int l0 = blockIdx.x * ROW_W;
+  for (int base = threadIdx.x; base < ROW_W * M; base += ROW_CHUNK * FFT_NT) {
+    float2 t[ROW_CHUNK];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < ROW_CHUNK; ++u) {
       const int idx = base + u * FFT_NT;
       const int c = idx / M, m = idx - c * M;
       const int l = l0 + c;
-      t[u] = (idx < FFT_W * M && l < D) ? in[(size_t)l * M + m] : make_float2(0.f, 0.f);
+      t[u] = (idx < ROW_W * M && l < D) ? in[(size_t)l * M + m] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < ROW_CHUNK; ++u) {
       const int idx = base + u * FFT_NT;
-      if (idx < FFT_W * M) {
+      if (idx < ROW_W * M) {
         const int c = idx / M, m = idx - c * M;
         float2 v = t[u];
         if (FWD && weight) v = cmul(v, __ldg(weight + m));
         if (m & 1) v = make_float2(-v.x, -v.y);
-        buf[m * FFT_PITCH + c] = v;
+        buf[m * ROW_PITCH + c] = v;
       }
     }
   }
   __syncthreads();
-  smem_fft<M, FFT_W, FFT_NT, FWD>(buf, FFT_PITCH, tw);
+  smem_fft<M, ROW_W, FFT_NT, FWD>(buf, ROW_PITCH, tw);
   const float sc = (((M / 2) & 1) ? -1.f : 1.f) / (float)M;
   if (!line_weight) {
-    for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
+    for (int idx = threadIdx.x; idx < ROW_W * M; idx += FFT_NT) {
       const int c = idx / M, t = idx - c * M;
       const int l = l0 + c;
       if (l < D) {
-        float2 v = cscale(buf[t * FFT_PITCH + c], (t & 1) ? -sc : sc);
+        float2 v = cscale(buf[t * ROW_PITCH + c], (t & 1) ? -sc : sc);
         if (!FWD && weight) v = cmulc(v, __ldg(weight + t));
         out[(size_t)l * M + t] = v;
       }
     }
   } else {
     // the per-line weight is a scalar: applied with the output scale (both directions)
-    for (int idx = threadIdx.x; idx < FFT_W * M; idx += FFT_NT) {
+    for (int idx = threadIdx.x; idx < ROW_W * M; idx += FFT_NT) {
       const int c = idx / M, t = idx - c * M;
       const int l = l0 + c;
       if (l < D) {
         const float s_l = sc * __ldg(line_weight + l);
-        float2 v = cscale(buf[t * FFT_PITCH + c], (t & 1) ? -s_l : s_l);
+        float2 v = cscale(buf[t * ROW_PITCH + c], (t & 1) ? -s_l : s_l);
         if (!FWD && weight) v = cmulc(v, __ldg(weight + t));
         out[(size_t)l * M + t] = v;
       }
@@ -322,6 +326,7 @@ cudaError_t launch_abs_bound(const void* vol, int cplx, const float* s, int N, f
 // host launchers
 // ----------------------------------------------------------------------------
 static size_t fft_smem(int L) { return (size_t)L * FFT_PITCH * sizeof(float2); }
+static size_t row_smem(int L) { return (size_t)L * ROW_PITCH * sizeof(float2); }
 
 template <typename F>
 static cudaError_t set_smem(F* f, size_t bytes) {
@@ -345,10 +350,10 @@ template <int K>
 static cudaError_t launch_row_fwd_t(const void* vol, int cplx, float2* out, const float* s, int N,
                                     const float2* tw, cudaStream_t st) {
   auto f = k_row_fwd<K>;
-  cudaError_t e = set_smem(f, fft_smem(K));
+  cudaError_t e = set_smem(f, row_smem(K));
   if (e != cudaSuccess) return e;
-  const int grid = (N * N + FFT_W - 1) / FFT_W;
-  f<<<grid, FFT_NT, fft_smem(K), st>>>(vol, cplx, out, s, N, tw);
+  const int grid = (N * N + ROW_W - 1) / ROW_W;
+  f<<<grid, FFT_NT, row_smem(K), st>>>(vol, cplx, out, s, N, tw);
   return cudaGetLastError();
 }
 
@@ -366,10 +371,10 @@ template <int K>
 static cudaError_t launch_row_adj_t(const float2* in, void* vol, int cplx, const float* s, int N,
                                     const float2* tw, cudaStream_t st) {
   auto f = k_row_adj<K>;
-  cudaError_t e = set_smem(f, fft_smem(K));
+  cudaError_t e = set_smem(f, row_smem(K));
   if (e != cudaSuccess) return e;
-  const int grid = (N * N + FFT_W - 1) / FFT_W;
-  f<<<grid, FFT_NT, fft_smem(K), st>>>(in, vol, cplx, s, N, tw);
+  const int grid = (N * N + ROW_W - 1) / ROW_W;
+  f<<<grid, FFT_NT, row_smem(K), st>>>(in, vol, cplx, s, N, tw);
   return cudaGetLastError();
 }
 
@@ -444,10 +449,10 @@ template <int M, bool FWD>
 static cudaError_t launch_line_t(const float2* in, float2* out, int D, const float2* w, const float* lw,
                                  const float2* tw, cudaStream_t st) {
   auto f = k_line<M, FWD>;
-  cudaError_t e = set_smem(f, fft_smem(M));
+  cudaError_t e = set_smem(f, row_smem(M));
   if (e != cudaSuccess) return e;
-  const int grid = (D + FFT_W - 1) / FFT_W;
-  f<<<grid, FFT_NT, fft_smem(M), st>>>(in, out, D, w, lw, tw);
+  const int grid = (D + ROW_W - 1) / ROW_W;
+  f<<<grid, FFT_NT, row_smem(M), st>>>(in, out, D, w, lw, tw);
   return cudaGetLastError();
 }
 
