@@ -169,9 +169,11 @@ struct NoPostLoad {
   __device__ __forceinline__ void operator()(int, int) const {}
 };
 
-// post_load(i, c) runs for every input row once all of the thread's first-stage
-// loads have been issued (a consumer that clears its input does it there, so
-// that no load waits behind a store to a possibly aliasing address).
+// post_load(i, c) runs once for every input row i and column c after the
+// first barrier, when every first-stage load of the CTA has completed (it is
+// called from the last stage, whose rows j + r NS cover each row once; a
+// consumer that clears its input does it there, so that no load waits behind a
+// store to a possibly aliasing address and no load address stays live).
 template <int L, int W, int NT, bool INV, class Load, class Store, class PostLoad = NoPostLoad>
 __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __restrict__ tw, Load&& load,
                                         Store&& store, PostLoad&& post_load = PostLoad{}) {
@@ -191,15 +193,6 @@ __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __
         const int c = b % W, j = b / W;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[p][r] = load(j + r * (L / R), c);
-      }
-    }
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int b = threadIdx.x + p * NT;
-      if (NBF % NT == 0 || b < NBF) {
-        const int c = b % W, j = b / W;
-#pragma unroll
-        for (int r = 0; r < R; ++r) post_load(j + r * (L / R), c);
       }
     }
 #pragma unroll
@@ -237,6 +230,8 @@ __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __
         small_dft<R, INV>(v);
 #pragma unroll
         for (int r = 0; r < R; ++r) store(j + r * NS, c, v[r]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) post_load(j + r * NS, c);
       }
     }
   }
