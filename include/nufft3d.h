@@ -186,7 +186,15 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
  * while the current one is computed (J = 6, T = 8; needs the tensor map the
  * plan encodes for its grid); spread only: 3 variant 2 with ten warps per SM and
  * the table read through L1 (the default spread), 4 one thread per point in
- * rounds of pairwise distinct tile-offset residues (no atomics).  T is 4, 8 or 16; changing it re-sorts the points.
+ * rounds of pairwise distinct tile-offset residues (no atomics), 5 variant 3
+ * with the tile accumulated in 32-bit fixed point by shared-memory integer
+ * adds, in units of a power-of-two scale per subproblem set by the largest
+ * |v| max|cx| max|cy| max|cz| of its points (J = 6, T = 8, at most 512 points
+ * per subproblem; samples whose bound exceeds 2^100, or is not finite, make
+ * the tile NaN), 6 the arithmetic of 5 with one tile shared by the four
+ * warps of a CTA, four CTAs per SM, and one scale per subproblem from the
+ * largest bound of all its points (J = 6, T = 8, at most 256 points per
+ * subproblem).  T is 4, 8 or 16; changing it re-sorts the points.
  * Synchronises the plan's last stream and works on cuda_stream.  Returns
  * NUFFT3D_ERR_UNSUPPORTED for a combination the plan cannot run.  Used by
  * the autotuner. */

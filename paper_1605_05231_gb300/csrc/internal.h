@@ -94,6 +94,8 @@ cudaError_t launch_gather_tma(const InterpGeom& g, int grid_dtype, const void* g
 bool v4_supported(int T, int J, int S, int L);
 bool v3s_supported(int T, int J);
 bool v4s_supported(int T, int J, int S);
+bool v5s_supported(int T, int J, int S);
+bool v6s_supported(int T, int J, int S);
 
 }  // namespace nufft
 

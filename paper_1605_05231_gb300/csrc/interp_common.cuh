@@ -197,6 +197,19 @@ static __device__ const unsigned short kLaneOvf13[24] = {1, 65, 129, 193, 257, 3
 static __device__ const unsigned char kLaneMain21[32] = {0, 8, 16, 32, 9, 17, 2, 10, 18, 26, 3, 11, 19, 12, 20, 21, 24, 40, 1, 25, 34, 42, 27, 35, 43, 28, 36, 44, 5, 13, 29, 45};
 static __device__ const unsigned short kLaneOvf21[24] = {33, 97, 161, 225, 289, 41, 105, 169, 4, 68, 132, 196, 260, 324, 101, 165, 353, 233, 297, 361, 37, 229, 293, 357};
 
+// Lane tables of the fixed-point spread (variant 5, E = 13): 4-byte cells, so
+// an instruction is one wavefront when its 32 lanes hit 32 distinct banks.  The
+// column offsets jx + 13 jy of the 36 (jx, jy) pairs reach 31 residues mod 32:
+// lanes 0..30 take 31 columns with distinct residues for every jz (lane 31
+// none, 255); lanes 0..29 take the remaining 30 taps, lanes 0..14 and 15..29
+// each with distinct residues of jx + 13 jy + 169 jz (lanes 30, 31 none).
+static __device__ const unsigned char kLaneMainI13[32] = {0, 1, 2, 3, 4, 5, 45, 24, 25, 26, 27, 28, 29, 8, 9, 10, 11, 12, 13, 32, 33, 34, 35, 36, 37, 16, 17, 18, 19, 20, 21, 255};
+static __device__ const unsigned short kLaneOvfI13[32] = {236, 40, 41, 42, 43, 296, 297, 298, 299, 300, 104, 105, 106, 107, 360, 44, 108, 361, 362, 363, 364, 168, 169, 170, 171, 172, 232, 233, 234, 235, 65535, 65535};
+// Lanes without a tap of their own (main: lane 31; extra: lanes 30, 31) add
+// zero to a cell at an offset whose residue is free in their instruction, so
+// the instruction runs without a predicate and keeps its wavefront count.
+static __device__ const unsigned char kPadI13[3] = {19, 24, 25};  // main lane 31, extra lanes 30 and 31
+
 constexpr int V2_WARPS = 8;
 constexpr int V2_CSTRIDE = 18;  // float2 per point: cx[6] cy[6] cz[6]
 

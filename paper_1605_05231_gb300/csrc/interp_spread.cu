@@ -421,6 +421,394 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
 }
 
 // ---------------------------------------------------------------------------
+// spread variant 5 (J = 6, T = 8): variant 3 with the warp's tile accumulated
+// in 32-bit fixed point.  A shared-memory integer add is a native reduction of
+// one wavefront per 32 lanes, where a floating-point cell update is a 64-bit
+// load plus a 64-bit store; the tile is kept as separate real and imaginary
+// int32 planes.
+//
+// Scale: while a subproblem is spread, its tile carries an exponent e with
+// 2^e >= |v| max|cx| max|cy| max|cz| for every point added so far, and counts
+// contributions in units of 2^e / B, B = 2^min(22, 30 - ceil(log2 S)) (1 - 2^-10).
+// Every contribution is then below 2^22 units, and no cell of a subproblem of
+// at most S points (one contribution per point and cell) reaches 2^30.  When a
+// batch of 32 points raises e, the tile is rescaled by a rounding right shift.
+// Rounding: adding 1.5 * 2^23 puts x in [2^23, 2^24), where floats are spaced
+// by 1, so the FMA that adds the constant rounds x to the nearest integer,
+// which is read back from the float's bits.
+// ---------------------------------------------------------------------------
+constexpr int V5S_WARPS = 10;
+constexpr float kRoundMagic = 12582912.0f;            // 1.5 * 2^23
+constexpr int kRoundMagicBits = 0x4B400000;           // its bits
+constexpr int kTileEmpty = -1000;                     // tile exponent before the first point
+constexpr unsigned kBoundLimitBits = (100u + 127u) << 23;  // 2^100: larger bounds (and NaN) poison the tile
+
+// two int32 planes take the bytes of one float2 tile
+__host__ __device__ inline size_t v5s_bytes(int T) { return V5S_WARPS * v3s_warp_bytes(T); }
+
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }  // -126 <= k <= 127
+
+// a b + c d rounded to an integer, for |a b|, |c d|, |a b + c d| < 2^22
+__device__ __forceinline__ int round_units(float a, float b, float c, float d) {
+  return __float_as_int(fmaf(a, b, fmaf(c, d, kRoundMagic))) - kRoundMagicBits;
+}
+
+struct V5Lanes {
+  int main_off, ovf_off;
+  int mjx, mjy, ojx, ojy, ojz;
+  bool has_main, has_ovf;
+};
+
+__device__ __forceinline__ V5Lanes v5_lanes(int lane) {
+  constexpr int E = 13;
+  const unsigned m = kLaneMainI13[lane], o = kLaneOvfI13[lane];
+  V5Lanes r;
+  r.has_main = m != 255u;
+  r.has_ovf = o != 65535u;
+  r.mjx = r.has_main ? (m & 7) : 0;
+  r.mjy = r.has_main ? ((m >> 3) & 7) : 0;
+  r.ojx = r.has_ovf ? (o & 7) : 0;
+  r.ojy = r.has_ovf ? ((o >> 3) & 7) : 0;
+  r.ojz = r.has_ovf ? ((o >> 6) & 7) : 0;
+  r.main_off = r.mjx + E * r.mjy;
+  r.ovf_off = r.ojx + E * r.ojy + E * E * r.ojz;
+  return r;
+}
+
+// divide every cell by 2^d, rounding half up
+__device__ __forceinline__ void v5s_rescale(int* tre, int* tim, int n, int d, int lane) {
+  __syncwarp();
+  if (d >= 31) {
+    for (int i = lane; i < n; i += 32) {
+      tre[i] = 0;
+      tim[i] = 0;
+    }
+  } else {
+    const int h = 1 << (d - 1);
+    for (int i = lane; i < n; i += 32) {
+      const int a = tre[i], b = tim[i];
+      if (a) tre[i] = (a + h) >> d;
+      if (b) tim[i] = (b + h) >> d;
+    }
+  }
+  __syncwarp();
+}
+
+template <int T>
+__global__ void __launch_bounds__(V5S_WARPS * 32, 1) k_spread_v5(InterpGeom g, const float2* __restrict__ in,
+                                                                 const int4* __restrict__ subs, int n_subs,
+                                                                 int* __restrict__ counter,
+                                                                 float2* __restrict__ grid, float budget,
+                                                                 float inv_budget) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int E = T + 5, E2 = E * E, E3 = E2 * E;
+  static_assert(E == 13, "lane tables are for E = 13");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nT = g.nT, K = g.K;
+  const size_t KK = (size_t)K * K;
+  float2* coef = (float2*)(smem_raw + warp * v3s_warp_bytes(T));
+  int* mos = (int*)(coef + 32 * V2_CSTRIDE);
+  int* tre = mos + 32;
+  int* tim = tre + E3;
+  for (int i = lane; i < E3; i += 32) {
+    tre[i] = 0;
+    tim[i] = 0;
+  }
+  __syncwarp();
+  const V5Lanes ln = v5_lanes(lane);
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(counter, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= n_subs) break;
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    int e_tile = kTileEmpty;
+    float scale = 0.f;
+    bool poison = false;
+    for (int b0 = 0; b0 < sp.z; b0 += 32) {
+      // phase 1: one point per lane; the bound |v| max|cx| max|cy| max|cz|
+      int off = -1;
+      float bound = 0.f;
+      const int pi = b0 + lane;
+      if (pi < sp.z) {
+        const uint2 ent = g.sorted[sp.y + pi];
+        int w0[3];
+        float f[3];
+        decode_point<6>(g, ent.x, w0, f);
+        const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+        if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+          off = (lz * E + ly) * E + lx;
+          float2 val = in[ent.x];
+          if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+          float4* c4 = (float4*)(coef + lane * V2_CSTRIDE);
+          float m2 = 1.f;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            float2 c[6];
+            point_coeffs<6>(g, f[a], c);
+            float mx = 0.f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) mx = fmaxf(mx, fmaf(c[q].x, c[q].x, c[q].y * c[q].y));
+            m2 *= mx;
+            if (a == 2) {
+#pragma unroll
+              for (int q = 0; q < 6; ++q) c[q] = cmulc(val, c[q]);  // v conj(cz)
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) c4[a * 3 + q] = make_float4(c[2 * q].x, c[2 * q].y, c[2 * q + 1].x, c[2 * q + 1].y);
+          }
+          bound = hypotf(val.x, val.y) * sqrtf(m2);
+        } else {
+          atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+        }
+      }
+      mos[lane] = off;
+      // bounds are >= 0 (or NaN), so their bits order like the values
+      const unsigned bb = __reduce_max_sync(0xffffffffu, __float_as_uint(bound));
+      __syncwarp();
+      if (bb > kBoundLimitBits) {
+        poison = true;
+      } else if (bb != 0u) {
+        const int e = max((int)(bb >> 23) - 127 + ((bb & 0x7FFFFFu) ? 1 : 0), -100);
+        if (e > e_tile) {
+          if (e_tile != kTileEmpty) v5s_rescale(tre, tim, E3, e - e_tile, lane);
+          e_tile = e;
+          scale = budget * pow2f(-e);
+        }
+      }
+      if (!poison && bb != 0u) {
+        // phase 2: one point at a time for the whole warp
+        const int np = min(32, sp.z - b0);
+#pragma unroll 2
+        for (int p = 0; p < np; ++p) {
+          const int mo = mos[p];
+          if (mo < 0) continue;
+          const float2* cp = coef + p * V2_CSTRIDE;
+          const float2 cx = cp[ln.mjx], cy = cp[6 + ln.mjy];
+          const float4 z01 = *(const float4*)(cp + 12), z23 = *(const float4*)(cp + 14),
+                       z45 = *(const float4*)(cp + 16);
+          const float2 ox = cp[ln.ojx], oy = cp[6 + ln.ojy];
+          const float2 zv[6] = {make_float2(z01.x, z01.y), make_float2(z01.z, z01.w),
+                                make_float2(z23.x, z23.y), make_float2(z23.z, z23.w),
+                                make_float2(z45.x, z45.y), make_float2(z45.z, z45.w)};
+          // contribution conj(cx cy) (v conj(cz)), in units
+          if (ln.has_main) {
+            const float2 pm = cmul(cscale(cx, scale), cy);
+            int* re = tre + mo + ln.main_off;
+            int* im = tim + mo + ln.main_off;
+#pragma unroll
+            for (int jz = 0; jz < 6; ++jz) {
+              atomicAdd(re + jz * E2, round_units(pm.x, zv[jz].x, pm.y, zv[jz].y));
+              atomicAdd(im + jz * E2, round_units(pm.x, zv[jz].y, -pm.y, zv[jz].x));
+            }
+          }
+          if (ln.has_ovf) {
+            float2 z = zv[0];
+#pragma unroll
+            for (int jz = 1; jz < 6; ++jz) z = ln.ojz == jz ? zv[jz] : z;
+            const float2 q = cmul(cscale(ox, scale), oy);
+            atomicAdd(tre + mo + ln.ovf_off, round_units(q.x, z.x, q.y, z.y));
+            atomicAdd(tim + mo + ln.ovf_off, round_units(q.x, z.y, -q.y, z.x));
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // add the tile to the grid: lanes walk (y, x) columns, each column along z
+    const float inv = e_tile == kTileEmpty ? 0.f : inv_budget * pow2f(e_tile);
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int c = lane; c < E2; c += 32) {
+      const int iy = c / E, ix = c - iy * E;
+      int gx = x0 + ix, gy = y0 + iy;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      int gz = z0;
+#pragma unroll
+      for (int iz = 0; iz < E; ++iz) {
+        const int idx = c + iz * E2;
+        const int a = tre[idx], b = tim[idx];
+        if ((a | b) != 0 || poison) {
+          tre[idx] = 0;
+          tim[idx] = 0;
+          const float2 v = poison ? make_float2(qnan, qnan) : make_float2((float)a * inv, (float)b * inv);
+          atomicAdd(&grid[((size_t)(gz >= K ? gz - K : gz)) * KK + (size_t)gy * K + gx], v);
+        }
+        ++gz;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spread variant 6 (J = 6, T = 8, at most 256 points per subproblem): the
+// fixed-point arithmetic of variant 5 with one tile per CTA.  Integer adds make
+// the tile safe to share, so four warps spread one subproblem together and an
+// SM holds four CTAs (16 warps) where the warp-private tiles allowed ten.
+//  phase 1: thread per point (decode, coefficients, v folded into the z row,
+//           the bound |v| max|cx| max|cy| max|cz|), then the CTA's largest
+//           bound fixes the subproblem's exponent: no rescaling;
+//  phase 2: warp w spreads points w, w + 4, ...; lanes without a tap of their
+//           own add zero at a free bank, so no instruction is predicated;
+//  flush:   all 128 threads add the tile to the grid and clear it, while the
+//           next subproblem's phase 1 starts in the warps that are done.
+// ---------------------------------------------------------------------------
+constexpr int V6S_WARPS = 4, V6S_THREADS = V6S_WARPS * 32, V6S_MAX_PTS = 256;
+
+struct V6SLayout {
+  static constexpr int E = 13, E3 = E * E * E;
+  static constexpr size_t coef = 0;                                                  // [256][18] float2
+  static constexpr size_t mos = coef + (size_t)V6S_MAX_PTS * V2_CSTRIDE * sizeof(float2);  // [256] int
+  static constexpr size_t tre = mos + V6S_MAX_PTS * sizeof(int);                      // [E3] int
+  static constexpr size_t tim = tre + E3 * sizeof(int);                               // [E3] int
+  static constexpr size_t wmax = tim + E3 * sizeof(int);                              // [4] unsigned
+  static constexpr size_t nxt = wmax + V6S_WARPS * sizeof(unsigned);                  // [2] int
+  static constexpr size_t bytes = (nxt + 2 * sizeof(int) + 15) / 16 * 16;
+};
+
+__global__ void __launch_bounds__(V6S_THREADS, 4) k_spread_v6(InterpGeom g, const float2* __restrict__ in,
+                                                             const int4* __restrict__ subs, int n_subs,
+                                                             int* __restrict__ counter,
+                                                             float2* __restrict__ grid, float budget,
+                                                             float inv_budget) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using Lay = V6SLayout;
+  constexpr int T = 8, E = Lay::E, E2 = E * E, E3 = Lay::E3;
+  float2* coef = (float2*)(smem_raw + Lay::coef);
+  int* mos = (int*)(smem_raw + Lay::mos);
+  int* tre = (int*)(smem_raw + Lay::tre);
+  int* tim = (int*)(smem_raw + Lay::tim);
+  unsigned* wmax = (unsigned*)(smem_raw + Lay::wmax);
+  int* nxt = (int*)(smem_raw + Lay::nxt);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nT = g.nT, K = g.K;
+  const size_t KK = (size_t)K * K;
+  for (int i = tid; i < E3; i += V6S_THREADS) {
+    tre[i] = 0;
+    tim[i] = 0;
+  }
+  // lane taps: a (jx, jy) column for every jz, and one extra tap
+  const V5Lanes ln = v5_lanes(lane);
+  const int main_off = ln.has_main ? ln.main_off : kPadI13[0];
+  const int ovf_off = ln.has_ovf ? ln.ovf_off : kPadI13[lane == 30 ? 1 : 2];
+  const int ozo = 12 + ln.ojz;
+  if (tid == 0) nxt[0] = atomicAdd(counter, 1);
+  __syncthreads();
+  int s = nxt[0], parity = 0;
+  while (s < n_subs) {
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    // phase 1; bounds are >= 0 (or NaN), so their bits order like the values
+    // (and a NaN wins, as it must)
+    unsigned bound = 0u;
+    for (int i = tid; i < sp.z; i += V6S_THREADS) {
+      const uint2 ent = g.sorted[sp.y + i];
+      int w0[3];
+      float f[3];
+      decode_point<6>(g, ent.x, w0, f);
+      const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+      float4* c4 = (float4*)(coef + i * V2_CSTRIDE);
+      int off = 0;
+      if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+        off = (lz * E + ly) * E + lx;
+        float2 val = in[ent.x];
+        if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+        float m2 = 1.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          float2 c[6];
+          point_coeffs<6>(g, f[a], c);
+          float mx = 0.f;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) mx = fmaxf(mx, fmaf(c[q].x, c[q].x, c[q].y * c[q].y));
+          m2 *= mx;
+          if (a == 2) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) c[q] = cmulc(val, c[q]);  // v conj(cz)
+          }
+#pragma unroll
+          for (int q = 0; q < 3; ++q) c4[a * 3 + q] = make_float4(c[2 * q].x, c[2 * q].y, c[2 * q + 1].x, c[2 * q + 1].y);
+        }
+        bound = max(bound, __float_as_uint(hypotf(val.x, val.y) * sqrtf(m2)));
+      } else {
+        // outside its tile (flagged): the point adds zero
+        atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) c4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      mos[i] = off;
+    }
+    const unsigned wb = __reduce_max_sync(0xffffffffu, bound);
+    if (lane == 0) wmax[warp] = wb;
+    if (tid == 0) nxt[parity ^ 1] = atomicAdd(counter, 1);
+    __syncthreads();
+    unsigned bb = wmax[0];
+#pragma unroll
+    for (int w = 1; w < V6S_WARPS; ++w) bb = max(bb, wmax[w]);
+    const bool poison = bb > kBoundLimitBits;
+    int e_tile = kTileEmpty;
+    if (!poison && bb != 0u) {
+      e_tile = max((int)(bb >> 23) - 127 + ((bb & 0x7FFFFFu) ? 1 : 0), -100);
+      const float sc = budget * pow2f(-e_tile);
+      const float sm = ln.has_main ? sc : 0.f, so = ln.has_ovf ? sc : 0.f;
+      // phase 2: contribution conj(cx cy) (v conj(cz)), in units
+      for (int p = warp; p < sp.z; p += V6S_WARPS) {
+        const int mo = mos[p];
+        const float2* cp = coef + p * V2_CSTRIDE;
+        const float2 cx = cp[ln.mjx], cy = cp[6 + ln.mjy];
+        const float4 z01 = *(const float4*)(cp + 12), z23 = *(const float4*)(cp + 14),
+                     z45 = *(const float4*)(cp + 16);
+        const float2 ox = cp[ln.ojx], oy = cp[6 + ln.ojy], zo = cp[ozo];
+        const float2 zv[6] = {make_float2(z01.x, z01.y), make_float2(z01.z, z01.w),
+                              make_float2(z23.x, z23.y), make_float2(z23.z, z23.w),
+                              make_float2(z45.x, z45.y), make_float2(z45.z, z45.w)};
+        const float2 pm = cmul(cscale(cx, sm), cy);
+        int* re = tre + mo + main_off;
+        int* im = tim + mo + main_off;
+#pragma unroll
+        for (int jz = 0; jz < 6; ++jz) {
+          atomicAdd(re + jz * E2, round_units(pm.x, zv[jz].x, pm.y, zv[jz].y));
+          atomicAdd(im + jz * E2, round_units(pm.x, zv[jz].y, -pm.y, zv[jz].x));
+        }
+        const float2 q = cmul(cscale(ox, so), oy);
+        atomicAdd(tre + mo + ovf_off, round_units(q.x, zo.x, q.y, zo.y));
+        atomicAdd(tim + mo + ovf_off, round_units(q.x, zo.y, -q.y, zo.x));
+      }
+    }
+    __syncthreads();
+    const int s_next = nxt[parity ^ 1];
+    // flush: threads walk (y, x) columns, each column along z
+    const float inv = e_tile == kTileEmpty ? 0.f : inv_budget * pow2f(e_tile);
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int c = tid; c < E2; c += V6S_THREADS) {
+      const int iy = c / E, ix = c - iy * E;
+      int gx = x0 + ix, gy = y0 + iy;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      float2* col = grid + (size_t)gy * K + gx;
+      int gz = z0;
+#pragma unroll
+      for (int iz = 0; iz < E; ++iz) {
+        const int idx = c + iz * E2;
+        const int a = tre[idx], b = tim[idx];
+        if ((a | b) != 0 || poison) {
+          tre[idx] = 0;
+          tim[idx] = 0;
+          const float2 v = poison ? make_float2(qnan, qnan) : make_float2((float)a * inv, (float)b * inv);
+          atomicAdd(col + (size_t)(gz >= K ? gz - K : gz) * KK, v);
+        }
+        ++gz;
+      }
+    }
+    parity ^= 1;
+    s = s_next;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // spread variant 4 (J = 6): one thread per point without atomics.  Each warp
 // owns a private E^3 tile.  The points of a subproblem are bucketed by the
 // residue of their first-tap offset modulo 32; in round r lane l spreads the
@@ -566,6 +954,14 @@ bool v4s_supported(int T, int J, int S) {
   return J == 6 && T == 8 && v4s_bytes(T, S) <= (size_t)max_optin_smem();
 }
 
+bool v5s_supported(int T, int J, int S) {
+  return J == 6 && T == 8 && S >= 1 && S <= 512 && v5s_bytes(T) <= (size_t)max_optin_smem();
+}
+
+bool v6s_supported(int T, int J, int S) {
+  return J == 6 && T == 8 && S >= 1 && S <= V6S_MAX_PTS && V6SLayout::bytes <= (size_t)max_optin_smem();
+}
+
 bool v3s_supported(int T, int J) {
   return J == 6 && T == 8 && v3s_bytes(T) <= (size_t)max_optin_smem();
 }
@@ -614,6 +1010,37 @@ cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, co
     e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     f<<<num_sms(), V4S_WARPS * 32, smem, st>>>(g, in, subs, n_subs, g.S, g.counter + 1, grid);
+    return cudaGetLastError();
+  }
+  if (variant == 6 && v6s_supported(g.T, g.J, g.S)) {
+    auto f = k_spread_v6;
+    const size_t smem = V6SLayout::bytes;
+    cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (n_subs == 0) return cudaSuccess;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, V6S_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    const float budget = ldexpf(1.f - 1.f / 1024.f, 22);  // at most 256 points per subproblem
+    e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    f<<<num_sms() * per_sm, V6S_THREADS, smem, st>>>(g, in, subs, n_subs, g.counter + 1, grid, budget, 1.f / budget);
+    return cudaGetLastError();
+  }
+  if (variant == 5 && v5s_supported(g.T, g.J, g.S)) {
+    auto f = k_spread_v5<8>;
+    const size_t smem = v5s_bytes(g.T);
+    cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (n_subs == 0) return cudaSuccess;
+    int lg = 0;
+    while ((1 << lg) < g.S) ++lg;
+    const int bits = lg > 8 ? 30 - lg : 22;
+    const float budget = ldexpf(1.f - 1.f / 1024.f, bits);
+    e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    f<<<num_sms(), V5S_WARPS * 32, smem, st>>>(g, in, subs, n_subs, g.counter + 1, grid, budget, 1.f / budget);
     return cudaGetLastError();
   }
   if (variant == 3 && v3s_supported(g.T, g.J)) {

@@ -510,12 +510,15 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->h_twin.swap(twin);
   pl->P_eval = (long long)pl->h_unique.size();
   pl->n_pairs = n_pairs;
-  pl->spread_variant = nufft::v3s_supported(r.T, r.J) ? 3 : (nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0);
-  // defaults measured at 256^3: with the table, 256-thread gather CTAs and 512
-  // points per subproblem; with exact coefficients (no table traffic), the
-  // 128-thread CTAs and 256 points per subproblem
+  // defaults measured at 256^3: with the table, 256-thread gather CTAs, 512
+  // points per subproblem and the warp-private FP32 spread; with exact
+  // coefficients (no table traffic), 128-thread gather CTAs, 256 points per
+  // subproblem and the CTA-shared fixed-point spread
   const int S0 = r.L == 0 && r.T == 8 ? 256 : 512;
   pl->gather_variant = nufft::v3_supported(r.T, r.J, S0) ? (r.L == 0 && r.T == 8 ? 5 : 3) : 0;
+  pl->spread_variant = r.L == 0 && nufft::v6s_supported(r.T, r.J, S0) ? 6
+                       : nufft::v3s_supported(r.T, r.J)             ? 3
+                       : (nufft::v2_supported(r.T, r.J, r.L) ? 2 : 0);
   CK(cudaGetDevice(&pl->device));
   CK(upload(&pl->d_s, h.s, st));
   CK(upload(&pl->d_table, h.table, st));
@@ -809,7 +812,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 8 || spread_variant < -1 || spread_variant > 4) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 8 || spread_variant < -1 || spread_variant > 6) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -828,6 +831,8 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   if (gv == 4 && !nufft::v4_supported(T, plan->J, S_new, plan->L)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 3 && !nufft::v3s_supported(T, plan->J)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 4 && !nufft::v4s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
+  if (sv == 5 && !nufft::v5s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
+  if (sv == 6 && !nufft::v6s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   int rc = ensure_device(plan);
   if (rc != NUFFT3D_OK) return rc;
   CK(cudaStreamSynchronize(plan->last_stream));

@@ -48,6 +48,7 @@ def test_tiny_workload_exact_coefficients(cuda_lib):
     info = plan.info()
     assert info["exact_coeffs"] == 1
     assert 0.0 < info["coeff_fit_error"] < 1e-7, info["coeff_fit_error"]
+    assert info["spread_variant"] == 6 and info["points_per_subproblem"] == 256  # the exact-mode defaults
     p, a = _fwd_adj(plan, x, y)
     op = _oplan(w.n, dirs, w.m, w.k, w.j)
     ef = O.rel_l2(p, O.nufft_forward(x.astype(np.float64), op))
@@ -85,7 +86,8 @@ def test_shapes_and_taps(cuda_lib, n, k, m, ndir, j):
 @pytest.mark.parametrize("gv,sv,pps,tile", [(0, 0, 1024, 8), (3, 3, 512, 8), (3, 3, 37, 8), (5, 4, 512, 8),
                                             (3, 4, 300, 8), (0, 3, 77, 8), (3, 0, 1024, 16), (5, 3, 2048, 8),
                                             (6, 3, 512, 8), (7, 3, 256, 8), (7, 4, 100, 8), (8, 3, 256, 8),
-                                            (8, 3, 5, 8)])
+                                            (8, 3, 5, 8), (5, 5, 256, 8), (8, 5, 100, 8),
+                                            (5, 6, 256, 8), (8, 6, 100, 8), (3, 6, 7, 8)])
 def test_variants_without_table(cuda_lib, gv, sv, pps, tile):
     n = 32
     dirs = I.umbrella_directions(35, 20)

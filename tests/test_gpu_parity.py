@@ -179,7 +179,9 @@ def test_mid_workload_sampled_lines(cuda_lib):
 @pytest.mark.parametrize("gv,sv,pps,tile", [(0, 0, 1024, 8), (0, 0, 700, 16), (1, 1, 1024, 16), (1, 1, 300, 8),
                                             (2, 2, 1024, 8), (2, 2, 64, 8), (2, 2, 5000, 8), (3, 2, 1024, 8),
                                             (3, 0, 2048, 16), (3, 2, 37, 8), (4, 2, 512, 8), (4, 2, 400, 8), (3, 3, 1024, 8), (4, 3, 512, 8), (0, 3, 77, 8), (3, 4, 512, 8), (3, 4, 33, 8), (3, 4, 560, 8), (5, 3, 512, 8), (5, 0, 300, 8), (6, 3, 512, 8), (7, 3, 256, 8), (7, 0, 37, 8), (6, 2, 2048, 8), (8, 3, 256, 8), (8, 0, 37, 8),
-                                            (8, 2, 1024, 8),
+                                            (8, 2, 1024, 8), (3, 5, 256, 8), (4, 5, 512, 8), (0, 5, 37, 8),
+                                            (5, 5, 1, 8), (3, 5, 300, 8), (3, 6, 256, 8), (5, 6, 37, 8),
+                                            (0, 6, 1, 8), (4, 6, 200, 8), (8, 6, 256, 8),
                                             (4, 0, 300, 8)])
 def test_kernel_variants_and_subproblem_split(cuda_lib, gv, sv, pps, tile):
     """Every gather/spread variant, tile edge and subproblem size gives the same operator."""
@@ -211,7 +213,65 @@ def test_unsupported_tuning_is_refused(cuda_lib):
     assert ei.value.status == -4
     with pytest.raises(cuda_lib.NufftError):
         plan.tune(9, 0, 0, 0)
+    # the fixed-point spread bounds its cells for at most 512 points per subproblem
+    with pytest.raises(cuda_lib.NufftError) as ei:
+        plan.tune(-1, 5, 1024, 8)
+    assert ei.value.status == -4
+    with pytest.raises(cuda_lib.NufftError) as ei:
+        plan.tune(-1, 6, 300, 8)
+    assert ei.value.status == -4
+    with pytest.raises(cuda_lib.NufftError):
+        plan.tune(-1, 7, 0, 0)
     assert plan.info()["gather_variant"] == 3 and plan.info()["tile"] == 8
+    plan.tune(-1, 5, 512, 8)
+    with pytest.raises(cuda_lib.NufftError) as ei:
+        plan.tune(-1, -1, 513, 8)
+    assert ei.value.status == -4
+    assert plan.info()["spread_variant"] == 5 and plan.info()["points_per_subproblem"] == 512
+
+
+@pytest.mark.parametrize("sv", [3, 5, 6])
+@pytest.mark.parametrize("scale", [1e-25, 1.0, 1e15])
+def test_spread_dynamic_range_and_growing_batches(cuda_lib, sv, scale):
+    """Line magnitudes that grow by 2^(1/16) per line, 40 binary orders over
+    the 640 lines, make later batches of a subproblem larger than the first
+    (the fixed-point spread rescales its tile as they arrive); three overall
+    scales."""
+    import torch
+
+    n = 32
+    dirs = I.umbrella_directions(40, 16)
+    y = I.random_lines(dirs.shape[0], 2 * n, 17) * (2.0 ** (np.arange(dirs.shape[0]) / 16.0))[:, None] * scale
+    y = y.astype(np.complex64)
+    plan = cuda_lib.Plan(n, dirs)
+    plan.tune(-1, sv, 256, 8)
+    a = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    ref = O.nufft_adjoint(y.astype(np.complex128), _oplan(n, dirs))
+    err = O.rel_l2(a, ref)
+    print(f"spread {sv}, scale {scale:g}: adjoint rel-L2 {err:.2e}")
+    assert err < TOL
+
+
+@pytest.mark.parametrize("sv", [3, 5, 6])
+def test_nan_sample_gives_nan_adjoint(cuda_lib, sv):
+    """A NaN sample reaches every output of the adjoint (the line transform
+    and the 3D FFT mix it into everything) in both spread arithmetics."""
+    import torch
+
+    n = 16
+    dirs = I.umbrella_directions(16, 8)
+    y = I.random_lines(dirs.shape[0], 2 * n, 19).astype(np.complex64)
+    y[5, 3] = np.nan
+    plan = cuda_lib.Plan(n, dirs)
+    plan.tune(-1, sv, 256, 8)
+    a = plan.adjoint(torch.from_numpy(y).cuda())
+    assert plan.sync_status() == 0
+    assert bool(torch.isnan(a).all())
+    # the plan stays usable: a finite input afterwards gives the oracle's result
+    y[5, 3] = 0
+    a = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert O.rel_l2(a, O.nufft_adjoint(y.astype(np.complex128), _oplan(n, dirs))) < TOL
 
 
 def test_variant1_dense_center_and_repeat_calls(cuda_lib):
