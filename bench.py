@@ -127,11 +127,13 @@ def parse_clocks(lines):
 # ----------------------------------------------------------------------------
 # roofline bookkeeping: algorithmic work per stage
 # ----------------------------------------------------------------------------
-def stage_work(n, k, j, m, d, p_eval=None):
+def stage_work(n, k, j, m, d, p_eval=None, spread_tap_bytes=16):
     """Algorithmic bytes and flops per launch of each stage: every stage moves
     its input and output arrays once; the interpolation does 8 (J^3 + J^2 + J)
     flops per evaluated point (coincident samples are evaluated once) and reads
-    the touched part of the grid (the ball |k| <= K/2 + J/2)."""
+    the touched part of the grid (the ball |k| <= K/2 + J/2).  Shared-memory
+    bytes per tap: 8 for the gather's read, 16 for the FP32 spread's
+    read-modify-write, 8 for the fixed-point spread's two 4-byte reductions."""
     P = d * m
     Pe = P if p_eval is None else p_eval
     c8 = 8
@@ -150,7 +152,7 @@ def stage_work(n, k, j, m, d, p_eval=None):
             "line_dft": {"bytes": 2 * c8 * P},
             "grid_clear": {"bytes": c8 * k ** 3},
             "spread": {"bytes": 2 * ball * c8 * k ** 3 + c8 * P + 8 * Pe, "flops": interp_flops,
-                       "smem_bytes": j ** 3 * 16 * Pe},
+                       "smem_bytes": j ** 3 * spread_tap_bytes * Pe},
             "z_pass": {"bytes": c8 * k ** 3 + c8 * n * k * k},
             "y_pass": {"bytes": c8 * n * k * k + c8 * n * n * k},
             "x_pass": {"bytes": c8 * n * n * k + 4 * n ** 3},
@@ -472,7 +474,8 @@ def run_ours(args):
     # ---- roofline of the dominant kernel ---------------------------------
     peaks = load_peaks()
     info = plan.info()
-    work = stage_work(w.n, w.k, w.j, w.m, plan.n_dirs, info["evaluated_points"])
+    fixed_point = info["spread_variant"] in (5, 6)
+    work = stage_work(w.n, w.k, w.j, w.m, plan.n_dirs, info["evaluated_points"], 8 if fixed_point else 16)
     per_call = {}
     for side in ("forward", "adjoint"):
         calls = max(1, stages[f"{side}_calls"])
@@ -497,7 +500,8 @@ def run_ours(args):
         smem_peak = SMS * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
         roof["smem_frac"] = wk["smem_bytes"] / t_dom / 1e12 / smem_peak
         roof["smem_basis"] = (f"shared-memory data path: {SMS} SMs x 128 B/clk x {peaks['sm_max_mhz']:.0f} MHz = "
-                              f"{smem_peak:.1f} TB/s; per evaluated point J^3 x 8 B (gather) or x 16 B (spread)")
+                              f"{smem_peak:.1f} TB/s; per evaluated point J^3 x 8 B (gather, fixed-point spread) "
+                              f"or x 16 B (FP32 spread)")
     roof["algorithmic_bytes"] = wk["bytes"]
     roof["hbm_frac"] = wk["bytes"] / t_dom / 1e9 / peaks["hbm_gbs"]
     roof["traffic"] = ncu_traffic(f"{dom[0]}.{dom[1]}")

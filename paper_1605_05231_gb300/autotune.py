@@ -16,6 +16,10 @@ from .binding import NufftError
 
 # (gather variant, spread variant, points per subproblem, tile edge)
 CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
+    (5, 6, 256, 8),
+    (8, 6, 256, 8),
+    (3, 6, 256, 8),
+    (3, 5, 512, 8),
     (5, 3, 256, 8),
     (5, 3, 512, 8),
     (3, 3, 256, 8),
