@@ -191,7 +191,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
  * adds, in units of a power-of-two scale per subproblem set by the largest
  * |v| max|cx| max|cy| max|cz| of its points (J = 6, T = 8, at most 512 points
  * per subproblem; samples whose bound exceeds 2^100, or is not finite, make
- * the tile NaN), 6 the arithmetic of 5 with one tile shared by the four
+ * the tile NaN), 6 the arithmetic of 5 with one tile shared by the six
  * warps of a CTA, four CTAs per SM, and one scale per subproblem from the
  * largest bound of all its points (J = 6, T = 8, at most 256 points per
  * subproblem).  T is 4, 8 or 16; changing it re-sorts the points.

@@ -80,6 +80,63 @@ __global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_row_fwd(const void* __
 }
 
 // ----------------------------------------------------------------------------
+// forward x pass of a real volume: two real rows per complex transform.  Rows
+// a = row0 + 2c and b = a + 1 go in as Z = a + i b; with Z~[k] = conj(Z[-k]),
+// the transforms are A = (Z + Z~) / 2 and B = (Z - Z~) / (2i), so one
+// transform of 8 columns serves 16 rows.
+// ----------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_row_fwd_real(const float* __restrict__ vol,
+                                                         float2* __restrict__ out, const float* __restrict__ s,
+                                                         int N, const float2* __restrict__ tw) {
+  extern __shared__ float2 buf[];
+  const int nrows = N * N;
+  const int row0 = blockIdx.x * (2 * ROW_W);
+  const int half = N / 2;
+  for (int base = threadIdx.x; base < ROW_W * N; base += ROW_CHUNK * FFT_NT) {
+    float2 t[ROW_CHUNK];
+#pragma unroll
+    for (int u = 0; u < ROW_CHUNK; ++u) {
+      const int idx = base + u * FFT_NT;
+      t[u] = make_float2(0.f, 0.f);
+      if (idx < ROW_W * N) {
+        const int c = idx / N, x = idx - c * N;
+        const int ra = row0 + 2 * c;
+        if (ra < nrows) t[u].x = vol[(size_t)ra * N + x];
+        if (ra + 1 < nrows) t[u].y = vol[(size_t)(ra + 1) * N + x];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < ROW_CHUNK; ++u) {
+      const int idx = base + u * FFT_NT;
+      if (idx < ROW_W * N) {
+        const int c = idx / N, x = idx - c * N;
+        const int ra = row0 + 2 * c, rb = ra + 1;
+        const int za = ra / N, ya = ra - za * N, zb = rb / N, yb = rb - zb * N;
+        const float sx = __ldg(s + x);
+        const float sa = ra < nrows ? sx * __ldg(s + ya) * __ldg(s + za) : 0.f;
+        const float sb = rb < nrows ? sx * __ldg(s + yb) * __ldg(s + zb) : 0.f;
+        buf[centred_to_grid(x, half, K) * ROW_PITCH + c] = make_float2(t[u].x * sa, t[u].y * sb);
+      }
+    }
+  }
+  for (int idx = threadIdx.x; idx < ROW_W * (K - N); idx += FFT_NT) {
+    const int c = idx % ROW_W, i = idx / ROW_W + (N - half);
+    buf[i * ROW_PITCH + c] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  smem_fft<K, ROW_W, FFT_NT, false>(buf, ROW_PITCH, tw);
+  for (int idx = threadIdx.x; idx < ROW_W * K; idx += FFT_NT) {
+    const int c = idx / K, k = idx - c * K;
+    const int ra = row0 + 2 * c;
+    const float2 z = buf[k * ROW_PITCH + c];
+    const float2 zm = buf[(k == 0 ? 0 : K - k) * ROW_PITCH + c];
+    if (ra < nrows) out[(size_t)ra * K + k] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+    if (ra + 1 < nrows) out[(size_t)(ra + 1) * K + k] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+  }
+}
+
+// ----------------------------------------------------------------------------
 // column pass: for each outer index o and chunk of W contiguous columns
 // (32 W threads; W = 16: 128-byte row segments, two CTAs per SM),
 // transform along a strided axis.
@@ -346,6 +403,14 @@ bool fft_length_supported(int L) {
 template <int K>
 static cudaError_t launch_row_fwd_t(const void* vol, int cplx, float2* out, const float* s, int N,
                                     const float2* tw, cudaStream_t st) {
+  if (!cplx) {
+    auto f = k_row_fwd_real<K>;
+    cudaError_t e = set_smem(f, row_smem(K));
+    if (e != cudaSuccess) return e;
+    const int grid = (N * N + 2 * ROW_W - 1) / (2 * ROW_W);
+    f<<<grid, FFT_NT, row_smem(K), st>>>((const float*)vol, out, s, N, tw);
+    return cudaGetLastError();
+  }
   auto f = k_row_fwd<K>;
   cudaError_t e = set_smem(f, row_smem(K));
   if (e != cudaSuccess) return e;

@@ -645,17 +645,17 @@ __global__ void __launch_bounds__(V5S_WARPS * 32, 1) k_spread_v5(InterpGeom g, c
 // ---------------------------------------------------------------------------
 // spread variant 6 (J = 6, T = 8, at most 256 points per subproblem): the
 // fixed-point arithmetic of variant 5 with one tile per CTA.  Integer adds make
-// the tile safe to share, so four warps spread one subproblem together and an
-// SM holds four CTAs (16 warps) where the warp-private tiles allowed ten.
+// the tile safe to share, so six warps spread one subproblem together and an
+// SM holds four CTAs (24 warps) where the warp-private tiles allowed ten.
 //  phase 1: thread per point (decode, coefficients, v folded into the z row,
 //           the bound |v| max|cx| max|cy| max|cz|), then the CTA's largest
 //           bound fixes the subproblem's exponent: no rescaling;
-//  phase 2: warp w spreads points w, w + 4, ...; lanes without a tap of their
+//  phase 2: warp w spreads points w, w + 6, ...; lanes without a tap of their
 //           own add zero at a free bank, so no instruction is predicated;
-//  flush:   all 128 threads add the tile to the grid and clear it, while the
+//  flush:   all 192 threads add the tile to the grid and clear it, while the
 //           next subproblem's phase 1 starts in the warps that are done.
 // ---------------------------------------------------------------------------
-constexpr int V6S_WARPS = 4, V6S_THREADS = V6S_WARPS * 32, V6S_MAX_PTS = 256;
+constexpr int V6S_WARPS = 6, V6S_THREADS = V6S_WARPS * 32, V6S_MAX_PTS = 256;
 
 struct V6SLayout {
   static constexpr int E = 13, E3 = E * E * E;
@@ -663,12 +663,12 @@ struct V6SLayout {
   static constexpr size_t mos = coef + (size_t)V6S_MAX_PTS * V2_CSTRIDE * sizeof(float2);  // [256] int
   static constexpr size_t tre = mos + V6S_MAX_PTS * sizeof(int);                      // [E3] int
   static constexpr size_t tim = tre + E3 * sizeof(int);                               // [E3] int
-  static constexpr size_t wmax = tim + E3 * sizeof(int);                              // [4] unsigned
+  static constexpr size_t wmax = tim + E3 * sizeof(int);                              // [6] unsigned
   static constexpr size_t nxt = wmax + V6S_WARPS * sizeof(unsigned);                  // [2] int
   static constexpr size_t bytes = (nxt + 2 * sizeof(int) + 15) / 16 * 16;
 };
 
-__global__ void __launch_bounds__(V6S_THREADS, 4) k_spread_v6(InterpGeom g, const float2* __restrict__ in,
+__global__ void __launch_bounds__(V6S_THREADS, 3) k_spread_v6(InterpGeom g, const float2* __restrict__ in,
                                                              const int4* __restrict__ subs, int n_subs,
                                                              int* __restrict__ counter,
                                                              float2* __restrict__ grid, float budget,
