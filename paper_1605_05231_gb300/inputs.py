@@ -244,3 +244,25 @@ def batched_workloads(seed: int = 4) -> List[Workload]:
                                 10, 0.0, seed + idx))
             idx += 1
     return out
+
+
+def shifted_polar_targets(shape, shift, device=None):
+    """Targets (u_s, u_theta, u_phi), in grid-index units, of every cell of a
+    polar grid of shape (n_phi, n_theta, n_s) moved by shift = (ds, dtheta, dphi)
+    cells: a resampling onto a shifted polar grid.  Rows in grid order (phi
+    slowest, s fastest).  float32; a torch tensor on `device` if one is given
+    (the 47 M targets of the 256^3 grid are made on the GPU), else NumPy."""
+    n_phi, n_theta, n_s = (int(v) for v in shape)
+    if device is not None:
+        import torch
+
+        p = torch.arange(n_phi, device=device, dtype=torch.float32) + float(shift[2])
+        t = torch.arange(n_theta, device=device, dtype=torch.float32) + float(shift[1])
+        s = torch.arange(n_s, device=device, dtype=torch.float32) + float(shift[0])
+        P, Tt, Ss = torch.meshgrid(p, t, s, indexing="ij")
+        return torch.stack([Ss.reshape(-1), Tt.reshape(-1), P.reshape(-1)], dim=1).contiguous()
+    p = np.arange(n_phi, dtype=np.float32) + np.float32(shift[2])
+    t = np.arange(n_theta, dtype=np.float32) + np.float32(shift[1])
+    s = np.arange(n_s, dtype=np.float32) + np.float32(shift[0])
+    P, Tt, Ss = np.meshgrid(p, t, s, indexing="ij")
+    return np.stack([Ss.ravel(), Tt.ravel(), P.ravel()], axis=1)
