@@ -139,6 +139,33 @@ int nufft3d_plan_sync_status(nufft3d_plan plan, int* device_status);
 /* Free a plan and everything it owns (NULL is accepted). */
 int nufft3d_plan_destroy(nufft3d_plan plan);
 
+/* Direct resampling of the polar Radon grid (Sec. 2.1, Eq. 2.15 with the
+ * second sparse operator the identity).  The radially sampled Radon data are
+ * uniform in (s, theta, phi) (Fig. 2.10); a separable truncated-sinc
+ * interpolator with J taps per axis (the paper's runs: J = 3, Sec. 3.2) takes
+ * them to arbitrary points:
+ *   out[i] = sum_k sinc(u_s - k_s) sinc(u_theta - k_theta) sinc(u_phi - k_phi)
+ *            grid[k_phi mod n_phi][k_theta][k_s],
+ * sinc(t) = sin(pi t) / (pi t), k0 .. k0 + J - 1 on each axis with
+ * k0 = floor(u - J/2) + 1.  The azimuth is periodic; taps beyond the ends of
+ * the theta and s ranges add nothing.
+ *   grid_dev    device, complex64 [n_phi][n_theta][n_s] (interleaved re, im):
+ *               the forward projector's [D][M] lines with D = n_phi n_theta in
+ *               azimuth-major order fit it as is; not modified
+ *   targets_dev device, float32 [n_targets][3] = (u_s, u_theta, u_phi) in
+ *               grid-index units; a coordinate that is not finite or is 2^24
+ *               or more in magnitude gives a NaN output
+ *   J           taps per axis, 2 ... 8
+ *   out_dev     device, complex64 [n_targets]; must not overlap the inputs
+ *   cuda_stream the stream to run on (NULL: the legacy default stream)
+ * All buffers are the caller's; nothing is allocated.  Asynchronous: the
+ * result is ready when the stream reaches it.  Returns NUFFT3D_OK (also for
+ * n_targets = 0, with any pointers), NUFFT3D_ERR_ARG (negative count, sizes
+ * below 1 or a grid above 2^40 cells, J outside 2 ... 8, a NULL pointer with
+ * n_targets > 0) or NUFFT3D_ERR_CUDA (the launch failed). */
+int nufft3d_polar_resample(const void* grid_dev, int n_phi, int n_theta, int n_s, const float* targets_dev,
+                           long long n_targets, int J, void* out_dev, void* cuda_stream);
+
 /* Weights that turn the adjoint into the direct (Fourier-slice) reconstruction
  * that inverts the image-to-Radon step (Sec. 2.3: ramp filtering in the
  * Fourier domain, then the NUFFT transpose; Sec. 1: the 3D parallel-beam

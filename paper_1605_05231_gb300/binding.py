@@ -36,6 +36,7 @@ EXPORTS = (
     "nufft3d_batch_invalidate",
     "nufft3d_batch_destroy",
     "nufft3d_fourier_slice_weights",
+    "nufft3d_polar_resample",
 )
 
 FWD_STAGES = ("x_pass", "y_pass", "z_pass", "gather", "line_dft")
@@ -108,6 +109,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.nufft3d_plan_set_timing.argtypes = [vp, i]
     lib.nufft3d_plan_stage_times.argtypes = [vp, fp, fp, ip]
     lib.nufft3d_fourier_slice_weights.argtypes = [i, i, ctypes.c_double, i, fp, fp]
+    lib.nufft3d_polar_resample.argtypes = [vp, i, i, i, vp, ctypes.c_longlong, i, vp, vp]
     for name in EXPORTS:
         if name != "nufft3d_error_string":
             getattr(lib, name).restype = ctypes.c_int
@@ -177,6 +179,30 @@ def fourier_slice_weights(n_az: int, n_pol: int, cone_half_angle: float, m: int)
         rw.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), lw.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
         "nufft3d_fourier_slice_weights")
     return (rw[0::2] + 1j * rw[1::2]).astype(np.complex64), lw
+
+
+def polar_resample(grid, targets, J: int = 3, out=None, stream=None):
+    """Direct resampling of the polar Radon grid (Eq. 2.15; nufft3d_polar_resample).
+    grid: complex64 CUDA tensor (n_phi, n_theta, n_s), e.g. a plan's (D, M)
+    lines viewed as (n_az, n_pol, M); targets: float32 CUDA tensor (P, 3) of
+    (u_s, u_theta, u_phi) in grid-index units.  Returns complex64 (P,)."""
+    import torch
+
+    if grid.dtype != torch.complex64 or grid.dim() != 3 or not grid.is_cuda or not grid.is_contiguous():
+        raise ValueError("grid must be a contiguous complex64 CUDA tensor (n_phi, n_theta, n_s)")
+    if targets.dtype != torch.float32 or targets.dim() != 2 or targets.shape[1] != 3 or not targets.is_cuda \
+            or not targets.is_contiguous() or targets.device != grid.device:
+        raise ValueError("targets must be a contiguous float32 (P, 3) tensor on the grid's device")
+    n = targets.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.complex64, device=grid.device)
+    elif out.dtype != torch.complex64 or out.shape != (n,) or not out.is_contiguous() or out.device != grid.device:
+        raise ValueError("out must be a contiguous complex64 (P,) tensor on the grid's device")
+    n_phi, n_theta, n_s = grid.shape
+    _check(load_library().nufft3d_polar_resample(
+        ctypes.c_void_p(grid.data_ptr()), int(n_phi), int(n_theta), int(n_s), ctypes.c_void_p(targets.data_ptr()),
+        int(n), int(J), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, grid.device)), "nufft3d_polar_resample")
+    return out
 
 
 def workspace_bytes(**kw) -> int:

@@ -1,0 +1,139 @@
+// Direct resampling of the polar Radon grid (Sec. 2.1, Eq. 2.15 with T2 = I):
+// the radially sampled Radon data are uniform in (s, theta, phi) (Fig. 2.10),
+// and a separable truncated-sinc interpolator takes them to arbitrary points:
+//
+//   x~(u) = sum_{k} sinc(u_s - k_s) sinc(u_theta - k_theta) sinc(u_phi - k_phi)
+//                  x[k_phi mod n_phi, k_theta, k_s],
+//
+// with the J integers k0 .. k0 + J - 1, k0 = floor(u - J/2) + 1, on every axis;
+// the azimuth is periodic, taps beyond the ends of the theta and s ranges add
+// nothing.  The paper's runs use J = 3 ([3 3 3], Sec. 3.2).
+//
+// One thread per target.  The J sinc weights of an axis share one sine:
+// sin(pi (u - k)) = (-1)^k sin(pi u), so an axis costs one sinpi and J
+// divisions.
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nufft {
+
+constexpr int POLAR_NT = 256;
+
+
+// weights and grid indices of one axis: periodic axes wrap the index; on the
+// others a tap beyond [0, n) gets weight 0 and a safe index
+template <int J>
+__device__ __forceinline__ void sinc_axis(float u, int n, bool periodic, float (&w)[J], int (&k)[J]) {
+  const int k0 = (int)floorf(u - 0.5f * (float)J) + 1;
+  const float su = sinpif(u);
+  constexpr float kInvPi = 0.318309886183790671537767526745f;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int kj = k0 + j;
+    const float t = u - (float)kj;
+    float wj = t == 0.f ? 1.f : __fdividef(((kj & 1) ? -su : su) * kInvPi, t);
+    int idx = kj;
+    if (periodic) {
+      idx = kj % n;
+      idx += idx < 0 ? n : 0;
+    } else {
+      const bool inside = (unsigned)kj < (unsigned)n;
+      wj = inside ? wj : 0.f;
+      idx = inside ? kj : 0;
+    }
+    w[j] = wj;
+    k[j] = idx;
+  }
+}
+
+template <int J>
+__global__ void __launch_bounds__(POLAR_NT) k_polar_resample(const float2* __restrict__ grid, int n_phi, int n_theta,
+                                                            int n_s, const float* __restrict__ targets,
+                                                            long long n, float2* __restrict__ out) {
+  const long long stride = (long long)gridDim.x * POLAR_NT;
+  for (long long i = (long long)blockIdx.x * POLAR_NT + threadIdx.x; i < n; i += stride) {
+    const float us = targets[3 * i], ut = targets[3 * i + 1], up = targets[3 * i + 2];
+    // coordinates must be finite and below 2^24 in magnitude (exact integers in float)
+    const float lim = 16777216.f;
+    if (!(fabsf(us) < lim && fabsf(ut) < lim && fabsf(up) < lim)) {
+      out[i] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+      continue;
+    }
+    float ws[J], wt[J], wp[J];
+    int ks[J], kt[J], kp[J];
+    sinc_axis<J>(us, n_s, false, ws, ks);
+    sinc_axis<J>(ut, n_theta, false, wt, kt);
+    sinc_axis<J>(up, n_phi, true, wp, kp);
+    // the J^3 loads are independent and all in flight at once; targets that
+    // follow the grid share rows through L1 / L2
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < J; ++a) {
+      const float2* plane = grid + (size_t)kp[a] * n_theta * n_s;
+      float2 pacc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < J; ++b) {
+        const float2* row = plane + (size_t)kt[b] * n_s;
+        float2 racc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < J; ++c) {
+          const float2 v = __ldg(row + ks[c]);
+          racc.x = fmaf(ws[c], v.x, racc.x);
+          racc.y = fmaf(ws[c], v.y, racc.y);
+        }
+        pacc.x = fmaf(wt[b], racc.x, pacc.x);
+        pacc.y = fmaf(wt[b], racc.y, pacc.y);
+      }
+      acc.x = fmaf(wp[a], pacc.x, acc.x);
+      acc.y = fmaf(wp[a], pacc.y, acc.y);
+    }
+    out[i] = acc;
+  }
+}
+
+static int polar_grid_cap() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  return sms * 16;  // eight resident CTAs of 256 threads per SM, two waves
+}
+
+template <int J>
+static cudaError_t launch_polar_t(const float2* grid, int n_phi, int n_theta, int n_s, const float* targets,
+                                  long long n, float2* out, cudaStream_t st) {
+  const long long blocks = (n + POLAR_NT - 1) / POLAR_NT;
+  const int cap = polar_grid_cap();
+  k_polar_resample<J><<<(int)(blocks < cap ? blocks : cap), POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets,
+                                                                             n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_polar_resample(const float2* grid, int n_phi, int n_theta, int n_s, const float* targets,
+                                  long long n, int J, float2* out, cudaStream_t st) {
+  switch (J) {
+    case 2: return launch_polar_t<2>(grid, n_phi, n_theta, n_s, targets, n, out, st);
+    case 3: return launch_polar_t<3>(grid, n_phi, n_theta, n_s, targets, n, out, st);
+    case 4: return launch_polar_t<4>(grid, n_phi, n_theta, n_s, targets, n, out, st);
+    case 5: return launch_polar_t<5>(grid, n_phi, n_theta, n_s, targets, n, out, st);
+    case 6: return launch_polar_t<6>(grid, n_phi, n_theta, n_s, targets, n, out, st);
+    case 7: return launch_polar_t<7>(grid, n_phi, n_theta, n_s, targets, n, out, st);
+    case 8: return launch_polar_t<8>(grid, n_phi, n_theta, n_s, targets, n, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nufft
+
+extern "C" int nufft3d_polar_resample(const void* grid_dev, int n_phi, int n_theta, int n_s,
+                                      const float* targets_dev, long long n_targets, int J, void* out_dev,
+                                      void* cuda_stream) {
+  if (n_targets < 0 || n_phi < 1 || n_theta < 1 || n_s < 1 || J < 2 || J > 8) return NUFFT3D_ERR_ARG;
+  if ((long long)n_phi * n_theta * n_s > (1LL << 40)) return NUFFT3D_ERR_ARG;
+  if (n_targets == 0) return NUFFT3D_OK;
+  if (!grid_dev || !targets_dev || !out_dev) return NUFFT3D_ERR_ARG;
+  const cudaError_t e = nufft::launch_polar_resample((const float2*)grid_dev, n_phi, n_theta, n_s, targets_dev,
+                                                     n_targets, J, (float2*)out_dev, (cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? NUFFT3D_OK : NUFFT3D_ERR_CUDA;
+}

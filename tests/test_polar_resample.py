@@ -100,3 +100,83 @@ def test_planted_off_by_one_tap_start_is_caught(monkeypatch):
     monkeypatch.setattr(R, "tap_start", lambda u, J: np.floor(np.asarray(u) - J / 2.0).astype(np.int64))
     got = R.polar_sinc_resample(x, t, 4)
     assert np.max(np.abs(got - want)) > 0.1
+
+
+def test_library_rejects_bad_arguments():
+    from paper_1605_05231_gb300 import binding
+
+    lib = binding.load_library()
+    import ctypes
+
+    f = lib.nufft3d_polar_resample
+    nul = ctypes.c_void_p(0)
+    # null pointers with a nonzero count, bad J and bad grid sizes fail before any device work
+    assert f(nul, 4, 4, 4, nul, 10, 3, nul, nul) == -1
+    assert f(nul, 4, 4, 4, nul, 0, 3, nul, nul) == 0
+    assert f(ctypes.c_void_p(16), 4, 4, 4, ctypes.c_void_p(16), 1, 1, ctypes.c_void_p(16), nul) == -1
+    assert f(ctypes.c_void_p(16), 4, 4, 4, ctypes.c_void_p(16), 1, 9, ctypes.c_void_p(16), nul) == -1
+    assert f(ctypes.c_void_p(16), 0, 4, 4, ctypes.c_void_p(16), 1, 3, ctypes.c_void_p(16), nul) == -1
+
+
+# ---------------------------------------------------------------------------
+# GPU parity
+# ---------------------------------------------------------------------------
+def _gpu(cuda_lib, x, t, J):
+    import torch
+
+    xd = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    td = torch.from_numpy(np.ascontiguousarray(t.astype(np.float32))).cuda()
+    out = cuda_lib.polar_resample(xd, td, J)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("J", [2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("n", [1, 37, 1000, 4099])
+def test_gpu_matches_oracle(cuda_lib, J, n):
+    shape = (12, 9, 40)
+    x = _grid(shape, 10 + J)
+    t = _targets(n, shape, 20 + n).astype(np.float32)
+    got = _gpu(cuda_lib, x, t, J)
+    want = R.polar_sinc_resample(x.astype(np.complex64), t.astype(np.float64), J)
+    assert O.rel_l2(got, want) < TOL
+
+
+@pytest.mark.gpu
+def test_gpu_edges_wrap_and_integers(cuda_lib):
+    shape = (16, 8, 32)
+    x = _grid(shape, 30)
+    t = np.array([[0.0, 0.0, 0.0], [31.0, 7.0, 15.0], [-0.4, 3.2, -0.5], [31.6, 7.9, 15.7], [10.5, 3.5, 47.25],
+                  [5.0, 2.0, -17.0], [-3.0, -3.0, 2.0], [40.0, 12.0, 3.0], [15.5, 4.0, 1e4 + 0.25]], dtype=np.float32)
+    for J in (3, 6):
+        got = _gpu(cuda_lib, x, t, J)
+        want = R.polar_sinc_resample(x.astype(np.complex64), t.astype(np.float64), J)
+        assert np.max(np.abs(got - want)) < 1e-5 * np.max(np.abs(x))
+    # nothing to do
+    import torch
+
+    out = cuda_lib.polar_resample(torch.from_numpy(x.astype(np.complex64)).cuda(),
+                                  torch.zeros((0, 3), dtype=torch.float32, device="cuda"), 3)
+    assert out.shape == (0,)
+
+
+@pytest.mark.gpu
+def test_gpu_full_size_polar_grid_sampled(cuda_lib):
+    """The 360 x 256 x 512 polar grid of the 256^3 workload's plane integrals,
+    resampled at 47,185,920 targets shifted off the grid by (0.37, 0.21, 0.43)
+    cells, in the launch configuration bench.py times; 4096 sampled targets
+    against the oracle."""
+    import torch
+
+    w = I.workload("full256")
+    shape = (w.n_az, w.n_pol, w.m)
+    x = _grid(shape, 40).astype(np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    td = I.shifted_polar_targets(shape, (0.37, 0.21, 0.43), device="cuda")
+    out = cuda_lib.polar_resample(xd, td, 3)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(41).choice(td.shape[0], 4096, replace=False))
+    t = td[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    want = R.polar_sinc_resample(x, t, 3)
+    assert O.rel_l2(out[torch.from_numpy(idx).cuda()].cpu().numpy(), want) < TOL
