@@ -280,6 +280,75 @@ __global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_row_adj(const float2* 
 }
 
 // ----------------------------------------------------------------------------
+// inverse x pass to a real volume: two rows per complex transform.  Only the
+// real part of each row's transform is kept, and Re IFFT(a) = IFFT(H a) with
+// the Hermitian part (H a)[k] = (a[k] + conj a[-k]) / 2.  So rows a and b go in
+// as Z = H a + i H b and come out as Re IFFT(a) + i Re IFFT(b).  A thread
+// builds Z[j] and Z[-j] = conj(H a[j]) + i conj(H b[j]) from the four loads
+// a[j], a[-j], b[j], b[-j]; 16 rows share one transform of 8 columns.
+// ----------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_row_adj_real(const float2* __restrict__ in,
+                                                         float* __restrict__ vol, const float* __restrict__ s,
+                                                         int N, const float2* __restrict__ tw) {
+  extern __shared__ float2 buf[];
+  const int nrows = N * N;
+  const int row0 = blockIdx.x * (2 * ROW_W);
+  const int half = N / 2;
+  constexpr int KH = K / 2 + 1;  // j = 0 .. K/2 pairs with K - j
+  constexpr int U = ROW_CHUNK / 4;
+  for (int base = threadIdx.x; base < ROW_W * KH; base += U * FFT_NT) {
+    float2 a[U], am[U], b[U], bm[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * FFT_NT;
+      a[u] = am[u] = b[u] = bm[u] = make_float2(0.f, 0.f);
+      if (idx < ROW_W * KH) {
+        const int c = idx / KH, j = idx - c * KH;
+        const int jm = j == 0 ? 0 : K - j;
+        const int ra = row0 + 2 * c;
+        if (ra < nrows) {
+          a[u] = in[(size_t)ra * K + j];
+          am[u] = in[(size_t)ra * K + jm];
+        }
+        if (ra + 1 < nrows) {
+          b[u] = in[(size_t)(ra + 1) * K + j];
+          bm[u] = in[(size_t)(ra + 1) * K + jm];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * FFT_NT;
+      if (idx < ROW_W * KH) {
+        const int c = idx / KH, j = idx - c * KH;
+        const int jm = j == 0 ? 0 : K - j;
+        const float2 ha = make_float2(0.5f * (a[u].x + am[u].x), 0.5f * (a[u].y - am[u].y));
+        const float2 hb = make_float2(0.5f * (b[u].x + bm[u].x), 0.5f * (b[u].y - bm[u].y));
+        buf[j * ROW_PITCH + c] = make_float2(ha.x - hb.y, ha.y + hb.x);
+        buf[jm * ROW_PITCH + c] = make_float2(ha.x + hb.y, hb.x - ha.y);
+      }
+    }
+  }
+  __syncthreads();
+  smem_fft<K, ROW_W, FFT_NT, true>(buf, ROW_PITCH, tw);
+  for (int idx = threadIdx.x; idx < ROW_W * N; idx += FFT_NT) {
+    const int c = idx / N, x = idx - c * N;
+    const int ra = row0 + 2 * c, rb = ra + 1;
+    const float2 v = buf[centred_to_grid(x, half, K) * ROW_PITCH + c];
+    const float sx = __ldg(s + x);
+    if (ra < nrows) {
+      const int z = ra / N, y = ra - z * N;
+      vol[(size_t)ra * N + x] = v.x * (sx * __ldg(s + y) * __ldg(s + z));
+    }
+    if (rb < nrows) {
+      const int z = rb / N, y = rb - z * N;
+      vol[(size_t)rb * N + x] = v.y * (sx * __ldg(s + y) * __ldg(s + z));
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // per-line centred DFTs.  FWD (projection): a[m] = lw[l] w[m] (-1)^m X[m];
 // p[t] = (-1)^{M/2} (-1)^t / M * sum_m a[m] e^{+2 pi i m t / M}.
 // ADJ: a[t] = (-1)^t y[t]; Y[m] = (-1)^{M/2} (-1)^m lw[l] conj(w[m]) / M * sum_t a[t] e^{-2 pi i m t / M}.
@@ -432,6 +501,14 @@ cudaError_t launch_row_fwd(int K, const void* vol, int cplx, float2* out, const 
 template <int K>
 static cudaError_t launch_row_adj_t(const float2* in, void* vol, int cplx, const float* s, int N,
                                     const float2* tw, cudaStream_t st) {
+  if (!cplx) {
+    auto f = k_row_adj_real<K>;
+    cudaError_t e = set_smem(f, row_smem(K));
+    if (e != cudaSuccess) return e;
+    const int grid = (N * N + 2 * ROW_W - 1) / (2 * ROW_W);
+    f<<<grid, FFT_NT, row_smem(K), st>>>(in, (float*)vol, s, N, tw);
+    return cudaGetLastError();
+  }
   auto f = k_row_adj<K>;
   cudaError_t e = set_smem(f, row_smem(K));
   if (e != cudaSuccess) return e;
