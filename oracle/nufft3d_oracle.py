@@ -26,7 +26,7 @@ Exact reference (O-exact): X(omega) = sum_n x[n] e^{-i omega.n} (the 3D analogue
 of Eq. 2.3) evaluated directly, then L_w.  With w = 1 this is the periodic-sinc
 (Dirichlet) plane sum of Eqs. 2.6-2.7: p[s] = sum_n x[n] D_M(d.n - s).
 
-Readings of points the paper leaves open (listed in the design doc too):
+Readings of points the paper leaves open:
   * scaling s(n) = Psi(0) / Psi(n/K), Psi the Fourier transform of the
     Kaiser-Bessel window of width J and shape alpha = 2.34 J (the paper names a
     Kaiser-Bessel / raised-cosine pre-window, Sec. 2.1.3, without formula);

@@ -16,11 +16,11 @@ that need no reordering; so x~ = T1 x with
                                 sinc(u_phi - k_phi) x[k_phi, k_theta, k_s],
     sinc(t) = sin(pi t) / (pi t),  sinc(0) = 1,
 
-each axis keeping the J integers nearest the target ("preserving the main
-lobe and a few side lobes", the text after Eq. 2.13); the paper's runs use
-J = 3 ([3 3 3], Sec. 3.2).
+each axis keeping the J integers nearest the target: the truncation after
+Eq. 2.13 keeps the sinc's central lobe and its closest side lobes.  The
+paper's runs use J = 3 ([3 3 3], Sec. 3.2).
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * taps k0 .. k0 + J - 1 with k0 = floor(u - J/2) + 1 on every axis;
   * the azimuth is periodic: k_phi is taken modulo n_phi;
   * the polar angle and the line offset are not: taps outside [0, n_theta) or
