@@ -164,10 +164,14 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_col(const float2* __restrict
   const int cy2 = pr.mode == 2 ? cen((int)o) * cen((int)o) : 0;
   int mcx2 = 0;  // smallest kx^2 over the CTA's columns
   if (pr.mode != 0) {
+    // columns k_lo .. k_hi: centred kx = k below K/2 (smallest square at k_lo >= 0)
+    // and k - K from K/2 on (smallest at k_hi)
+    const int k_lo = ch * W, k_hi = ch * W + W - 1;
     mcx2 = 0x7fffffff;
-    for (int c = 0; c < W; ++c) {
-      const int cx = cen(ch * W + c);
-      mcx2 = cx * cx < mcx2 ? cx * cx : mcx2;
+    if (k_lo < hk) mcx2 = k_lo * k_lo;
+    if (k_hi >= hk) {
+      const int e = k_hi - pr.K;
+      mcx2 = e * e < mcx2 ? e * e : mcx2;
     }
     // a z pass whose columns all lie outside the disk kx^2 + ky^2 <= r2 has nothing to do
     if (pr.mode == 2 && (long long)mcx2 + cy2 > pr.r2) return;
