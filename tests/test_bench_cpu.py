@@ -32,6 +32,16 @@ def test_stage_work_model():
     assert f["z_pass"]["bytes"] == 8 * 256 * 512 * 512 + 8 * 512 ** 3
     assert f["gather"]["flops"] == 8 * (216 + 36 + 6) * 23639040
     assert w["adjoint"]["spread"]["smem_bytes"] == 2 * f["gather"]["smem_bytes"]
+    # the fixed-point spread moves two 4-byte reductions per tap, as many bytes as the gather's reads
+    wf = bench.stage_work(256, 512, 6, 512, 92160, 23639040, spread_tap_bytes=8)
+    assert wf["adjoint"]["spread"]["smem_bytes"] == f["gather"]["smem_bytes"] == 216 * 8 * 23639040
+
+
+def test_resample_source_hash_is_separate():
+    # the traffic entries of the interpolation kernels and of the polar resampler
+    # are keyed by the hashes of their own sources
+    assert bench.source_hash() != bench.source_hash(bench.RESAMPLE_SOURCES)
+    assert len(bench.source_hash(bench.RESAMPLE_SOURCES)) == 16
 
 
 def _free_port():
