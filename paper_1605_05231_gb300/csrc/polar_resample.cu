@@ -29,6 +29,13 @@ __device__ __forceinline__ void sinc_axis(float u, int n, bool periodic, float (
   const int k0 = (int)floorf(u - 0.5f * (float)J) + 1;
   const float su = sinpif(u);
   constexpr float kInvPi = 0.318309886183790671537767526745f;
+  // periodic axis: one modulo for the first tap, then wrap by subtraction
+  // (one subtraction suffices when the period is at least J)
+  int p0 = 0;
+  if (periodic) {
+    p0 = k0 % n;
+    p0 += p0 < 0 ? n : 0;
+  }
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int kj = k0 + j;
@@ -36,8 +43,12 @@ __device__ __forceinline__ void sinc_axis(float u, int n, bool periodic, float (
     float wj = t == 0.f ? 1.f : __fdividef(((kj & 1) ? -su : su) * kInvPi, t);
     int idx = kj;
     if (periodic) {
-      idx = kj % n;
-      idx += idx < 0 ? n : 0;
+      idx = p0 + j;
+      if (n >= J) {
+        idx -= idx >= n ? n : 0;
+      } else {
+        idx %= n;
+      }
     } else {
       const bool inside = (unsigned)kj < (unsigned)n;
       wj = inside ? wj : 0.f;
