@@ -200,8 +200,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
  * subproblem and the grid tile edge T of a plan (-1 / 0 keep the current
  * choice).  Variants: 0 one thread per point, one CTA per subproblem (any
  * J); 1 one warp per point, CTA-shared tile (J = 6); 2 one warp per point,
- * warp-private tile, no shared atomics (J = 6, T = 8; the default spread
- * when available); gather only: 3 one thread per point, points reordered so
+ * warp-private tile, no shared atomics (J = 6, T = 8); gather only: 3 one thread per point, points reordered so
  * that every half-warp's tile accesses fall in distinct banks (any J; the
  * default gather with a table), 4 the same with the table in shared memory, 5
  * the same as 3 with 128-thread CTAs (T = 8; the default with exact_coeffs,
@@ -212,7 +211,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
  * copy the next subproblem's tile into shared memory with a TMA tensor copy
  * while the current one is computed (J = 6, T = 8; needs the tensor map the
  * plan encodes for its grid); spread only: 3 variant 2 with ten warps per SM and
- * the table read through L1 (the default spread), 4 one thread per point in
+ * the table read through L1 (the default spread with a table), 4 one thread per point in
  * rounds of pairwise distinct tile-offset residues (no atomics), 5 variant 3
  * with the tile accumulated in 32-bit fixed point by shared-memory integer
  * adds, in units of a power-of-two scale per subproblem set by the largest
@@ -221,7 +220,8 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out);
  * the tile NaN), 6 the arithmetic of 5 with one tile shared by the six
  * warps of a CTA, four CTAs per SM, and one scale per subproblem from the
  * largest bound of all its points (J = 6, T = 8, at most 256 points per
- * subproblem).  T is 4, 8 or 16; changing it re-sorts the points.
+ * subproblem; the default spread with exact_coeffs).  T is 4, 8 or 16;
+ * changing it re-sorts the points.
  * Synchronises the plan's last stream and works on cuda_stream.  Returns
  * NUFFT3D_ERR_UNSUPPORTED for a combination the plan cannot run.  Used by
  * the autotuner. */
