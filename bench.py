@@ -35,8 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "nonuniform pts/s fwd+adj NUFFT at 256^3 FP32"
 UNIT = "pts/s"
-SMS = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (nominal; the peak itself is measured)
+SMEM_BYTES_PER_CLK = 128  # shared-memory data path per SM and clock
 
 
 def parse_args():
@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fft-compare", action="store_true", help="skip the cuFFT comparison")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the reduced-precision, keep-duplicates and batch24 measurements beside the headline")
     ap.add_argument("--cpu-sample-lines", type=int, default=0,
                     help="lines of the CPU oracle sample (0: sized for about 20 s of CPU work)")
     return ap.parse_args()
@@ -285,13 +287,22 @@ def bench_workload(args):
     return dataclasses.replace(w, table_oversamp=0) if args.coeffs == "exact" else w
 
 
+def bench_config(w, args, world=1):
+    """The workload description shared by both arms (no implementation keys)."""
+    return {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "coefficients": coeff_desc(w),
+            "dirs": f"{w.n_az}x{w.n_pol}", "m": w.m, "points": w.n_points, "grid_dtype": args.grid_dtype,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "working set per step >> L2 (1.07 GB grid, 0.38 GB lines, 0.19 GB point ids)"}
+
+
 def coeff_desc(w, info=None, oracle=False):
     if w.table_oversamp:
         return f"table, L = {w.table_oversamp}, linear interpolation"
     if oracle:
         return "exact min-max per point (FP64 solve of T c = r at every point)"
-    err = f", fit error {info['coeff_fit_error']:.1e} of max|c|" if info else ""
-    return f"exact min-max per point (degree-8 polynomials fitted in FP64{err})"
+    if info:
+        return f"exact min-max per point (degree-8 polynomials fitted in FP64, fit error {info['coeff_fit_error']:.1e} of max|c|)"
+    return "exact min-max per point"
 
 
 def oracle_fixed(w, x, dirs):
@@ -356,35 +367,54 @@ def cpu_cores():
 # arms
 # ----------------------------------------------------------------------------
 def run_reference(args):
+    """The FP64 oracle on the host cores.  Each step runs the oracle's
+    size-fixed stages at full size (deapodise + pad + K^3 FFT, K^3 inverse FFT +
+    crop + deapodise) and its per-point stages (gather, line DFTs, spread) on 8
+    random lines of the 92,160, all measured; the value projects those measured
+    times to the whole workload (fixed stages once, per-point stages for every
+    line)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import numpy as np
 
-    from paper_1605_05231_gb300 import inputs as I
-
     w = bench_workload(args)
     dirs = w.directions()
     x = w.volume(np.float32)
-    op, Y, t_fixed = oracle_fixed(w, x, dirs)
     per_step_lines = 8
     rng = np.random.default_rng(0)
+
+    def one_step():
+        op, Y, tf = oracle_fixed(w, x, dirs)
+        tp = oracle_points(op, Y, np.sort(rng.choice(dirs.shape[0], per_step_lines, replace=False)))
+        return tf, tp
+
     for _ in range(args.warmup):
-        oracle_points(op, Y, np.sort(rng.choice(dirs.shape[0], per_step_lines, replace=False)))
-    t_pts = []
+        one_step()
+    t_fixed, t_pts = [], []
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        t_pts.append(oracle_points(op, Y, np.sort(rng.choice(dirs.shape[0], per_step_lines, replace=False))))
+        tf, tp = one_step()
+        t_fixed.append(tf)
+        t_pts.append(tp)
+    wall = time.perf_counter() - t0
     P = w.n_points
-    t = t_fixed + statistics.mean(t_pts) * dirs.shape[0] / per_step_lines
-    value = P / t
-    sample = (f"K^3 FFT + inverse FFT of the FP64 oracle timed once at full size ({t_fixed:.1f} s); each step "
-              f"runs its gather, spread and line DFTs on {per_step_lines} random lines of {dirs.shape[0]}, "
-              f"scaled to all {P} points")
+    tf, tp = statistics.mean(t_fixed), statistics.mean(t_pts)
+    t_full = tf + tp * dirs.shape[0] / per_step_lines
+    value = P / t_full
+    sample = (f"each step: the FP64 oracle's K^3 FFT + inverse FFT at full size ({tf:.2f} s) and its gather, "
+              f"spread and line DFTs on {per_step_lines} random lines of {dirs.shape[0]} "
+              f"({per_step_lines * w.m} points, {tp:.2f} s); value = all {P} points over the fixed stages plus "
+              f"the per-point time scaled to every line ({t_full:.0f} s projected)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "coefficients": coeff_desc(w, oracle=True),
-                       "dirs": f"{w.n_az}x{w.n_pol}", "m": w.m, "points": P},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": bench_config(w, args),
+            "measured": {"ms_per_step": 1e3 * wall / args.steps, "fixed_stages_s": tf,
+                         "per_point_stages_s": tp, "points_per_step": per_step_lines * w.m,
+                         "timed_region_s": wall},
+            "projected": {"full_workload_s": t_full, "basis": "fixed stages once + per-point stages x "
+                          f"{dirs.shape[0]}/{per_step_lines}"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -446,7 +476,7 @@ def run_ours(args):
     ms_max = max_over_ranks(world, ms)
     value = world * P / (ms_max * 1e-3)
 
-    # ---- end to end through pinned host buffers -------------------------
+    # ---- end to end: host buffers through the library's host pipeline ----
     e2e = None
     if not args.no_e2e:
         from paper_1605_05231_gb300 import HostPipeline
@@ -458,6 +488,8 @@ def run_ours(args):
         for _ in range(3):
             pipe.run(xh, lh, vh)
         pipe.synchronize()
+        if float((lh[:4].abs()).max()) == 0.0:
+            raise RuntimeError("host pipeline returned empty lines")
         n_e2e = max(3, min(args.steps, 20))
         barrier(world)
         torch.cuda.synchronize()
@@ -469,14 +501,20 @@ def run_ours(args):
         e2e = {"value": world * P / (ms_e2e * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(xh.numel() * 4),
                "d2h_bytes_per_step": int(lh.numel() * 8 + vh.numel() * 4), "ms_per_step": ms_e2e,
-               "copies": "pinned host buffers; uploads and downloads on their own streams, overlapped with the kernels",
-               "timer": "host wall clock around the enqueue loop and the final synchronize"}
+               "copies": ("pinned host buffers through the C ABI (nufft3d_host_forward_adjoint): the library "
+                          "copies the volume in and the lines and output volume out on its own streams, "
+                          "overlapped with the kernels of the neighbouring calls"),
+               "timer": "host wall clock around the enqueue loop and the final nufft3d_host_pipeline_sync"}
+        pipe.close()
     if plan.sync_status() != 0:
         raise RuntimeError("device check failed")
 
     # ---- roofline of the dominant kernel ---------------------------------
     peaks = load_peaks()
     info = plan.info()
+    from paper_1605_05231_gb300 import fp32_fma_peak
+
+    fp32_tflops, sms = fp32_fma_peak()
     fixed_point = info["spread_variant"] in (5, 6)
     work = stage_work(w.n, w.k, w.j, w.m, plan.n_dirs, info["evaluated_points"], 8 if fixed_point else 16)
     per_call = {}
@@ -487,24 +525,37 @@ def run_ours(args):
     dom = max(per_call, key=per_call.get)
     t_dom = per_call[dom] * 1e-3
     wk = work[dom[0]][dom[1]]
+    f_mhz = peaks["sm_max_mhz"]
     if "flops" in wk:
-        f_mhz = peaks["sm_max_mhz"]
-        peak = SMS * FP32_LANES_PER_SM * 2 * f_mhz * 1e6 / 1e12
+        nominal = sms * FP32_LANES_PER_SM * 2 * f_mhz * 1e6 / 1e12
         achieved = wk["flops"] / t_dom / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "kernel": f"{dom[0]}.{dom[1]}",
-                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {f_mhz:.0f} MHz"}
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp32_tflops, "kernel": f"{dom[0]}.{dom[1]}",
+                "peak_source": "measured (FP32 FMA microbenchmark, nufft3d_fp32_fma_peak, this run)",
+                "peak_nominal": nominal,
+                "peak_nominal_basis": f"{sms} SMs (device attribute) x {FP32_LANES_PER_SM} lanes x 2 x {f_mhz:.0f} MHz",
+                "flops_basis": "8 (J^3 + J^2 + J) flops per evaluated point"}
     else:
         achieved = wk["bytes"] / t_dom / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "kernel": f"{dom[0]}.{dom[1]}"}
-    roof["peak_source"] = peaks["source"]
+                "frac": achieved / peaks["hbm_gbs"], "kernel": f"{dom[0]}.{dom[1]}",
+                "peak_source": peaks["source"]}
     if "smem_bytes" in wk:
-        smem_peak = SMS * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        smem_peak = sms * SMEM_BYTES_PER_CLK * f_mhz * 1e6 / 1e12
         roof["smem_frac"] = wk["smem_bytes"] / t_dom / 1e12 / smem_peak
-        roof["smem_basis"] = (f"shared-memory data path: {SMS} SMs x 128 B/clk x {peaks['sm_max_mhz']:.0f} MHz = "
-                              f"{smem_peak:.1f} TB/s; per evaluated point J^3 x 8 B (gather, fixed-point spread) "
-                              f"or x 16 B (FP32 spread)")
+        roof["smem_basis"] = (f"shared-memory data path (derived, not measured): {sms} SMs x "
+                              f"{SMEM_BYTES_PER_CLK} B/clk x {f_mhz:.0f} MHz = {smem_peak:.1f} TB/s; per evaluated "
+                              f"point J^3 x 8 B (gather, fixed-point spread) or x 16 B (FP32 spread)")
+    # the other interpolation kernel, in the same terms
+    other = ("forward", "gather") if dom == ("adjoint", "spread") else ("adjoint", "spread")
+    if other in per_call and "flops" in work[other[0]][other[1]]:
+        wo = work[other[0]][other[1]]
+        to = per_call[other] * 1e-3
+        roof["other_interp"] = {"kernel": f"{other[0]}.{other[1]}", "ms": per_call[other],
+                                "alu_frac": wo["flops"] / to / 1e12 / fp32_tflops,
+                                "smem_frac": wo["smem_bytes"] / to / 1e12 /
+                                (sms * SMEM_BYTES_PER_CLK * f_mhz * 1e6 / 1e12),
+                                "hbm_frac": wo["bytes"] / to / 1e9 / peaks["hbm_gbs"]}
     roof["algorithmic_bytes"] = wk["bytes"]
     roof["hbm_frac"] = wk["bytes"] / t_dom / 1e9 / peaks["hbm_gbs"]
     roof["traffic"] = ncu_traffic(f"{dom[0]}.{dom[1]}")
@@ -531,25 +582,136 @@ def run_ours(args):
                           f"on {r['sample_lines']} of {plan.n_dirs} lines ({r['sample_points']} points), "
                           f"per-point time scaled to all {P} points; {r['wall']:.1f} s of CPU work")}
 
+    plan.close()
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "full256":
+        del xd, lines, vout
+        torch.cuda.empty_cache()
+        extras = run_extras(args, w, dirs, x, dev)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.grid_dtype == "c64" else f"f32+{args.grid_dtype} grid",
-                "data": "synthetic",
-                "config": {"workload": w.name, "n": w.n, "k": w.k, "j": w.j, "coefficients": coeff_desc(w, info),
-                           "dirs": f"{w.n_az}x{w.n_pol}", "m": w.m, "points": P, "grid_dtype": args.grid_dtype,
-                           "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "working set per step >> L2 (1.07 GB grid, 0.38 GB lines, 0.19 GB point ids)",
-                           "variants": plan.info()},
+                "data": "synthetic", "config": bench_config(w, args, world),
+                "plan": {"coefficients": coeff_desc(w, info), "variants": info, "plan_s": plan_s},
                 "gpu_launches": 10 * args.steps, "clocks": clk, "e2e": e2e, "roofline": roof,
-                "cpu_baseline": cpu, "stage_ms": stage_ms, "plan_s": plan_s, "cufft_comparison": fft_cmp}
+                "cpu_baseline": cpu, "stage_ms": stage_ms, "cufft_comparison": fft_cmp,
+                "fp32_fma_peak_tflops": fp32_tflops, "sm_count": sms}
+        if extras:
+            line.update(extras)
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
     return 0
+
+
+def time_steps(fn, steps, warmup, stream):
+    """Milliseconds per call of fn, CUDA events on `stream` after warm-up."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_extras(args, w, dirs, x, dev, steps=10):
+    """The forms reported beside the FP32 headline, on the same 256^3 workload
+    and coefficients: the bf16 and fp16 grid storage (throughput, and rel-L2
+    of the forward against the FP64 oracle on 64 seeded random lines), every
+    sample interpolated separately (keep_duplicates = 1), and the 24-problem
+    batch in one CUDA graph (throughput, worst per-item forward rel-L2 against
+    the oracle on 8 lines per item)."""
+    import numpy as np
+    import torch
+
+    from oracle import nufft3d_oracle as O
+    from paper_1605_05231_gb300 import Batch, Plan, autotune
+    from paper_1605_05231_gb300 import inputs as I
+
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    exact = w.table_oversamp == 0
+    xd = torch.from_numpy(x).to(dev)
+    lines = np.sort(np.random.default_rng(7).choice(dirs.shape[0], 64, replace=False))
+    op = O.OraclePlan(w.n, w.k, w.j, w.table_oversamp, dirs, w.m)
+    ref = O.nufft_forward(x.astype(np.float64), op, lines=lines)
+
+    def measure(**kw):
+        plan = Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp or 1024,
+                    exact_coeffs=exact, **kw)
+        lb = torch.empty((plan.n_dirs, plan.m), dtype=torch.complex64, device=dev)
+        vb = torch.empty_like(xd)
+
+        def step():
+            plan.forward(xd, out=lb)
+            plan.adjoint(lb, out=vb)
+
+        ms = time_steps(step, steps, 3, stream)
+        plan.forward(xd, out=lb)
+        if plan.sync_status() != 0:
+            raise RuntimeError("device check failed")
+        err = O.rel_l2(lb.cpu().numpy()[lines], ref)
+        info = plan.info()
+        plan.close()
+        return {"value": plan.n_points / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                "fwd_rel_l2_vs_oracle_64_lines": err, "evaluated_points": info["evaluated_points"]}
+
+    rp = {}
+    for dt, bar in (("bf16", 1e-4), ("fp16", 1e-4)):
+        r = measure(grid_dtype=dt)
+        r["bar"] = bar
+        r["meets_bar"] = bool(r["fwd_rel_l2_vs_oracle_64_lines"] <= bar)
+        rp[dt] = r
+    rp["note"] = ("forward grid stored as bf16 / fp16 pairs with a power-of-two scale, FP32 arithmetic; the "
+                  "adjoint stays FP32.  bf16 (unit roundoff 2^-8) misses the 1e-4 bar by its storage rounding")
+    out["reduced_precision"] = rp
+    kd = measure(keep_duplicates=True)
+    kd["note"] = ("every one of the 47,185,920 samples interpolated separately (coincident antipodal samples "
+                  "not merged); value counts samples per second, as the headline does")
+    out["keep_duplicates"] = kd
+    del xd
+    torch.cuda.empty_cache()
+
+    # 24 mixed problems in one CUDA graph
+    works = I.batched_workloads()
+    items = [dict(n=v.n, dirs=v.directions(), m=v.m, k=v.k, j=v.j, table_oversamp=v.table_oversamp,
+                  exact_coeffs=exact) for v in works]
+    t0 = time.perf_counter()
+    b = Batch(items)
+    tuned = autotune.tune_batch(b, reps=2, cache=None)
+    plan_s = time.perf_counter() - t0
+    vols = [torch.from_numpy(v.volume(np.float32)).to(dev) for v in works]
+    lns = [torch.empty((p.n_dirs, p.m), dtype=torch.complex64, device=dev) for p in b.items]
+    outs = [torch.empty_like(v) for v in vols]
+    ms = time_steps(lambda: b.forward_adjoint(vols, lns, outs), steps, 3, stream)
+    worst = 0.0
+    for i, v in enumerate(works):
+        if b.items[i].sync_status() != 0:
+            raise RuntimeError("device check failed in the batch")
+        dv = v.directions()
+        sel = np.sort(np.random.default_rng(1000 + i).choice(dv.shape[0], 8, replace=False))
+        o = O.OraclePlan(v.n, v.k, v.j, v.table_oversamp if not exact else 0, dv, v.m)
+        r = O.nufft_forward(vols[i].cpu().numpy().astype(np.float64), o, lines=sel)
+        worst = max(worst, O.rel_l2(lns[i].cpu().numpy()[sel], r))
+    Pb = sum(p.n_points for p in b.items)
+    out["batch24"] = {"value": Pb / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                      "points": Pb, "worst_item_fwd_rel_l2_vs_oracle_8_lines": worst, "plan_and_tune_s": plan_s,
+                      "items": "8 each at 64^3, 128^3, 192^3, K = M = 2N, azimuths {90,180,360} x polar {64,128}",
+                      "autotune": {k: v["best"] for k, v in tuned.items()}}
+    b.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args):

@@ -28,8 +28,15 @@
  *           plane offset s = t - M/2 (voxel units along d).
  *   dirs    unit vectors (x, y, z) in float64, copied at plan creation.
  *   grid    u = omega / gamma, gamma = 2 pi / K; taps k0 + 1 .. k0 + J with
- *           k0 = floor(u) - J/2 (J even); coefficients from a table of the
- *           min-max interpolator at f = i / L, linearly interpolated.
+ *           k0 = floor(u) - J/2 (J even), f = u - floor(u).  The min-max
+ *           coefficients c(f) = T^-1 r(f) (Eq. 2.11's interpolator) are either
+ *           exact at each point's own f (exact_coeffs = 1: degree-8 polynomial
+ *           fits, FP64-fitted, evaluated in FP32 per point) or linearly
+ *           interpolated from a table of L + 1 rows at f = i / L
+ *           (exact_coeffs = 0).
+ *   device  every call that takes a plan or a batch runs on the device that
+ *           was current when it was created and restores the caller's current
+ *           device before returning.
  *
  * Ownership and threading
  *   The caller owns every device buffer passed in and the CUDA stream.  A plan
@@ -185,6 +192,16 @@ int nufft3d_polar_resample(const void* grid_dev, int n_phi, int n_theta, int n_s
 int nufft3d_fourier_slice_weights(int n_az, int n_pol, double cone_half_angle, int m, float* radial_weight,
                                   float* line_weight);
 
+/* Measurement utility (no counterpart in the paper): the FP32 fused
+ * multiply-add throughput of the current device, measured with a kernel of
+ * independent FMA chains on every SM (the fastest of five timed launches,
+ * CUDA events on cuda_stream; about 10 ms of GPU time), in TFLOP/s (two
+ * flops per FMA), and the device's SM count.  It allocates and frees a small
+ * scratch buffer.  The arithmetic roofline of the interpolation kernels is
+ * quoted against this number.  Returns NUFFT3D_ERR_ARG for NULL outputs,
+ * NUFFT3D_ERR_CUDA if a CUDA call fails. */
+int nufft3d_fp32_fma_peak(double* tflops, int* sm_count, void* cuda_stream);
+
 /* Static description of a status code (never NULL). */
 const char* nufft3d_error_string(int status);
 
@@ -248,6 +265,17 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
  * every call): calls that overlap on the GPU, on any streams or plans, race. */
 int nufft3d_adjoint_noalloc(nufft3d_plan plan, const void* lines_dev, void* vol_dev, void* cuda_stream);
 
+/* Testing hook for the bounded device waits.  The TMA gather (variant 8)
+ * waits on an mbarrier for each tile copy; a wait that runs out of polls sets
+ * NUFFT3D_ERR_TIMEOUT in the plan's device check word, after which the CTA
+ * waits (with the full limit) for its copies still in flight and returns, so
+ * the context stays usable and the call's output is incomplete.
+ * first_wait_polls >= 0 caps the first wait on every copy at that many polls
+ * (0: it gives up at once), which makes the timeout path run on demand;
+ * first_wait_polls < 0 restores the default limit (2^22 polls).  Host only;
+ * takes effect from the next call.  Returns NUFFT3D_ERR_ARG for a NULL plan. */
+int nufft3d_plan_set_wait_limit(nufft3d_plan plan, int first_wait_polls);
+
 /* Per-stage timing with CUDA events recorded on the launching stream between
  * the kernels of each call.  nufft3d_plan_set_timing(plan, n) arms timing of
  * the next n forward and n adjoint calls (0 disarms; it synchronises the
@@ -258,6 +286,31 @@ int nufft3d_adjoint_noalloc(nufft3d_plan plan, const void* lines_dev, void* vol_
  * numbers of recorded forward and adjoint calls to calls[2], and re-arms. */
 int nufft3d_plan_set_timing(nufft3d_plan plan, int max_calls);
 int nufft3d_plan_stage_times(nufft3d_plan plan, float* fwd_ms, float* adj_ms, int* calls);
+
+/* ---------------------------------------------------------------------------
+ * Host-to-host use: the forward projection and its adjoint of volumes held in
+ * host memory (the way a reconstruction program on the CPU calls the
+ * projector; the paper's own projector runs on the host, Sec. 3.2).  A
+ * pipeline owns two sets of device buffers (volume, lines, output volume) and
+ * three streams: every call copies the volume in on the upload stream, runs
+ * the plan's forward and adjoint on the compute stream and copies the lines
+ * and the output volume out on the download stream, so the copies of one
+ * call overlap the kernels of its neighbours.  Host buffers: vol_host N^3
+ * float32 (complex64 with complex_volume), lines_host D*M complex64,
+ * vol_out_host like vol_host; they should be page-locked (cudaHostAlloc or
+ * cudaHostRegister) for the copies to overlap, and must stay untouched until
+ * nufft3d_host_pipeline_sync returns.  nufft3d_host_forward_adjoint is
+ * asynchronous; nufft3d_host_pipeline_sync waits for every call so far and
+ * returns NUFFT3D_ERR_CUDA if any of it failed.  The plan must outlive the
+ * pipeline and must not be used on other streams while calls are in flight.
+ * create allocates 2 (2 N^3 + D M) elements of device memory.
+ * ------------------------------------------------------------------------- */
+typedef struct nufft3d_host_pipeline_s* nufft3d_host_pipeline;   /* opaque */
+int nufft3d_host_pipeline_create(nufft3d_plan plan, nufft3d_host_pipeline* out);
+int nufft3d_host_forward_adjoint(nufft3d_host_pipeline pipe, const void* vol_host, void* lines_host,
+                                 void* vol_out_host);
+int nufft3d_host_pipeline_sync(nufft3d_host_pipeline pipe);
+int nufft3d_host_pipeline_destroy(nufft3d_host_pipeline pipe);
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent problems of mixed sizes and view counts (the

@@ -27,6 +27,7 @@ EXPORTS = (
     "nufft3d_plan_info",
     "nufft3d_plan_tune",
     "nufft3d_plan_set_timing",
+    "nufft3d_plan_set_wait_limit",
     "nufft3d_plan_stage_times",
     "nufft3d_adjoint_noalloc",
     "nufft3d_batch_create",
@@ -37,6 +38,11 @@ EXPORTS = (
     "nufft3d_batch_destroy",
     "nufft3d_fourier_slice_weights",
     "nufft3d_polar_resample",
+    "nufft3d_fp32_fma_peak",
+    "nufft3d_host_pipeline_create",
+    "nufft3d_host_forward_adjoint",
+    "nufft3d_host_pipeline_sync",
+    "nufft3d_host_pipeline_destroy",
 )
 
 FWD_STAGES = ("x_pass", "y_pass", "z_pass", "gather", "line_dft")
@@ -107,9 +113,15 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.nufft3d_plan_tune.argtypes = [vp, i, i, i, i, vp]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.nufft3d_plan_set_timing.argtypes = [vp, i]
+    lib.nufft3d_plan_set_wait_limit.argtypes = [vp, i]
     lib.nufft3d_plan_stage_times.argtypes = [vp, fp, fp, ip]
     lib.nufft3d_fourier_slice_weights.argtypes = [i, i, ctypes.c_double, i, fp, fp]
     lib.nufft3d_polar_resample.argtypes = [vp, i, i, i, vp, ctypes.c_longlong, i, vp, vp]
+    lib.nufft3d_fp32_fma_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ip, vp]
+    lib.nufft3d_host_pipeline_create.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.nufft3d_host_forward_adjoint.argtypes = [vp, vp, vp, vp]
+    lib.nufft3d_host_pipeline_sync.argtypes = [vp]
+    lib.nufft3d_host_pipeline_destroy.argtypes = [vp]
     for name in EXPORTS:
         if name != "nufft3d_error_string":
             getattr(lib, name).restype = ctypes.c_int
@@ -327,6 +339,12 @@ class Plan:
                                           int(points_per_subproblem), int(tile_edge),
                                           _stream_ptr(stream, self.device)), "nufft3d_plan_tune")
 
+    def set_wait_limit(self, first_wait_polls: int):
+        """Testing hook: cap the first wait on each TMA tile copy (variant 8) at
+        this many polls (0 gives up at once); a negative value restores the default."""
+        _check(self.lib.nufft3d_plan_set_wait_limit(self._handle, int(first_wait_polls)),
+               "nufft3d_plan_set_wait_limit")
+
     def set_timing(self, max_calls: int):
         """Arm per-stage CUDA-event timing of the next max_calls calls."""
         _check(self.lib.nufft3d_plan_set_timing(self._handle, int(max_calls)), "nufft3d_plan_set_timing")
@@ -447,57 +465,62 @@ class Batch:
 
 
 class HostPipeline:
-    """Forward + adjoint of volumes that live in (pinned) host memory, with the
-    host<->device copies overlapped with the projector's kernels.
-
-    Per call: the volume is copied in on an upload stream, forward runs on the
-    compute stream, the projections are copied out on a download stream while
-    the adjoint runs (both only read them), and the adjoint volume is copied out.
-    Double-buffered device inputs let the next call's upload overlap the
-    current call's kernels.  run() returns immediately; results are valid after
-    synchronize().
+    """Forward + adjoint of volumes that live in host memory, through the
+    library's host pipeline (nufft3d_host_pipeline_*): the library copies the
+    volume in, runs the plan's forward and adjoint and copies the lines and the
+    output volume out on its own streams, overlapping the copies of one call
+    with the kernels of its neighbours.  Host tensors should be pinned
+    (``tensor.pin_memory()``).  run() returns immediately; results are valid
+    after synchronize().
     """
 
     def __init__(self, plan: "Plan"):
-        import torch
-
         self.plan = plan
-        dev = plan.device
-        self.compute = torch.cuda.Stream(dev)
-        self.upload = torch.cuda.Stream(dev)
-        self.download = torch.cuda.Stream(dev)
-        self.vol = [torch.empty((plan.n,) * 3, dtype=plan.vol_dtype, device=dev) for _ in range(2)]
-        self.lines = [torch.empty((plan.n_dirs, plan.m), dtype=torch.complex64, device=dev) for _ in range(2)]
-        self.vout = [torch.empty((plan.n,) * 3, dtype=plan.vol_dtype, device=dev) for _ in range(2)]
-        self.ev_free = [torch.cuda.Event() for _ in range(2)]
-        self.k = 0
+        self.lib = plan.lib
+        h = ctypes.c_void_p()
+        _check(self.lib.nufft3d_host_pipeline_create(plan._handle, ctypes.byref(h)), "nufft3d_host_pipeline_create")
+        self._handle = h
+        self._inflight = []
 
     def run(self, vol_host, lines_host, vout_host):
-        """Enqueue one forward + adjoint: vol_host -> lines_host, vout_host."""
+        """Enqueue one forward + adjoint: vol_host -> lines_host, vout_host (host tensors)."""
         import torch
 
-        b = self.k % 2
-        self.k += 1
-        up = torch.cuda.Event()
-        fwd_done = torch.cuda.Event()
-        adj_done = torch.cuda.Event()
-        with torch.cuda.stream(self.upload):
-            self.upload.wait_event(self.ev_free[b])
-            self.vol[b].copy_(vol_host, non_blocking=True)
-            up.record(self.upload)
-        self.compute.wait_event(up)
-        self.plan.forward(self.vol[b], out=self.lines[b], stream=self.compute)
-        fwd_done.record(self.compute)
-        self.plan.adjoint(self.lines[b], out=self.vout[b], stream=self.compute)
-        adj_done.record(self.compute)
-        with torch.cuda.stream(self.download):
-            self.download.wait_event(fwd_done)
-            lines_host.copy_(self.lines[b], non_blocking=True)
-            self.download.wait_event(adj_done)
-            vout_host.copy_(self.vout[b], non_blocking=True)
-            self.ev_free[b].record(self.download)
+        p = self.plan
+        for t, shape, dt in ((vol_host, (p.n,) * 3, p.vol_dtype), (lines_host, (p.n_dirs, p.m), torch.complex64),
+                             (vout_host, (p.n,) * 3, p.vol_dtype)):
+            if t.device.type != "cpu" or tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous():
+                raise ValueError(f"host tensor must be a contiguous CPU {dt} of shape {shape}")
+        _check(self.lib.nufft3d_host_forward_adjoint(self._handle, ctypes.c_void_p(vol_host.data_ptr()),
+                                                     ctypes.c_void_p(lines_host.data_ptr()),
+                                                     ctypes.c_void_p(vout_host.data_ptr())),
+               "nufft3d_host_forward_adjoint")
+        self._inflight.append((vol_host, lines_host, vout_host))
+        del self._inflight[:-2]
 
     def synchronize(self):
-        self.compute.synchronize()
-        self.upload.synchronize()
-        self.download.synchronize()
+        _check(self.lib.nufft3d_host_pipeline_sync(self._handle), "nufft3d_host_pipeline_sync")
+        self._inflight.clear()
+
+    def close(self):
+        if getattr(self, "_handle", None):
+            self.lib.nufft3d_host_pipeline_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fp32_fma_peak(stream=None):
+    """Measured FP32 FMA throughput (TFLOP/s) and SM count of the current device."""
+    import torch
+
+    t = ctypes.c_double(0.0)
+    n = ctypes.c_int(0)
+    dev = torch.cuda.current_device()
+    _check(load_library().nufft3d_fp32_fma_peak(ctypes.byref(t), ctypes.byref(n), _stream_ptr(stream, dev)),
+           "nufft3d_fp32_fma_peak")
+    return float(t.value), int(n.value)

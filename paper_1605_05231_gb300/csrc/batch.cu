@@ -148,10 +148,9 @@ int nufft3d_batch_forward_adjoint(nufft3d_batch b, const void* const* vols, void
     key.push_back(lines[i]);
     key.push_back(vols_out[i]);
   }
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_rc(e);
-  if (dev != b->device && (e = cudaSetDevice(b->device)) != cudaSuccess) return cuda_rc(e);
+  nufft::DeviceGuard guard(b->device);
+  if (guard.status != cudaSuccess) return cuda_rc(guard.status);
+  cudaError_t e = cudaSuccess;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (!b->exec || key != b->key) {
     // plans' earlier work on other streams must not race the replay
@@ -172,7 +171,7 @@ int nufft3d_batch_invalidate(nufft3d_batch b) {
 
 int nufft3d_batch_destroy(nufft3d_batch b) {
   if (!b) return NUFFT3D_OK;
-  cudaSetDevice(b->device);
+  nufft::DeviceGuard guard(b->device);
   cudaDeviceSynchronize();
   free_batch(b);
   return NUFFT3D_OK;

@@ -14,6 +14,24 @@ namespace nufft {
 
 constexpr uint32_t kNoTwin = 0xffffffffu;
 
+// Makes `dev` the current device for the lifetime of the guard and then
+// restores the device that was current before (every C-ABI call that takes a
+// plan or a batch runs on its device and leaves the caller's choice alone).
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t status = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    status = cudaGetDevice(&prev);
+    if (status == cudaSuccess && prev != dev) status = cudaSetDevice(dev);
+    if (status != cudaSuccess || prev == dev) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // Exact min-max coefficients without a table: each c_j(f), f in [0, 1], is
 // replaced by its degree-kPolyDeg Chebyshev interpolant (fitted in FP64 at plan
 // time), stored as monomials in t = 2 f - 1 and evaluated per point by Horner's
@@ -38,6 +56,7 @@ struct InterpGeom {
   const float* lp_bound; // bound on |Y| for a reduced-precision grid (else null)
   CoefPoly poly;         // coefficient polynomials (used when L == 0)
   const CUtensorMap* tmap = nullptr;  // host copy of the grid's tensor map (gather variant 8), or null
+  int first_wait_polls = -1;          // polls of the first wait on each TMA copy (< 0: the default limit)
 };
 
 // Pruning of the column FFT passes to the cells the interpolation touches:
@@ -148,4 +167,5 @@ struct nufft3d_plan_s {
   // host copy of the per-bin offsets (for re-tuning the subproblem split)
   std::vector<long long> bin_offsets;
   cudaStream_t last_stream = nullptr;
+  int first_wait_polls = -1;  // testing hook of nufft3d_plan_set_wait_limit (< 0: default)
 };

@@ -13,8 +13,10 @@
 // some axis) cannot be one box; the threads load it instead.
 //
 // Every wait on an mbarrier is bounded: a copy that does not complete within
-// the limit sets NUFFT3D_ERR_TIMEOUT in the device check word, the CTA waits
-// (bounded again) for its other copy in flight and returns.
+// the limit sets NUFFT3D_ERR_TIMEOUT in the device check word; the CTA then
+// waits (bounded again, with the full limit) for both of its copies that may
+// still be in flight, and returns.  The limit of the first wait on each copy is
+// a launch parameter so that tests can make it run out.
 #include <cudaTypedefs.h>
 
 #include "interp_common.cuh"
@@ -67,8 +69,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kTmaWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit = kTmaWaitLimit) {
+  for (int it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -86,7 +88,7 @@ template <typename G>
 __global__ void __launch_bounds__(V8_NT, 5) k_gather_v8(InterpGeom g, const __grid_constant__ CUtensorMap tmap,
                                                         const typename G::T* __restrict__ grid,
                                                         const int4* __restrict__ subs, int n_subs, int S,
-                                                        float2* __restrict__ out) {
+                                                        float2* __restrict__ out, int first_wait_limit) {
   typedef typename G::T TT;
   typedef V8Geo<(int)sizeof(TT)> Geo;
   constexpr int J = V8_J, T = V8_T, E = V8_E, EX = Geo::EX, PP = E * EX, kRes = Geo::KRES;
@@ -185,10 +187,15 @@ __global__ void __launch_bounds__(V8_NT, 5) k_gather_v8(InterpGeom g, const __gr
       }
       __syncthreads();
     } else {
-      const bool ok = mbar_wait_bounded(bar0 + 8 * st, (parity >> st) & 1u);
+      const uint32_t ph = (parity >> st) & 1u;
+      const bool ok = mbar_wait_bounded(bar0 + 8 * st, ph, first_wait_limit);
       parity ^= 1u << st;
       if (!__syncthreads_and(ok)) {
+        // give up on this CTA, but not while a copy into its shared memory is
+        // in flight: wait (with the full limit) for the copy into this buffer
+        // and for the next one, if it was started
         if (tid == 0) atomicExch(g.err, (int)NUFFT3D_ERR_TIMEOUT);
+        mbar_wait_bounded(bar0 + 8 * st, ph);
         if (nxt < n_subs && !manual[st ^ 1]) mbar_wait_bounded(bar0 + 8 * (st ^ 1), (parity >> (st ^ 1)) & 1u);
         return;
       }
@@ -271,7 +278,8 @@ static cudaError_t launch_gather_v8_t(const InterpGeom& g, const CUtensorMap* tm
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const long long want = (long long)num_sms() * per_sm;
   const int n_cta = (int)(want < n_subs ? want : n_subs);
-  f<<<n_cta, V8_NT, smem, st>>>(g, *tmap, (const typename G::T*)grid, subs, n_subs, g.S, out);
+  const int first_limit = g.first_wait_polls >= 0 ? g.first_wait_polls : kTmaWaitLimit;
+  f<<<n_cta, V8_NT, smem, st>>>(g, *tmap, (const typename G::T*)grid, subs, n_subs, g.S, out, first_limit);
   return cudaGetLastError();
 }
 

@@ -59,16 +59,12 @@ extern "C" int nufft3d_adjoint_noalloc(nufft3d_plan pl, const void* lines_dev, v
   const size_t n_a = round_up((size_t)N * N * K);
   const size_t n_cnt = kAlignF2;
   if ((n_lines + n_grid + n_b + n_a + n_cnt) * sizeof(float2) > kNoAllocScratchBytes) return NUFFT3D_ERR_UNSUPPORTED;
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return status_of(e);
-  if (dev != pl->device) {
-    e = cudaSetDevice(pl->device);
-    if (e != cudaSuccess) return status_of(e);
-    dev = pl->device;
-  }
+  // the plan's device is current until return; the caller's device is restored then
+  nufft::DeviceGuard guard(pl->device);
+  if (guard.status != cudaSuccess) return status_of(guard.status);
+  const int dev = pl->device;
   float2* base = nullptr;
-  e = scratch_address(dev, &base);
+  cudaError_t e = scratch_address(dev, &base);
   if (e != cudaSuccess) return status_of(e);
   float2* lines_tmp = base;
   float2* grid = lines_tmp + n_lines;

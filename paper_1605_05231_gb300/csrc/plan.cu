@@ -401,6 +401,7 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.lp_bound = pl->d_lp_bound;
   g.poly = pl->poly;
   g.tmap = pl->tmap_ok ? &pl->tmap_grid : nullptr;
+  g.first_wait_polls = pl->first_wait_polls;
   return g;
 }
 
@@ -561,12 +562,11 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   return NUFFT3D_OK;
 }
 
-int ensure_device(nufft3d_plan pl) {
-  int dev = -1;
-  CK(cudaGetDevice(&dev));
-  if (dev != pl->device) CK(cudaSetDevice(pl->device));
-  return NUFFT3D_OK;
-}
+// the plan's device, current until the end of the calling scope; the caller's
+// current device is restored on return
+#define PLAN_DEVICE(pl)                                 \
+  nufft::DeviceGuard dev_guard_((pl)->device);          \
+  if (dev_guard_.status != cudaSuccess) return NUFFT3D_ERR_CUDA
 
 // records the event closing stage `stage` of the current timed call (stage -1 opens it)
 struct StageClock {
@@ -693,16 +693,14 @@ int nufft3d_plan_create(nufft3d_plan* out, const nufft3d_params* p, void* cuda_s
 
 int nufft3d_forward(nufft3d_plan plan, const void* vol_dev, void* lines_dev, void* cuda_stream) {
   if (!plan || !vol_dev || !lines_dev) return NUFFT3D_ERR_ARG;
-  int rc = ensure_device(plan);
-  if (rc != NUFFT3D_OK) return rc;
+  PLAN_DEVICE(plan);
   plan->last_stream = (cudaStream_t)cuda_stream;
   return forward_impl(plan, vol_dev, lines_dev, (cudaStream_t)cuda_stream);
 }
 
 int nufft3d_adjoint(nufft3d_plan plan, const void* lines_dev, void* vol_dev, void* cuda_stream) {
   if (!plan || !vol_dev || !lines_dev) return NUFFT3D_ERR_ARG;
-  int rc = ensure_device(plan);
-  if (rc != NUFFT3D_OK) return rc;
+  PLAN_DEVICE(plan);
   plan->last_stream = (cudaStream_t)cuda_stream;
   return adjoint_impl(plan, lines_dev, vol_dev, (cudaStream_t)cuda_stream);
 }
@@ -754,8 +752,7 @@ int nufft3d_workspace_bytes(const nufft3d_params* p, size_t* bytes) {
 
 int nufft3d_plan_sync_status(nufft3d_plan plan, int* device_status) {
   if (!plan || !device_status) return NUFFT3D_ERR_ARG;
-  int rc = ensure_device(plan);
-  if (rc != NUFFT3D_OK) return rc;
+  PLAN_DEVICE(plan);
   int v = 0;
   CK(cudaStreamSynchronize(plan->last_stream));
   CK(cudaMemcpy(&v, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -766,7 +763,7 @@ int nufft3d_plan_sync_status(nufft3d_plan plan, int* device_status) {
 
 int nufft3d_plan_destroy(nufft3d_plan plan) {
   if (!plan) return NUFFT3D_OK;
-  ensure_device(plan);
+  nufft::DeviceGuard guard(plan->device);
   cudaDeviceSynchronize();
   free_plan(plan);
   return NUFFT3D_OK;
@@ -833,8 +830,8 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   if (sv == 4 && !nufft::v4s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 5 && !nufft::v5s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 6 && !nufft::v6s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
-  int rc = ensure_device(plan);
-  if (rc != NUFFT3D_OK) return rc;
+  PLAN_DEVICE(plan);
+  int rc = NUFFT3D_OK;
   CK(cudaStreamSynchronize(plan->last_stream));
   plan->gather_variant = gv;
   plan->spread_variant = sv;
@@ -855,10 +852,15 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   return rc;
 }
 
+int nufft3d_plan_set_wait_limit(nufft3d_plan plan, int first_wait_polls) {
+  if (!plan) return NUFFT3D_ERR_ARG;
+  plan->first_wait_polls = first_wait_polls < 0 ? -1 : first_wait_polls;
+  return NUFFT3D_OK;
+}
+
 int nufft3d_plan_set_timing(nufft3d_plan plan, int max_calls) {
   if (!plan || max_calls < 0) return NUFFT3D_ERR_ARG;
-  int rc = ensure_device(plan);
-  if (rc != NUFFT3D_OK) return rc;
+  PLAN_DEVICE(plan);
   CK(cudaStreamSynchronize(plan->last_stream));
   for (cudaEvent_t e : plan->ev_fwd) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_adj) cudaEventDestroy(e);
@@ -878,8 +880,7 @@ int nufft3d_plan_set_timing(nufft3d_plan plan, int max_calls) {
 
 int nufft3d_plan_stage_times(nufft3d_plan plan, float* fwd_ms, float* adj_ms, int* calls) {
   if (!plan || !fwd_ms || !adj_ms || !calls) return NUFFT3D_ERR_ARG;
-  int rc = ensure_device(plan);
-  if (rc != NUFFT3D_OK) return rc;
+  PLAN_DEVICE(plan);
   CK(cudaStreamSynchronize(plan->last_stream));
   for (int s = 0; s < FWD_STAGES; ++s) fwd_ms[s] = 0.f;
   for (int s = 0; s < ADJ_STAGES; ++s) adj_ms[s] = 0.f;

@@ -17,7 +17,9 @@ from paper_1605_05231_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
-LP_BOUND = {"bf16": 4e-3, "fp16": 5e-4}
+# fp16 grid storage meets the 1e-4 bar; bf16 (unit roundoff 2^-8) misses it by
+# storage rounding, so its bound pins the measured level instead
+LP_BOUND = {"bf16": 1e-3, "fp16": 1e-4}
 
 
 def _plan(binding, n, dirs, m=0, k=0, j=6, **kw):

@@ -351,6 +351,22 @@ def test_host_pipeline_matches_device_path(cuda_lib):
         ref_o = plan.adjoint(ref_l)
         assert torch.allclose(l, ref_l.cpu(), rtol=0, atol=1e-5 * float(ref_l.abs().max()))
         assert torch.allclose(o, ref_o.cpu(), rtol=0, atol=1e-5 * float(ref_o.abs().max()))
+    pipe.close()
+
+
+def test_fp32_fma_peak_is_plausible(cuda_lib):
+    """The measured FP32 FMA throughput lies between half and 1.05x of the
+    nominal SMs x 128 lanes x 2 flops x the device's maximum clock."""
+    import torch
+
+    tflops, sms = cuda_lib.fp32_fma_peak()
+    props = torch.cuda.get_device_properties(0)
+    assert sms == props.multi_processor_count
+    lib = cuda_lib.load_library()
+    assert lib.nufft3d_fp32_fma_peak(None, None, None) == -1
+    nominal_at_2_1ghz = sms * 128 * 2 * 2.1e9 / 1e12
+    print(f"FP32 FMA peak {tflops:.1f} TFLOP/s on {sms} SMs")
+    assert 0.5 * nominal_at_2_1ghz < tflops < 1.05 * nominal_at_2_1ghz
 
 
 @pytest.mark.parametrize("grid_dtype", ["c64", "bf16"])

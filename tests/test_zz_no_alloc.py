@@ -30,13 +30,17 @@ def _noalloc(lib, plan, lines, out):
                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def test_noalloc_adjoint_matches_adjoint_twice(cuda_lib):
+@pytest.mark.parametrize("exact", [False, True], ids=["table", "exact"])
+def test_noalloc_adjoint_matches_adjoint_twice(cuda_lib, exact):
+    """Both coefficient modes: the table with its default spread (FP32 tiles)
+    and the exact coefficients with theirs (fixed-point tiles shared by a CTA)."""
     import torch
 
     lib = cuda_lib.load_library()
     w = I.workload("tiny32")
     dirs = w.directions()
-    plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp)
+    plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp, exact_coeffs=exact)
+    assert plan.info()["spread_variant"] == (6 if exact else 3)
     for seed in (21, 22):
         y = torch.from_numpy(I.random_lines(dirs.shape[0], w.m, seed).astype(np.complex64)).cuda()
         ref = plan.adjoint(y).clone()
@@ -47,7 +51,7 @@ def test_noalloc_adjoint_matches_adjoint_twice(cuda_lib):
         err = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
         assert err < TOL, err
     # and against the FP64 oracle for the last call
-    op = O.OraclePlan(w.n, w.k, w.j, w.table_oversamp, dirs, w.m)
+    op = O.OraclePlan(w.n, w.k, w.j, 0 if exact else w.table_oversamp, dirs, w.m)
     assert O.rel_l2(out.cpu().numpy(), O.nufft_adjoint(y.cpu().numpy().astype(np.complex128), op)) < TOL
     plan.close()
 
