@@ -302,7 +302,9 @@ int nufft3d_plan_stage_times(nufft3d_plan plan, float* fwd_ms, float* adj_ms, in
  * nufft3d_host_pipeline_sync returns.  nufft3d_host_forward_adjoint is
  * asynchronous; nufft3d_host_pipeline_sync waits for every call so far and
  * returns NUFFT3D_ERR_CUDA if any of it failed.  The plan must outlive the
- * pipeline and must not be used on other streams while calls are in flight.
+ * pipeline and must not be used on other streams while calls are in flight;
+ * destroying the pipeline hands the plan back to the legacy default stream
+ * (the stream nufft3d_plan_sync_status synchronises) until its next call.
  * create allocates 2 (2 N^3 + D M) elements of device memory.
  * ------------------------------------------------------------------------- */
 typedef struct nufft3d_host_pipeline_s* nufft3d_host_pipeline;   /* opaque */

@@ -128,6 +128,8 @@ int nufft3d_host_pipeline_destroy(nufft3d_host_pipeline hp) {
   cudaStreamSynchronize(hp->upload);
   cudaStreamSynchronize(hp->compute);
   cudaStreamSynchronize(hp->download);
+  // the plan remembers the stream of its last call; that stream is about to go
+  if (hp->plan->last_stream == hp->compute) hp->plan->last_stream = nullptr;
   release(hp);
   return NUFFT3D_OK;
 }

@@ -351,7 +351,14 @@ def test_host_pipeline_matches_device_path(cuda_lib):
         ref_o = plan.adjoint(ref_l)
         assert torch.allclose(l, ref_l.cpu(), rtol=0, atol=1e-5 * float(ref_l.abs().max()))
         assert torch.allclose(o, ref_o.cpu(), rtol=0, atol=1e-5 * float(ref_o.abs().max()))
+    pipe2 = cuda_lib.HostPipeline(plan)
+    pipe2.run(vols[0], lines[0], outs[0])
+    pipe2.synchronize()
+    pipe2.close()
     pipe.close()
+    # the plan no longer refers to the pipelines' streams
+    assert plan.sync_status() == 0
+    plan.close()
 
 
 def test_fp32_fma_peak_is_plausible(cuda_lib):
