@@ -205,7 +205,8 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-INTERP_SOURCES = ("interp_common.cuh", "interp_gather.cu", "interp_spread.cu", "interp_tma.cu", "common.cuh")
+INTERP_SOURCES = ("interp_common.cuh", "interp_gather.cu", "interp_spread.cu", "interp_tma.cu", "interp_real.cu",
+                  "common.cuh")
 
 
 def source_hash(files=INTERP_SOURCES) -> str:

@@ -27,9 +27,11 @@ of Eq. 2.3) evaluated directly, then L_w.  With w = 1 this is the periodic-sinc
 (Dirichlet) plane sum of Eqs. 2.6-2.7: p[s] = sum_n x[n] D_M(d.n - s).
 
 Readings of points the paper leaves open:
-  * scaling s(n) = Psi(0) / Psi(n/K), Psi the Fourier transform of the
-    Kaiser-Bessel window of width J and shape alpha = 2.34 J (the paper names a
-    Kaiser-Bessel / raised-cosine pre-window, Sec. 2.1.3, without formula);
+  * scaling s(n) = Psi(0) / Psi((n - n_c)/K), Psi the Fourier transform of the
+    Kaiser-Bessel window of width J and shape alpha = 2.34 J, centred on the
+    middle n_c of the index range (n_c = -1/2 for even N, 0 for odd N), so the
+    pre-window is symmetric over the volume (the paper names a Kaiser-Bessel /
+    raised-cosine pre-window, Sec. 2.1.3 and Eq. 2.11, without formula);
   * taps k0 + j, j = 1..J, k0 = floor(u - J/2), f = u - J/2 - k0 in [0, 1),
     u = omega / gamma, gamma = 2 pi / K;
   * min-max coefficients c(f) = T^{-1} r(f), T_{jj'} = sum_n s(n)^2 e^{i gamma (j-j') n},
@@ -92,10 +94,18 @@ def kb_window_ft(nu, J: int, alpha: Optional[float] = None):
     return J * out
 
 
+def index_centre(N: int) -> float:
+    """Middle of the centred index range -N//2 .. N - N//2 - 1: -1/2 for even N,
+    0 for odd N."""
+    return 0.5 * ((-(N // 2)) + (N - N // 2 - 1))
+
+
 def scaling_factors(N: int, K: int, J: int) -> np.ndarray:
-    """s(n) = Psi(0) / Psi(n / K) for the centred index n = -N/2 .. N/2-1."""
+    """s(n) = Psi(0) / Psi((n - n_c) / K) for the centred index n = -N/2 .. N/2-1,
+    n_c the middle of that range: the Kaiser-Bessel pre-window symmetric over
+    the volume (s(n) = s(2 n_c - n))."""
     n = np.arange(-(N // 2), N - N // 2, dtype=np.float64)
-    return kb_window_ft(0.0, J) / kb_window_ft(n / K, J)
+    return kb_window_ft(0.0, J) / kb_window_ft((n - index_centre(N)) / K, J)
 
 
 # -----------------------------------------------------------------------------

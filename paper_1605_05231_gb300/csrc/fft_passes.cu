@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_row_fwd_real(const flo
 //   CROP_OUT: only the N centred outputs are written (inverse passes)
 // element (i, c) of the input at in[o in_outer + i in_stride + ch W + c]
 // ----------------------------------------------------------------------------
-template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT, int W>
+template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT, int W, bool PHASE = false>
 __global__ void __launch_bounds__(32 * W, 32 / W) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
                                                 int N, int n_chunks, long long in_outer, long long in_stride,
                                                 long long out_outer, long long out_stride,
@@ -195,6 +195,12 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_col(const float2* __restrict
     const int cx = cen(ch * W + c);
     return (long long)cx * cx + cy2 <= pr.r2;
   };
+  // z passes of the real-weight kernels: e^{-i gamma (kx + ky + kz)/2} for the
+  // cell (kz = k, ky = o, kx = ch W + c), from the per-axis table.  A thread
+  // always serves column c = threadIdx.x % W, so its (ky, kx) factor is fixed.
+  float2 col_ph = make_float2(1.f, 0.f);
+  if (PHASE) col_ph = cmul(__ldg(pr.phase + o), __ldg(pr.phase + ch * W + (int)(threadIdx.x % W)));
+  auto cell_phase = [&](int k, int c) -> float2 { return cmul(__ldg(pr.phase + k), col_ph); };
   // centred row i of an N-row input or output <-> grid row k of the L-point
   // transform: k = i - N/2 (mod L); rows N/2 <= k < L - N/2 are the padding
   auto load = [&](int k, int c) -> float2 {
@@ -211,9 +217,11 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_col(const float2* __restrict
     } else if (INV && !live(k, c)) {
       return make_float2(0.f, 0.f);  // cells outside the touched ball are zero
     }
+    if constexpr (INV && PHASE) return cmulc(ib[(long long)i * in_stride + c], cell_phase(k, c));
     return ib[(long long)i * in_stride + c];
   };
   auto store = [&](int k, int c, float2 v) {
+    if constexpr (!INV && PHASE) v = cmul(v, cell_phase(k, c));  // the real-weight gather's grid phase
     int i = k;
     if (CROP_OUT) {
       if (k < half) i = k + half;
@@ -531,12 +539,12 @@ cudaError_t launch_row_adj(int K, const float2* in, void* vol, int cplx, const f
   return cudaErrorInvalidValue;
 }
 
-template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT, int W>
+template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT, int W, bool PHASE>
 static cudaError_t launch_col_w(const float2* in, OutT* out, int N, int n_outer, int row_len,
                                 long long in_outer, long long in_stride, long long out_outer,
                                 long long out_stride, const float2* tw, const float* out_scale, ColPrune pr,
                                 cudaStream_t st) {
-  auto f = k_col<L, INV, PAD_IN, CROP_OUT, OutT, W>;
+  auto f = k_col<L, INV, PAD_IN, CROP_OUT, OutT, W, PHASE>;
   const size_t smem = (size_t)L * (W + 1) * sizeof(float2);
   cudaError_t e = set_smem(f, smem);
   if (e != cudaSuccess) return e;
@@ -554,8 +562,11 @@ static cudaError_t launch_col_t(const float2* in, OutT* out, int N, int n_outer,
                                 cudaStream_t st) {
   // 16 columns (128-byte row segments), 512 threads, two CTAs per SM: 32
   // columns with 1024 threads (one CTA per SM) measured 0.1 ms slower per z pass
-  return launch_col_w<L, INV, PAD_IN, CROP_OUT, OutT, 16>(in, out, N, n_outer, row_len, in_outer, in_stride,
-                                                           out_outer, out_stride, tw, out_scale, pr, st);
+  if (pr.phase)
+    return launch_col_w<L, INV, PAD_IN, CROP_OUT, OutT, 16, true>(in, out, N, n_outer, row_len, in_outer, in_stride,
+                                                                   out_outer, out_stride, tw, out_scale, pr, st);
+  return launch_col_w<L, INV, PAD_IN, CROP_OUT, OutT, 16, false>(in, out, N, n_outer, row_len, in_outer, in_stride,
+                                                                  out_outer, out_stride, tw, out_scale, pr, st);
 }
 
 cudaError_t launch_col_fwd(int L, const float2* in, float2* out, int N, int n_outer, int row_len,

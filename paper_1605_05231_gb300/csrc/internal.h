@@ -42,6 +42,14 @@ constexpr int kPolyMaxJ = 8;
 struct CoefPoly {
   float a[kPolyMaxJ][2][kPolyDeg + 1];  // [tap][re, im][power of t]
 };
+// With the pre-window symmetric about the middle of the index range, the
+// min-max coefficients factor as c_j(f) = e^{i gamma (f + J/2 - j)/2} rho_j(f)
+// with rho_j real; the real-weight kernels evaluate rho_j from these fits and
+// carry the phases on the point (e^{i gamma (ux + uy + uz)/2}) and on the grid
+// cell (e^{-i gamma (kx + ky + kz)/2}, applied by the z passes).
+struct RealPoly {
+  float a[kPolyMaxJ][kPolyDeg + 1];  // [tap][power of t]
+};
 
 // point-to-tile binning and the interpolation kernels' view of a plan
 struct InterpGeom {
@@ -55,6 +63,7 @@ struct InterpGeom {
   int S;                 // most points in one subproblem
   const float* lp_bound; // bound on |Y| for a reduced-precision grid (else null)
   CoefPoly poly;         // coefficient polynomials (used when L == 0)
+  RealPoly rpoly;        // real weights rho_j (real-weight variants, L == 0)
   const CUtensorMap* tmap = nullptr;  // host copy of the grid's tensor map (gather variant 8), or null
   int first_wait_polls = -1;          // polls of the first wait on each TMA copy (< 0: the default limit)
 };
@@ -71,6 +80,11 @@ struct ColPrune {
   int K = 0;
   long long r2 = 0;
   int consume = 0;  // inverse z pass: zero every grid row it reads (the adjoint grid is left clear)
+  // z passes only: per-cell phase e^{-i gamma (kx + ky + kz)/2} (centred k) of the
+  // real-weight interpolation kernels, from the K-entry table phase[k] =
+  // e^{-i gamma k_c / 2}: the forward pass multiplies its output by it, the
+  // inverse pass its input by the conjugate.  Null: no phase.
+  const float2* phase = nullptr;
 };
 
 bool fft_length_supported(int L);
@@ -115,6 +129,15 @@ bool v3s_supported(int T, int J);
 bool v4s_supported(int T, int J, int S);
 bool v5s_supported(int T, int J, int S);
 bool v6s_supported(int T, int J, int S);
+bool v9_supported(int T, int J, int S);
+bool v7s_supported(int T, int J, int S);
+cudaError_t launch_gather_real(const InterpGeom& g, int grid_dtype, const void* grid, const int4* subs, int n_subs,
+                               float2* out, cudaStream_t st);
+cudaError_t launch_spread_real(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
+                               cudaStream_t st);
+// the variants with real weights and phases (they need the phased grid)
+inline bool gather_real(int variant) { return variant == 9; }
+inline bool spread_real(int variant) { return variant == 7; }
 
 }  // namespace nufft
 
@@ -126,6 +149,9 @@ struct nufft3d_plan_s {
   int N, K, J, L, D, M;  // L = 0: exact coefficients from the fitted polynomials
   long long P;
   nufft::CoefPoly poly{};
+  nufft::RealPoly rpoly{};
+  bool real_ok = false;         // the real-weight variants may run (exact coefficients, phase table built)
+  float2* d_phase = nullptr;    // K entries e^{-i gamma k_c / 2}
   CUtensorMap tmap_grid{};  // tensor map of the grid the gather reads (d_grid or d_grid_lp)
   bool tmap_ok = false;
   double poly_err = 0.0;  // max |fit - exact| / max |c| of the polynomials (0 with a table)

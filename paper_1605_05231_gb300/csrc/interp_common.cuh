@@ -8,6 +8,16 @@
 
 namespace nufft {
 
+// The first tap fl - J/2 + 1 wrapped into [0, K).  The plan admits |u| <= K/2
+// (|omega| <= pi, |d| <= 1), so one conditional add or subtract of K wraps it;
+// anything else takes the general modulo.
+__device__ __forceinline__ int wrap_tap(int s, int K) {
+  s += s < 0 ? K : 0;
+  s -= s >= K ? K : 0;
+  if ((unsigned)s >= (unsigned)K) s = ((s % K) + K) % K;
+  return s;
+}
+
 // first tap (wrapped into [0, K)) and fractional offset of each axis
 template <int J>
 __device__ __forceinline__ void decode_point(const InterpGeom& g, uint32_t id, int (&w0)[3], float (&f)[3]) {
@@ -19,9 +29,59 @@ __device__ __forceinline__ void decode_point(const InterpGeom& g, uint32_t id, i
     const float2 d = __ldg(g.dir + (size_t)l * 3 + a);
     int fl;
     reduce_coord(r.x, r.y, d.x, d.y, fl, f[a]);
-    int s = (fl - J / 2 + 1) % g.K;
-    if (s < 0) s += g.K;
-    w0[a] = s;
+    w0[a] = wrap_tap(fl - J / 2 + 1, g.K);
+  }
+}
+
+// decode_point plus what the real-weight kernels need: per axis the mask of
+// taps whose unwrapped index k lies outside [-K/2, K/2) (their grid cell holds
+// the phase of k -/+ K, which differs by a sign), and the point's phase
+// e^{i gamma (ux + uy + uz) / 2} = e^{i pi (ux + uy + uz) / K}.
+template <int J>
+__device__ __forceinline__ void decode_point_real(const InterpGeom& g, uint32_t id, int (&w0)[3], float (&f)[3],
+                                                  int (&flip)[3], float2& phase) {
+  const int l = (int)(id / (uint32_t)g.M);
+  const int m = (int)(id - (uint32_t)l * (uint32_t)g.M);
+  const float2 r = __ldg(g.rad + m);
+  const int K = g.K, h = K / 2;
+  int su = 0;
+  float sf = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float2 d = __ldg(g.dir + (size_t)l * 3 + a);
+    int fl;
+    reduce_coord(r.x, r.y, d.x, d.y, fl, f[a]);
+    const int kf = fl - J / 2 + 1;  // unwrapped first tap
+    w0[a] = wrap_tap(kf, K);
+    int mk = 0;
+    if (kf < -h || kf + J - 1 >= h) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) mk |= ((kf + j < -h) || (kf + j >= h)) ? (1 << j) : 0;
+    }
+    flip[a] = mk;
+    su += fl;
+    sf += f[a];
+  }
+  // e^{i pi (su + sf) / K}: su reduced modulo 2K into [-K, K) first
+  su = su % (2 * K);
+  su += su < -K ? 2 * K : 0;
+  su -= su >= K ? 2 * K : 0;
+  float sn, cs;
+  sincospif(((float)su + sf) / (float)K, &sn, &cs);
+  phase = make_float2(cs, sn);
+}
+
+// real weights rho_j(f) of one axis from their fitted polynomials (Horner in
+// t = 2 f - 1), with the taps of `flip` negated
+template <int J>
+__device__ __forceinline__ void real_coeffs(const RealPoly& P, float f, int flip, float (&c)[J]) {
+  const float t = fmaf(2.f, f, -1.f);
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    float v = P.a[j][kPolyDeg];
+#pragma unroll
+    for (int q = kPolyDeg - 1; q >= 0; --q) v = fmaf(v, t, P.a[j][q]);
+    c[j] = (flip >> j) & 1 ? -v : v;
   }
 }
 
@@ -209,6 +269,50 @@ static __device__ const unsigned short kLaneOvfI13[32] = {236, 40, 41, 42, 43, 2
 // zero to a cell at an offset whose residue is free in their instruction, so
 // the instruction runs without a predicate and keeps its wavefront count.
 static __device__ const unsigned char kPadI13[3] = {19, 24, 25};  // main lane 31, extra lanes 30 and 31
+
+// ---------------------------------------------------------------------------
+// fixed-point tile accumulation (spreads 5, 6 and 7): rounding of a
+// contribution to an integer number of units by an FMA with 1.5 * 2^23 (floats
+// in [2^23, 2^24) are spaced by 1), and the lanes' taps on a 13^3 int32 tile
+// ---------------------------------------------------------------------------
+constexpr float kRoundMagic = 12582912.0f;            // 1.5 * 2^23
+constexpr int kRoundMagicBits = 0x4B400000;           // its bits
+constexpr int kTileEmpty = -1000;                     // tile exponent before the first point
+constexpr unsigned kBoundLimitBits = (100u + 127u) << 23;  // 2^100: larger bounds (and NaN) poison the tile
+
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }  // -126 <= k <= 127
+
+// a b + c d rounded to an integer, for |a b|, |c d|, |a b + c d| < 2^22
+__device__ __forceinline__ int round_units(float a, float b, float c, float d) {
+  return __float_as_int(fmaf(a, b, fmaf(c, d, kRoundMagic))) - kRoundMagicBits;
+}
+
+struct V5Lanes {
+  int main_off, ovf_off;
+  int mjx, mjy, ojx, ojy, ojz;
+  bool has_main, has_ovf;
+};
+
+__device__ __forceinline__ V5Lanes v5_lanes(int lane) {
+  constexpr int E = 13;
+  const unsigned m = kLaneMainI13[lane], o = kLaneOvfI13[lane];
+  V5Lanes r;
+  r.has_main = m != 255u;
+  r.has_ovf = o != 65535u;
+  r.mjx = r.has_main ? (m & 7) : 0;
+  r.mjy = r.has_main ? ((m >> 3) & 7) : 0;
+  r.ojx = r.has_ovf ? (o & 7) : 0;
+  r.ojy = r.has_ovf ? ((o >> 3) & 7) : 0;
+  r.ojz = r.has_ovf ? ((o >> 6) & 7) : 0;
+  r.main_off = r.mjx + E * r.mjy;
+  r.ovf_off = r.ojx + E * r.ojy + E * E * r.ojz;
+  return r;
+}
+
+// a b rounded to an integer, for |a b| < 2^22
+__device__ __forceinline__ int round_unit1(float a, float b) {
+  return __float_as_int(fmaf(a, b, kRoundMagic)) - kRoundMagicBits;
+}
 
 constexpr int V2_WARPS = 8;
 constexpr int V2_CSTRIDE = 18;  // float2 per point: cx[6] cy[6] cz[6]

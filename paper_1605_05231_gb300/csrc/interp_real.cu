@@ -1,0 +1,360 @@
+// Interpolation kernels with real weights (gather variant 9, spread variant 7).
+//
+// With the pre-window symmetric about the middle of the index range the
+// min-max coefficients of Eq. 2.11's interpolator factor exactly as
+//   c_j(f) = e^{i gamma (u - k) / 2} rho_j(f),  rho_j real,  k = k0 + j,
+// so the forward interpolation of one point is
+//   X^(u) = e^{i gamma (ux + uy + uz)/2}
+//           sum_k rho(fx) rho(fy) rho(fz) e^{-i gamma (kx + ky + kz)/2} Y[k mod K].
+// The grid phase e^{-i gamma (kx + ky + kz)/2} is applied by the forward z pass
+// (the grid then holds Y~), and its conjugate by the inverse z pass for the
+// spread, which accumulates e^{-i gamma (ux + uy + uz)/2} v rho rho rho.  A tap
+// whose unwrapped index lies outside [-K/2, K/2) reads a cell whose centred
+// index differs by K, hence a phase of opposite sign: its weight is negated.
+// Per tap this is a real weight times a complex value (2 FMAs) instead of a
+// complex product (4), and the coefficient evaluation is real.
+//
+// Gather 9: the one-thread-per-point gather of variant 5 (128-thread CTAs,
+// points in round-robin order over the residue classes of their tile offset).
+// Spread 7: the fixed-point spread of variant 6 (one 13^3 int32 tile per CTA
+// of six warps, lane tables, exponent per subproblem).
+#include "interp_common.cuh"
+
+namespace nufft {
+
+// ---------------------------------------------------------------------------
+// gather 9
+// ---------------------------------------------------------------------------
+constexpr int V9_NT = 128;
+
+// per point: id, twin, tile offset, f[3], flip masks, phase (2), ordered index
+__host__ __device__ inline size_t v9_bytes(int T, int J, int S, int elem) {
+  const int E = T + J - 1;
+  const size_t tile = ((size_t)E * E * E * elem + 15) / 16 * 16;
+  return tile + (size_t)S * 10 * sizeof(int) + 64 * sizeof(int);
+}
+
+template <int J, typename G>
+__global__ void __launch_bounds__(V9_NT, J <= 6 ? 8 : 1) k_gather_v9(InterpGeom g, const typename G::T* __restrict__ grid,
+                                                                 const int4* __restrict__ subs, int S,
+                                                                 float2* __restrict__ out) {
+  typedef typename G::T TT;
+  constexpr int T = 8, NT = V9_NT;
+  constexpr int kRes = sizeof(TT) == 4 ? 32 : 16;
+  constexpr int E = T + J - 1, E2 = E * E, PP = E2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const float inv_scale = lp_inv_scale<G>(g);
+  const int nT = g.nT, K = g.K;
+  const size_t tile_bytes = ((size_t)E * E * E * sizeof(TT) + 15) / 16 * 16;
+  TT* tile = (TT*)smem_raw;
+  int* p_id = (int*)(smem_raw + tile_bytes);
+  int* p_tw = p_id + S;
+  int* p_off = p_tw + S;
+  float* p_f = (float*)(p_off + S);  // [3][S]
+  int* p_flip = (int*)(p_f + 3 * S);
+  float2* p_ph = (float2*)(p_flip + S);  // 8-byte aligned: S is even
+  int* order = (int*)(p_ph + S);
+  int* ncls = order + S;  // [kRes] counts, [kRes] cursors
+  const int4 sp = subs[blockIdx.x];
+  const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+  const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+  const int cnt = sp.z;
+  if (threadIdx.x < 2 * kRes) ncls[threadIdx.x] = 0;
+  for (int r = threadIdx.x; r < E2 * E; r += NT) {
+    const int row = r / E, ix = r - row * E;
+    const int iz = row / E, iy = row - iz * E;
+    int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+    gx -= gx >= K ? K : 0;
+    gy -= gy >= K ? K : 0;
+    gz -= gz >= K ? K : 0;
+    tile[r] = grid[((size_t)gz * K + gy) * K + gx];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += NT) {
+    const uint2 ent = g.sorted[sp.y + i];
+    int w0[3], fm[3];
+    float f[3];
+    float2 ph;
+    decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+    const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+    int off = -1;
+    if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+      off = (lz * E + ly) * E + lx;
+    } else {
+      atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+    }
+    p_id[i] = (int)ent.x;
+    p_tw[i] = (int)ent.y;
+    p_off[i] = off;
+    p_f[i] = f[0];
+    p_f[S + i] = f[1];
+    p_f[2 * S + i] = f[2];
+    p_flip[i] = fm[0] | (fm[1] << 8) | (fm[2] << 16);
+    p_ph[i] = ph;
+    atomicAdd(&ncls[off < 0 ? 0 : (off & (kRes - 1))], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += NT) {
+    const int c = p_off[i] < 0 ? 0 : (p_off[i] & (kRes - 1));
+    const int r = atomicAdd(&ncls[kRes + c], 1);
+    int pos = 0;
+#pragma unroll
+    for (int q = 0; q < kRes; ++q) {
+      const int n = ncls[q];
+      pos += n < r ? n : r;
+      pos += (q < c && n > r) ? 1 : 0;
+    }
+    order[pos] = i;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < cnt; k += NT) {
+    const int i = order[k];
+    const int off = p_off[i];
+    if (off < 0) continue;
+    const int fm = p_flip[i];
+    float rx[J], ry[J], rz[J];
+    real_coeffs<J>(g.rpoly, p_f[i], fm & 0xff, rx);
+    real_coeffs<J>(g.rpoly, p_f[S + i], (fm >> 8) & 0xff, ry);
+    real_coeffs<J>(g.rpoly, p_f[2 * S + i], fm >> 16, rz);
+    float2 acc = make_float2(0.f, 0.f);
+    const TT* base = tile + off;
+#pragma unroll
+    for (int jz = 0; jz < J; ++jz) {
+      float2 zacc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jy = 0; jy < J; ++jy) {
+        const TT* tp = base + jz * PP + jy * E;
+        float2 row = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jx = 0; jx < J; ++jx) rmac(row, rx[jx], G::to_f2(tp[jx]));
+        rmac(zacc, ry[jy], row);
+      }
+      rmac(acc, rz[jz], zacc);
+    }
+    const float2 res = cmul(cscale(acc, inv_scale), p_ph[i]);
+    out[p_id[i]] = res;
+    if ((uint32_t)p_tw[i] != kNoTwin) out[p_tw[i]] = res;
+  }
+}
+
+template <int J, typename G>
+static cudaError_t launch_gather_v9_t(const InterpGeom& g, const void* grid, const int4* subs, int n_subs,
+                                      float2* out, cudaStream_t st) {
+  auto f = k_gather_v9<J, G>;
+  const size_t smem = v9_bytes(8, J, g.S, (int)sizeof(typename G::T));
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  f<<<n_subs, V9_NT, smem, st>>>(g, (const typename G::T*)grid, subs, g.S, out);
+  return cudaGetLastError();
+}
+
+template <int J>
+static cudaError_t launch_gather_v9_j(const InterpGeom& g, int dtype, const void* grid, const int4* subs, int n_subs,
+                                      float2* out, cudaStream_t st) {
+  switch (dtype) {
+    case 0: return launch_gather_v9_t<J, GridC64>(g, grid, subs, n_subs, out, st);
+    case 1: return launch_gather_v9_t<J, GridBF16>(g, grid, subs, n_subs, out, st);
+    case 2: return launch_gather_v9_t<J, GridF16>(g, grid, subs, n_subs, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+bool v9_supported(int T, int J, int S) {
+  return T == 8 && (J == 2 || J == 4 || J == 6 || J == 8) && S >= 2 && S % 2 == 0 &&
+         v9_bytes(T, J, S, 8) <= (size_t)max_optin_smem();
+}
+
+cudaError_t launch_gather_real(const InterpGeom& g, int grid_dtype, const void* grid, const int4* subs, int n_subs,
+                               float2* out, cudaStream_t st) {
+  if (!v9_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
+  switch (g.J) {
+    case 2: return launch_gather_v9_j<2>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 4: return launch_gather_v9_j<4>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 6: return launch_gather_v9_j<6>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 8: return launch_gather_v9_j<8>(g, grid_dtype, grid, subs, n_subs, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// spread 7
+//  phase 1: thread per point: decode, real weights, v' = e^{-i gamma (ux+uy+uz)/2} v,
+//           the z row folded into v' (v' rho_z), the bound |v| max|rx| max|ry| max|rz|;
+//           the CTA's largest bound fixes the subproblem's exponent;
+//  phase 2: warp w spreads points w, w + 6, ...: lane taps as in spread 6, each
+//           contribution w_xy (v' rho_z) with w_xy = rho_x rho_y real, rounded
+//           to units by one FMA per plane;
+//  flush:   all 192 threads add the tile to the grid and clear it.
+// ---------------------------------------------------------------------------
+constexpr int V7S_WARPS = 6, V7S_THREADS = V7S_WARPS * 32, V7S_MAX_PTS = 256;
+constexpr int V7S_CSTRIDE = 24;  // floats per point: rx[6] ry[6] (v' rz)[6] as float2
+
+struct V7SLayout {
+  static constexpr int E = 13, E3 = E * E * E;
+  static constexpr size_t coef = 0;                                                     // [256][24] float
+  static constexpr size_t mos = coef + (size_t)V7S_MAX_PTS * V7S_CSTRIDE * sizeof(float);  // [256] int
+  static constexpr size_t tre = mos + V7S_MAX_PTS * sizeof(int);                         // [E3] int
+  static constexpr size_t tim = tre + E3 * sizeof(int);                                  // [E3] int
+  static constexpr size_t wmax = tim + E3 * sizeof(int);                                 // [6] unsigned
+  static constexpr size_t nxt = wmax + V7S_WARPS * sizeof(unsigned);                     // [2] int
+  static constexpr size_t bytes = (nxt + 2 * sizeof(int) + 15) / 16 * 16;
+};
+
+__global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, const float2* __restrict__ in,
+                                                             const int4* __restrict__ subs, int n_subs,
+                                                             int* __restrict__ counter,
+                                                             float2* __restrict__ grid, float budget,
+                                                             float inv_budget) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using Lay = V7SLayout;
+  constexpr int T = 8, E = Lay::E, E2 = E * E, E3 = Lay::E3;
+  float* coef = (float*)(smem_raw + Lay::coef);
+  int* mos = (int*)(smem_raw + Lay::mos);
+  int* tre = (int*)(smem_raw + Lay::tre);
+  int* tim = (int*)(smem_raw + Lay::tim);
+  unsigned* wmax = (unsigned*)(smem_raw + Lay::wmax);
+  int* nxt = (int*)(smem_raw + Lay::nxt);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nT = g.nT, K = g.K;
+  const size_t KK = (size_t)K * K;
+  for (int i = tid; i < E3; i += V7S_THREADS) {
+    tre[i] = 0;
+    tim[i] = 0;
+  }
+  const V5Lanes ln = v5_lanes(lane);
+  const int main_off = ln.has_main ? ln.main_off : kPadI13[0];
+  const int ovf_off = ln.has_ovf ? ln.ovf_off : kPadI13[lane == 30 ? 1 : 2];
+  if (tid == 0) nxt[0] = atomicAdd(counter, 1);
+  __syncthreads();
+  int s = nxt[0], parity = 0;
+  while (s < n_subs) {
+    const int4 sp = subs[s];
+    const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    unsigned bound = 0u;
+    for (int i = tid; i < sp.z; i += V7S_THREADS) {
+      const uint2 ent = g.sorted[sp.y + i];
+      int w0[3], fm[3];
+      float f[3];
+      float2 ph;
+      decode_point_real<6>(g, ent.x, w0, f, fm, ph);
+      const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+      float4* c4 = (float4*)(coef + i * V7S_CSTRIDE);
+      int off = 0;
+      if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+        off = (lz * E + ly) * E + lx;
+        float2 val = in[ent.x];
+        if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+        const float2 vp = cmulc(val, ph);  // e^{-i gamma sum u / 2} v
+        float rx[6], ry[6], rz[6];
+        real_coeffs<6>(g.rpoly, f[0], fm[0], rx);
+        real_coeffs<6>(g.rpoly, f[1], fm[1], ry);
+        real_coeffs<6>(g.rpoly, f[2], fm[2], rz);
+        float mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          mx = fmaxf(mx, fabsf(rx[q]));
+          my = fmaxf(my, fabsf(ry[q]));
+          mz = fmaxf(mz, fabsf(rz[q]));
+        }
+        c4[0] = make_float4(rx[0], rx[1], rx[2], rx[3]);
+        c4[1] = make_float4(rx[4], rx[5], ry[0], ry[1]);
+        c4[2] = make_float4(ry[2], ry[3], ry[4], ry[5]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          c4[3 + q] = make_float4(vp.x * rz[2 * q], vp.y * rz[2 * q], vp.x * rz[2 * q + 1], vp.y * rz[2 * q + 1]);
+        bound = max(bound, __float_as_uint(hypotf(val.x, val.y) * (mx * my * mz)));
+      } else {
+        atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) c4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      mos[i] = off;
+    }
+    const unsigned wb = __reduce_max_sync(0xffffffffu, bound);
+    if (lane == 0) wmax[warp] = wb;
+    if (tid == 0) nxt[parity ^ 1] = atomicAdd(counter, 1);
+    __syncthreads();
+    unsigned bb = wmax[0];
+#pragma unroll
+    for (int w = 1; w < V7S_WARPS; ++w) bb = max(bb, wmax[w]);
+    const bool poison = bb > kBoundLimitBits;
+    int e_tile = kTileEmpty;
+    if (!poison && bb != 0u) {
+      e_tile = max((int)(bb >> 23) - 127 + ((bb & 0x7FFFFFu) ? 1 : 0), -100);
+      const float sc = budget * pow2f(-e_tile);
+      const float sm = ln.has_main ? sc : 0.f, so = ln.has_ovf ? sc : 0.f;
+      for (int p = warp; p < sp.z; p += V7S_WARPS) {
+        const int mo = mos[p];
+        const float* cp = coef + p * V7S_CSTRIDE;
+        const float wxy = cp[ln.mjx] * cp[6 + ln.mjy] * sm;
+        const float4 z01 = *(const float4*)(cp + 12), z23 = *(const float4*)(cp + 16),
+                     z45 = *(const float4*)(cp + 20);
+        const float wo = cp[ln.ojx] * cp[6 + ln.ojy] * so;
+        const float2 zo = *(const float2*)(cp + 12 + 2 * ln.ojz);
+        const float zv[12] = {z01.x, z01.y, z01.z, z01.w, z23.x, z23.y, z23.z, z23.w, z45.x, z45.y, z45.z, z45.w};
+        int* re = tre + mo + main_off;
+        int* im = tim + mo + main_off;
+#pragma unroll
+        for (int jz = 0; jz < 6; ++jz) {
+          atomicAdd(re + jz * E2, round_unit1(wxy, zv[2 * jz]));
+          atomicAdd(im + jz * E2, round_unit1(wxy, zv[2 * jz + 1]));
+        }
+        atomicAdd(tre + mo + ovf_off, round_unit1(wo, zo.x));
+        atomicAdd(tim + mo + ovf_off, round_unit1(wo, zo.y));
+      }
+    }
+    __syncthreads();
+    const int s_next = nxt[parity ^ 1];
+    const float inv = e_tile == kTileEmpty ? 0.f : inv_budget * pow2f(e_tile);
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int c = tid; c < E2; c += V7S_THREADS) {
+      const int iy = c / E, ix = c - iy * E;
+      int gx = x0 + ix, gy = y0 + iy;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      float2* col = grid + (size_t)gy * K + gx;
+      int gz = z0;
+#pragma unroll
+      for (int iz = 0; iz < E; ++iz) {
+        const int idx = c + iz * E2;
+        const int a = tre[idx], b = tim[idx];
+        if ((a | b) != 0 || poison) {
+          tre[idx] = 0;
+          tim[idx] = 0;
+          const float2 v = poison ? make_float2(qnan, qnan) : make_float2((float)a * inv, (float)b * inv);
+          atomicAdd(col + (size_t)(gz >= K ? gz - K : gz) * KK, v);
+        }
+        ++gz;
+      }
+    }
+    parity ^= 1;
+    s = s_next;
+  }
+}
+
+bool v7s_supported(int T, int J, int S) {
+  return J == 6 && T == 8 && S >= 1 && S <= V7S_MAX_PTS && V7SLayout::bytes <= (size_t)max_optin_smem();
+}
+
+cudaError_t launch_spread_real(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
+                               cudaStream_t st) {
+  if (!v7s_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
+  auto f = k_spread_v7;
+  const size_t smem = V7SLayout::bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, V7S_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const float budget = ldexpf(1.f - 1.f / 1024.f, 22);  // at most 256 points per subproblem
+  e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  f<<<num_sms() * per_sm, V7S_THREADS, smem, st>>>(g, in, subs, n_subs, g.counter + 1, grid, budget, 1.f / budget);
+  return cudaGetLastError();
+}
+
+}  // namespace nufft

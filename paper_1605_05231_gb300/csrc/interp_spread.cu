@@ -438,42 +438,8 @@ __global__ void __launch_bounds__(V3S_WARPS * 32, 1) k_spread_v3(InterpGeom g, c
 // which is read back from the float's bits.
 // ---------------------------------------------------------------------------
 constexpr int V5S_WARPS = 10;
-constexpr float kRoundMagic = 12582912.0f;            // 1.5 * 2^23
-constexpr int kRoundMagicBits = 0x4B400000;           // its bits
-constexpr int kTileEmpty = -1000;                     // tile exponent before the first point
-constexpr unsigned kBoundLimitBits = (100u + 127u) << 23;  // 2^100: larger bounds (and NaN) poison the tile
-
 // two int32 planes take the bytes of one float2 tile
 __host__ __device__ inline size_t v5s_bytes(int T) { return V5S_WARPS * v3s_warp_bytes(T); }
-
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }  // -126 <= k <= 127
-
-// a b + c d rounded to an integer, for |a b|, |c d|, |a b + c d| < 2^22
-__device__ __forceinline__ int round_units(float a, float b, float c, float d) {
-  return __float_as_int(fmaf(a, b, fmaf(c, d, kRoundMagic))) - kRoundMagicBits;
-}
-
-struct V5Lanes {
-  int main_off, ovf_off;
-  int mjx, mjy, ojx, ojy, ojz;
-  bool has_main, has_ovf;
-};
-
-__device__ __forceinline__ V5Lanes v5_lanes(int lane) {
-  constexpr int E = 13;
-  const unsigned m = kLaneMainI13[lane], o = kLaneOvfI13[lane];
-  V5Lanes r;
-  r.has_main = m != 255u;
-  r.has_ovf = o != 65535u;
-  r.mjx = r.has_main ? (m & 7) : 0;
-  r.mjy = r.has_main ? ((m >> 3) & 7) : 0;
-  r.ojx = r.has_ovf ? (o & 7) : 0;
-  r.ojy = r.has_ovf ? ((o >> 3) & 7) : 0;
-  r.ojz = r.has_ovf ? ((o >> 6) & 7) : 0;
-  r.main_off = r.mjx + E * r.mjy;
-  r.ovf_off = r.ojx + E * r.ojy + E * E * r.ojz;
-  return r;
-}
 
 // divide every cell by 2^d, rounding half up
 __device__ __forceinline__ void v5s_rescale(int* tre, int* tim, int n, int d, int lane) {
@@ -1012,6 +978,7 @@ cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, co
     f<<<num_sms(), V4S_WARPS * 32, smem, st>>>(g, in, subs, n_subs, g.S, g.counter + 1, grid);
     return cudaGetLastError();
   }
+  if (variant == 7) return launch_spread_real(g, in, subs, n_subs, grid, st);
   if (variant == 6 && v6s_supported(g.T, g.J, g.S)) {
     auto f = k_spread_v6;
     const size_t smem = V6SLayout::bytes;

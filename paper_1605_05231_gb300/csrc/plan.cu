@@ -136,6 +136,9 @@ struct HostTables {
   std::vector<float> line_weight;  // D or empty
   nufft::CoefPoly poly{};       // exact-coefficient mode (L = 0)
   double poly_err = 0.0;
+  nufft::RealPoly rpoly{};      // real weights rho_j (L = 0)
+  bool real_ok = false;
+  std::vector<float2> phase;    // K entries e^{-i gamma k_c / 2}
 };
 
 float2 split(double v) {
@@ -150,7 +153,7 @@ float2 split(double v) {
 // exact c on 1025 evenly spaced f; the largest error relative to max |c| is
 // kept for plan_info, and a fit above 1e-7 is refused.
 template <class F>
-int fit_coeff_polys(int J, F&& coeffs_at, HostTables& h) {
+double fit_coeff_polys(int J, F&& coeffs_at, nufft::CoefPoly& out) {
   constexpr int D = nufft::kPolyDeg, n = D + 1;
   std::vector<cd> cv((size_t)n * J);
   for (int i = 0; i < n; ++i) {
@@ -173,13 +176,13 @@ int fit_coeff_polys(int J, F&& coeffs_at, HostTables& h) {
   for (int k = 2; k < n; ++k)
     for (int q = 0; q < n; ++q)
       Tm[(size_t)k * n + q] = (q > 0 ? 2.0 * Tm[(size_t)(k - 1) * n + q - 1] : 0.0) - Tm[(size_t)(k - 2) * n + q];
-  h.poly = nufft::CoefPoly{};
+  out = nufft::CoefPoly{};
   for (int j = 0; j < J; ++j)
     for (int q = 0; q < n; ++q) {
       cd m = 0;
       for (int k = q; k < n; ++k) m += b[(size_t)k * J + j] * Tm[(size_t)k * n + q];
-      h.poly.a[j][0][q] = (float)m.real();
-      h.poly.a[j][1][q] = (float)m.imag();
+      out.a[j][0][q] = (float)m.real();
+      out.a[j][1][q] = (float)m.imag();
     }
   double err = 0.0, cmax = 0.0;
   std::vector<cd> ce(J);
@@ -187,29 +190,30 @@ int fit_coeff_polys(int J, F&& coeffs_at, HostTables& h) {
     const double f = i / 1024.0, t = 2.0 * f - 1.0;
     coeffs_at(f, ce.data());
     for (int j = 0; j < J; ++j) {
-      double re = h.poly.a[j][0][D], im = h.poly.a[j][1][D];
+      double re = out.a[j][0][D], im = out.a[j][1][D];
       for (int q = D - 1; q >= 0; --q) {
-        re = re * t + h.poly.a[j][0][q];
-        im = im * t + h.poly.a[j][1][q];
+        re = re * t + out.a[j][0][q];
+        im = im * t + out.a[j][1][q];
       }
       err = std::max(err, std::abs(cd(re, im) - ce[j]));
       cmax = std::max(cmax, std::abs(ce[j]));
     }
   }
-  h.poly_err = err / cmax;
-  return h.poly_err <= 1e-7 ? NUFFT3D_OK : NUFFT3D_ERR_UNSUPPORTED;
+  return err / cmax;
 }
 
 int build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
   const int N = r.N, K = r.K, J = r.J, L = r.L;
   const double alpha = 2.34 * J;
   const double gam = 2.0 * M_PI / K;
-  // scaling factors s(n) = Psi(0) / Psi(n / K), n = -N/2 .. N/2 - 1 (Eq. 2.11, P)
+  // scaling factors s(n) = Psi(0) / Psi((n + 1/2) / K), n = -N/2 .. N/2 - 1
+  // (Eq. 2.11, P): the Kaiser-Bessel pre-window centred on the middle -1/2 of
+  // the (even) index range, so it is symmetric over the volume
   std::vector<double> s(N);
   const double psi0 = kb_ft(0.0, J, alpha);
   for (int i = 0; i < N; ++i) {
     const int n = i - N / 2;
-    s[i] = psi0 / kb_ft((double)n / K, J, alpha);
+    s[i] = psi0 / kb_ft(((double)n + 0.5) / K, J, alpha);
   }
   h.s.resize(N);
   for (int i = 0; i < N; ++i) h.s[i] = (float)s[i];
@@ -252,8 +256,37 @@ int build_tables(const nufft3d_params* p, const Resolved& r, HostTables& h) {
       for (int a = 0; a < J; ++a) h.table[(size_t)t * J + a] = make_float2((float)c[a].real(), (float)c[a].imag());
     }
   } else {
-    const int rc = fit_coeff_polys(J, coeffs_at, h);
-    if (rc != NUFFT3D_OK) return rc;
+    h.poly_err = fit_coeff_polys(J, coeffs_at, h.poly);
+    if (!(h.poly_err <= 1e-7)) return NUFFT3D_ERR_UNSUPPORTED;
+    // real weights rho_j(f) = c_j(f) e^{-i gam (f + J/2 - j)/2}: real because the
+    // pre-window is symmetric about -1/2; kept only if the imaginary part
+    // vanishes to rounding and the real fit is as close as the complex one
+    double imax = 0.0, cmax = 0.0;
+    for (int i = 0; i <= 256; ++i) {
+      const double f = i / 256.0;
+      coeffs_at(f, c.data());
+      for (int a = 0; a < J; ++a) {
+        const cd rho = c[a] * std::exp(cd(0, -0.5 * gam * (f + 0.5 * J - (a + 1))));
+        imax = std::max(imax, std::fabs(rho.imag()));
+        cmax = std::max(cmax, std::abs(c[a]));
+      }
+    }
+    nufft::CoefPoly rp{};
+    const double rerr = fit_coeff_polys(
+        J,
+        [&](double f, cd* out) {
+          coeffs_at(f, out);
+          for (int a = 0; a < J; ++a) out[a] = cd((out[a] * std::exp(cd(0, -0.5 * gam * (f + 0.5 * J - (a + 1))))).real(), 0.0);
+        },
+        rp);
+    h.real_ok = imax <= 1e-9 * cmax && rerr <= 1e-7;
+    for (int a = 0; a < J; ++a)
+      for (int q = 0; q <= nufft::kPolyDeg; ++q) h.rpoly.a[a][q] = rp.a[a][0][q];
+    h.phase.resize(K);
+    for (int k = 0; k < K; ++k) {
+      const int kc = k < K / 2 ? k : k - K;
+      h.phase[k] = make_float2((float)std::cos(-0.5 * gam * kc), (float)std::sin(-0.5 * gam * kc));
+    }
   }
   auto twiddles = [](int Lt, std::vector<float2>& out) {
     out.resize(Lt);
@@ -374,7 +407,7 @@ void free_plan(nufft3d_plan pl) {
   if (!pl) return;
   void* ptrs[] = {pl->d_dir, pl->d_rad, pl->d_weight, pl->d_line_weight, pl->d_s, pl->d_table, pl->d_twK, pl->d_twM,
                   pl->d_sorted, pl->d_sub, pl->d_grid, pl->d_grid_adj, pl->d_grid_lp, pl->d_bufA, pl->d_bufB,
-                  pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound};
+                  pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound, pl->d_phase};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : pl->ev_fwd) cudaEventDestroy(e);
@@ -400,6 +433,7 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.S = pl->pts_per_sub;
   g.lp_bound = pl->d_lp_bound;
   g.poly = pl->poly;
+  g.rpoly = pl->rpoly;
   g.tmap = pl->tmap_ok ? &pl->tmap_grid : nullptr;
   g.first_wait_polls = pl->first_wait_polls;
   return g;
@@ -492,6 +526,8 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->J = r.J;
   pl->L = r.L;
   pl->poly = h.poly;
+  pl->rpoly = h.rpoly;
+  pl->real_ok = r.L == 0 && h.real_ok;
   {
     // every tap of a point with |u| <= K/2 lies within (J/2) sqrt 3 of it; one
     // more cell covers a rounding of the tap base
@@ -529,6 +565,7 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   CK(upload(&pl->d_rad, h.rad, st));
   CK(upload(&pl->d_weight, h.weight, st));
   CK(upload(&pl->d_line_weight, h.line_weight, st));
+  CK(upload(&pl->d_phase, h.phase, st));
   CK(dalloc(&pl->d_err, 1));
   CK(dalloc(&pl->d_counter, 2));
   CK(cudaMemsetAsync(pl->d_err, 0, sizeof(int), st));
@@ -599,11 +636,13 @@ int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st)
   CK(clk.mark(1));
   const void* grid = pl->d_grid;
   float inv_scale = 1.f;
+  nufft::ColPrune pzf = prune(pl, 2);
+  if (nufft::gather_real(pl->gather_variant)) pzf.phase = pl->d_phase;
   if (pl->grid_dtype == NUFFT3D_GRID_C64) {
-    CK(nufft::launch_col_fwd(K, pl->d_bufB, pl->d_grid, N, K, K, K, KK, K, KK, pl->d_twK, st, prune(pl, 2)));
+    CK(nufft::launch_col_fwd(K, pl->d_bufB, pl->d_grid, N, K, K, K, KK, K, KK, pl->d_twK, st, pzf));
   } else {
     CK(nufft::launch_col_fwd_lp(K, pl->grid_dtype, pl->d_bufB, pl->d_grid_lp, N, K, K, K, KK, K, KK, pl->d_twK,
-                                pl->d_lp_bound, st, prune(pl, 2)));
+                                pl->d_lp_bound, st, pzf));
     grid = pl->d_grid_lp;
   }
   CK(clk.mark(2));
@@ -642,6 +681,7 @@ int adjoint_impl(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st)
   CK(clk.mark(2));
   nufft::ColPrune pz = prune(pl, 2);
   pz.consume = 1;
+  if (nufft::spread_real(pl->spread_variant)) pz.phase = pl->d_phase;
   CK(nufft::launch_col_inv(K, ag, pl->d_bufB, N, K, K, K, KK, K, KK, pl->d_twK, st, pz));
   pl->adj_dirty = false;
   CK(clk.mark(3));
@@ -809,7 +849,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 8 || spread_variant < -1 || spread_variant > 6) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 9 || spread_variant < -1 || spread_variant > 7) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -830,6 +870,8 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   if (sv == 4 && !nufft::v4s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 5 && !nufft::v5s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 6 && !nufft::v6s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
+  if (gv == 9 && (!plan->real_ok || !nufft::v9_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
+  if (sv == 7 && (!plan->real_ok || !nufft::v7s_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
   PLAN_DEVICE(plan);
   int rc = NUFFT3D_OK;
   CK(cudaStreamSynchronize(plan->last_stream));

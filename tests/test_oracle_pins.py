@@ -57,11 +57,45 @@ def test_kb_fourier_transform_matches_quadrature(J):
 
 
 def test_scaling_factors_shape_and_symmetry():
-    s = O.scaling_factors(16, 32, 6)
+    """The pre-window is centred on the middle of the index range: n = -8..7
+    mirrored about -1/2, smallest at the two central indices, where it equals
+    Psi(0) / Psi(1/(2K)) computed by quadrature of the window itself."""
+    N, K, J = 16, 32, 6
+    s = O.scaling_factors(N, K, J)
     assert s.shape == (16,)
-    assert s[8] == pytest.approx(1.0)            # n = 0
-    assert np.allclose(s[1:], s[1:][::-1])       # even in n (n = -7..7 mirrored)
+    assert np.allclose(s, s[::-1], rtol=1e-15)   # s(n) = s(-1 - n)
+    assert s[7] == s[8] == s.min()               # n = -1 and n = 0
+    alpha = O.kb_alpha(J)
+    psi = lambda nu: integrate.quad(
+        lambda t: special.i0(alpha * np.sqrt(max(0.0, 1 - (2 * t / J) ** 2))) * np.cos(2 * np.pi * nu * t),
+        -J / 2, J / 2, limit=200, epsabs=1e-12, epsrel=1e-12)[0]
+    assert s[8] == pytest.approx(psi(0.0) / psi(0.5 / K), rel=1e-9)
+    assert s[0] == pytest.approx(psi(0.0) / psi(7.5 / K), rel=1e-9)   # n = -8
     assert np.all(s >= 1.0)
+    # odd N: the range -7..7 is centred on 0
+    so = O.scaling_factors(15, 32, 6)
+    assert np.allclose(so, so[::-1], rtol=1e-15) and so[7] == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("N,K,J", [(16, 32, 6), (32, 64, 6), (64, 128, 8), (16, 24, 4)])
+def test_minmax_coeffs_are_a_phase_times_real_weights(N, K, J):
+    """With the pre-window symmetric about the middle n_c = -1/2 of an even
+    index range, T = D T~ D^H and r(f) = e^{i gamma (f + J/2 - j)/2} r~(f) with T~,
+    r~ real, so c_j(f) = e^{i gamma (f + J/2 - j)/2} rho_j(f) with rho real: the
+    identity the GPU's real-weight kernels rest on.  A pre-window centred on
+    n = 0 instead breaks it (the imaginary part is then of order 1e-3)."""
+    s = O.scaling_factors(N, K, J)
+    gam = 2 * np.pi / K
+    f = np.random.default_rng(3).uniform(0, 1, 200)
+    c = O.minmax_coeffs_exact(f, N, K, J, s)
+    j = np.arange(1, J + 1)
+    rho = c * np.exp(-1j * gam * (f[:, None] + J / 2 - j[None, :]) / 2)
+    assert np.max(np.abs(rho.imag)) < 1e-10 * np.max(np.abs(c))   # rounding of the J x J solve
+    n = O.centred_index(N)
+    s0 = O.kb_window_ft(0.0, J) / O.kb_window_ft(n / K, J)   # centred on n = 0
+    c0 = O.minmax_coeffs_exact(f, N, K, J, s0)
+    rho0 = c0 * np.exp(-1j * gam * (f[:, None] + J / 2 - j[None, :]) / 2)
+    assert np.max(np.abs(rho0.imag)) > 1e-5 * np.max(np.abs(c0))
 
 
 # --------------------------------------------------------------------------
