@@ -3,14 +3,14 @@ FMAs against 1.5 * 2^23 and reads the integer from the float's bits, and sizes
 its unit so that no cell of a subproblem overflows int32.  These CPU checks
 pin both claims: the FMA rounding is emulated exactly in float64 (a float32
 product is exact in float64, and the sum with the constant spans at most 50
-bits here), and the unit follows the formula in interp_spread.cu."""
+bits here), and the unit follows the formula of the fixed-point spreads."""
 import os
 import re
 
 import numpy as np
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1605_05231_gb300", "csrc",
-                   "interp_spread.cu")
+                   "interp_common.cuh")
 MAGIC = np.float32(12582912.0)   # 1.5 * 2^23
 MAGIC_BITS = 0x4B400000
 
@@ -63,3 +63,19 @@ def test_unit_budget_bounds_cells():
         assert S * worst < 2 ** 31
     # the CTA-shared variant fixes S <= 256 and B = 2^22 (1 - 2^-10)
     assert 256 * (2.0 ** 22 * (1 - 2.0 ** -10) + 3) < 2 ** 31
+
+
+def test_single_product_rounding_is_nearest_integer():
+    """round_unit1 (the real-weight spread): one FMA of a b with 1.5 * 2^23 puts
+    the product in [2^23, 2^24), where floats are spaced by 1, so the result is
+    a b rounded to the nearest integer (ties to even) for |a b| < 2^22."""
+    rng = np.random.default_rng(1)
+    n = 200000
+    lim = 2.0 ** 22 * (1 - 2.0 ** -10)
+    a = rng.uniform(-1, 1, n).astype(np.float32)
+    b = (rng.uniform(-1, 1, n) * lim).astype(np.float32)
+    exact = np.float64(a) * np.float64(b)
+    # FMA: exact product, one rounding of the sum with the magic constant
+    s = (exact + 12582912.0).astype(np.float32)
+    got = s.view(np.int32).astype(np.int64) - 0x4B400000
+    assert np.array_equal(got, np.rint(exact).astype(np.int64))
