@@ -169,14 +169,25 @@ struct NoPostLoad {
   __device__ __forceinline__ void operator()(int, int) const {}
 };
 
+// Optional scaling of the butterflies' inputs (first stage, after the loads,
+// before the first radix-R DFT of inputs j + r L/R) and of their outputs (last
+// stage, after the last DFT, before the stores of outputs j + r L/R).
+struct NoHook {
+  template <int R>
+  __device__ __forceinline__ void first(float2 (&)[R], int, int) const {}
+  template <int R>
+  __device__ __forceinline__ void last(float2 (&)[R], int, int) const {}
+};
+
 // post_load(i, c) runs once for every input row i and column c after the
 // first barrier, when every first-stage load of the CTA has completed (it is
 // called from the last stage, whose rows j + r NS cover each row once; a
 // consumer that clears its input does it there, so that no load waits behind a
 // store to a possibly aliasing address and no load address stays live).
-template <int L, int W, int NT, bool INV, class Load, class Store, class PostLoad = NoPostLoad>
+template <int L, int W, int NT, bool INV, class Load, class Store, class PostLoad = NoPostLoad,
+          class Hook = NoHook>
 __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __restrict__ tw, Load&& load,
-                                        Store&& store, PostLoad&& post_load = PostLoad{}) {
+                                        Store&& store, PostLoad&& post_load = PostLoad{}, Hook&& hook = Hook{}) {
   constexpr int S = fft_num_stages(L);
   static_assert(S >= 2, "reg_fft needs at least two stages");
   {
@@ -200,6 +211,7 @@ __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __
       const int b = threadIdx.x + p * NT;
       if (NBF % NT == 0 || b < NBF) {
         const int c = b % W, j = b / W;
+        hook.template first<R>(v[p], j, c);
         small_dft<R, INV>(v[p]);
 #pragma unroll
         for (int r = 0; r < R; ++r) buf[(j * R + r) * pitch + c] = v[p][r];
@@ -228,6 +240,7 @@ __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __
           v[r] = cmul(v[r], w);
         }
         small_dft<R, INV>(v);
+        hook.template last<R>(v, j, c);
 #pragma unroll
         for (int r = 0; r < R; ++r) store(j + r * NS, c, v[r]);
 #pragma unroll

@@ -144,6 +144,62 @@ __global__ void __launch_bounds__(FFT_NT, ROW_MIN_CTAS) k_row_fwd_real(const flo
 //   CROP_OUT: only the N centred outputs are written (inverse passes)
 // element (i, c) of the input at in[o in_outer + i in_stride + ch W + c]
 // ----------------------------------------------------------------------------
+// e^{-i pi r / R} for the radices of the transforms (compile-time r and R)
+template <int R>
+__device__ __forceinline__ float2 conj_unit_rot(int r) {
+  constexpr float c8 = 0.92387953251128674f, s8 = 0.38268343236508977f, h = 0.70710678118654752f,
+                  t = 0.86602540378443865f;
+  if (R == 2) return r == 0 ? make_float2(1.f, 0.f) : make_float2(0.f, -1.f);
+  if (R == 3) return r == 0 ? make_float2(1.f, 0.f) : r == 1 ? make_float2(0.5f, -t) : make_float2(-0.5f, -t);
+  if (R == 4) {
+    switch (r) {
+      case 0: return make_float2(1.f, 0.f);
+      case 1: return make_float2(h, -h);
+      case 2: return make_float2(0.f, -1.f);
+      default: return make_float2(-h, -h);
+    }
+  }
+  switch (r) {  // R == 8
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(c8, -s8);
+    case 2: return make_float2(h, -h);
+    case 3: return make_float2(s8, -c8);
+    case 4: return make_float2(0.f, -1.f);
+    case 5: return make_float2(-s8, -c8);
+    case 6: return make_float2(-h, -h);
+    default: return make_float2(-c8, -s8);
+  }
+}
+
+// The phase hook of the real-weight z passes: rows j + r L/R of a butterfly
+// carry e^{-i gamma k_c/2} = e^{-i gamma j/2} e^{-i pi r/R} (negated for k >= L/2,
+// where k_c = k - L); applied, times the thread's column factor, to the
+// outputs of the forward pass's last stage and (conjugated) to the inputs of
+// the inverse pass's first stage.
+template <int L, bool INV, bool PHASE>
+struct PhaseHook {
+  const float2* ph;
+  float2 col;
+  template <int R>
+  __device__ __forceinline__ void apply(float2 (&v)[R], int j) const {
+    const float2 f = cmul(__ldg(ph + j), col);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float2 t = cmul(f, conj_unit_rot<R>(r));
+      if (j + r * (L / R) >= L / 2) t = make_float2(-t.x, -t.y);
+      v[r] = INV ? cmulc(v[r], t) : cmul(v[r], t);
+    }
+  }
+  template <int R>
+  __device__ __forceinline__ void first(float2 (&v)[R], int j, int) const {
+    if constexpr (PHASE && INV) apply<R>(v, j);
+  }
+  template <int R>
+  __device__ __forceinline__ void last(float2 (&v)[R], int j, int) const {
+    if constexpr (PHASE && !INV) apply<R>(v, j);
+  }
+};
+
 template <int L, bool INV, bool PAD_IN, bool CROP_OUT, typename OutT, int W, bool PHASE = false>
 __global__ void __launch_bounds__(32 * W, 32 / W) k_col(const float2* __restrict__ in, OutT* __restrict__ out,
                                                 int N, int n_chunks, long long in_outer, long long in_stride,
@@ -195,12 +251,15 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_col(const float2* __restrict
     const int cx = cen(ch * W + c);
     return (long long)cx * cx + cy2 <= pr.r2;
   };
-  // z passes of the real-weight kernels: e^{-i gamma (kx + ky + kz)/2} for the
-  // cell (kz = k, ky = o, kx = ch W + c), from the per-axis table.  A thread
-  // always serves column c = threadIdx.x % W, so its (ky, kx) factor is fixed.
+  // z passes of the real-weight kernels: the cell (kz = k, ky = o, kx = ch W + c)
+  // carries e^{-i gamma (kx + ky + kz)/2} (centred k).  A thread always serves
+  // column c = threadIdx.x % W, so its (ky, kx) factor is fixed; the kz factor
+  // of rows j + r L/R (a butterfly's rows in the first / last stage) is
+  // e^{-i gamma j/2} e^{-i pi r/R}, negated for rows k >= L/2 (k_c = k - L), so
+  // only e^{-i gamma j/2} is looked up, once per butterfly.
   float2 col_ph = make_float2(1.f, 0.f);
   if (PHASE) col_ph = cmul(__ldg(pr.phase + o), __ldg(pr.phase + ch * W + (int)(threadIdx.x % W)));
-  auto cell_phase = [&](int k, int c) -> float2 { return cmul(__ldg(pr.phase + k), col_ph); };
+  const PhaseHook<L, INV, PHASE> hook{pr.phase, col_ph};
   // centred row i of an N-row input or output <-> grid row k of the L-point
   // transform: k = i - N/2 (mod L); rows N/2 <= k < L - N/2 are the padding
   auto load = [&](int k, int c) -> float2 {
@@ -217,11 +276,9 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_col(const float2* __restrict
     } else if (INV && !live(k, c)) {
       return make_float2(0.f, 0.f);  // cells outside the touched ball are zero
     }
-    if constexpr (INV && PHASE) return cmulc(ib[(long long)i * in_stride + c], cell_phase(k, c));
     return ib[(long long)i * in_stride + c];
   };
   auto store = [&](int k, int c, float2 v) {
-    if constexpr (!INV && PHASE) v = cmul(v, cell_phase(k, c));  // the real-weight gather's grid phase
     int i = k;
     if (CROP_OUT) {
       if (k < half) i = k + half;
@@ -244,7 +301,7 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_col(const float2* __restrict
     if (INV && !PAD_IN && pr.consume && row_live(k))
       const_cast<float2*>(ib)[(long long)k * in_stride + c] = make_float2(0.f, 0.f);
   };
-  reg_fft<L, W, 32 * W, INV>(buf, W + 1, tw, load, store, clear_read);
+  reg_fft<L, W, 32 * W, INV>(buf, W + 1, tw, load, store, clear_read, hook);
 }
 
 // ----------------------------------------------------------------------------

@@ -64,8 +64,12 @@ struct InterpGeom {
   const float* lp_bound; // bound on |Y| for a reduced-precision grid (else null)
   CoefPoly poly;         // coefficient polynomials (used when L == 0)
   RealPoly rpoly;        // real weights rho_j (real-weight variants, L == 0)
+  const float2* phase = nullptr;  // K entries e^{-i gamma k_c / 2} (real-weight variants)
   const CUtensorMap* tmap = nullptr;  // host copy of the grid's tensor map (gather variant 8), or null
   int first_wait_polls = -1;          // polls of the first wait on each TMA copy (< 0: the default limit)
+  const int4* sched = nullptr;        // per-subproblem conflict schedules (gather 10, spread 8), or null
+  const uint16_t* gslots = nullptr;
+  const uint16_t* sslots = nullptr;
 };
 
 // Pruning of the column FFT passes to the cells the interpolation touches:
@@ -136,8 +140,16 @@ cudaError_t launch_gather_real(const InterpGeom& g, int grid_dtype, const void* 
 cudaError_t launch_spread_real(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
                                cudaStream_t st);
 // the variants with real weights and phases (they need the phased grid)
-inline bool gather_real(int variant) { return variant == 9; }
-inline bool spread_real(int variant) { return variant == 7; }
+inline bool gather_real(int variant) { return variant == 9 || variant == 10; }
+inline bool spread_real(int variant) { return variant == 7 || variant == 8; }
+bool v10_supported(int T, int J, int S);
+bool v8s_supported(int T, int J, int S);
+cudaError_t launch_gather_sched(const InterpGeom& g, int grid_dtype, const void* grid, const int4* subs, int n_subs,
+                                float2* out, cudaStream_t st);
+cudaError_t launch_spread_sched(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
+                                cudaStream_t st);
+// plane pitches of the scheduled kernels' tiles: E^2 + code, code < 16 (gather) or < 32 (spread)
+constexpr int kGatherPitchCodes = 16, kSpreadPitchCodes = 32;
 
 }  // namespace nufft
 
@@ -192,6 +204,18 @@ struct nufft3d_plan_s {
   std::vector<cudaEvent_t> ev_fwd, ev_adj;  // slots * (FWD_STAGES + 1), slots * (ADJ_STAGES + 1)
   // host copy of the per-bin offsets (for re-tuning the subproblem split)
   std::vector<long long> bin_offsets;
+  std::vector<int> bin_dc;          // per bin: its leading points at the origin (radius 0)
+  std::vector<uint2> h_sorted;      // host copy of d_sorted
+  std::vector<int4> h_sub;          // host copy of d_sub
+  std::vector<float2> h_dir, h_rad; // host copies of d_dir, d_rad
+  // conflict schedules of the thread-per-point real-weight kernels (gather 10,
+  // spread 8), one int4 per subproblem: (gather slot start, gather slots |
+  // plane-pitch code << 16, spread slot start, spread slots | code << 16); the
+  // slots hold the subproblem-local point index or 0xffff (an idle lane)
+  int4* d_sched = nullptr;
+  uint16_t* d_gslots = nullptr;
+  uint16_t* d_sslots = nullptr;
+  bool sched_ok = false;
   cudaStream_t last_stream = nullptr;
   int first_wait_polls = -1;  // testing hook of nufft3d_plan_set_wait_limit (< 0: default)
 };

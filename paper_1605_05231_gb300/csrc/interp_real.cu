@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, cons
     }
     __syncthreads();
     const int s_next = nxt[parity ^ 1];
+    // flush: the tile added to the grid (the inverse z pass applies the grid phase)
     const float inv = e_tile == kTileEmpty ? 0.f : inv_budget * pow2f(e_tile);
     const float qnan = __int_as_float(0x7fc00000);
     for (int c = tid; c < E2; c += V7S_THREADS) {
@@ -355,6 +356,410 @@ cudaError_t launch_spread_real(const InterpGeom& g, const float2* in, const int4
   if (e != cudaSuccess) return e;
   f<<<num_sms() * per_sm, V7S_THREADS, smem, st>>>(g, in, subs, n_subs, g.counter + 1, grid, budget, 1.f / budget);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// gather 10: the real-weight gather with the plan's conflict schedule.  One
+// CTA per subproblem stages the tile with the subproblem's plane pitch; then
+// thread k serves slot k of the schedule (a point of the subproblem, or
+// nothing): decode, weights and taps in registers, no reordering at run time.
+// The 16 slots of a half-warp hold points whose base offsets are distinct
+// modulo 16 cells or equal, so every tap read is one wavefront per half-warp.
+// ---------------------------------------------------------------------------
+constexpr int V10_NT = 128;
+
+template <int J>
+__host__ __device__ inline size_t v10_bytes(int elem) {
+  constexpr int E = 8 + J - 1;
+  return ((size_t)E * (E * E + kGatherPitchCodes - 1) * elem + 15) / 16 * 16;
+}
+
+template <int J, typename G>
+__global__ void __launch_bounds__(V10_NT, 8) k_gather_v10(InterpGeom g, const typename G::T* __restrict__ grid,
+                                                          const int4* __restrict__ subs, float2* __restrict__ out) {
+  typedef typename G::T TT;
+  constexpr int T = 8, NT = V10_NT, E = T + J - 1, E2 = E * E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TT* tile = (TT*)smem_raw;
+  const float inv_scale = lp_inv_scale<G>(g);
+  const int nT = g.nT, K = g.K;
+  const int4 sp = subs[blockIdx.x];
+  const int4 sc = g.sched[blockIdx.x];
+  const int PP = E2 + (sc.y >> 16), nslots = sc.y & 0xffff;
+  const int x0 = (sp.x % nT) * T, y0 = ((sp.x / nT) % nT) * T, z0 = (sp.x / (nT * nT)) * T;
+  for (int r = threadIdx.x; r < E2 * E; r += NT) {
+    const int row = r / E, ix = r - row * E;
+    const int iz = row / E, iy = row - iz * E;
+    int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+    gx -= gx >= K ? K : 0;
+    gy -= gy >= K ? K : 0;
+    gz -= gz >= K ? K : 0;
+    tile[iz * PP + iy * E + ix] = grid[((size_t)gz * K + gy) * K + gx];
+  }
+  __syncthreads();
+  const uint16_t* slots = g.gslots + sc.x;
+  for (int k = threadIdx.x; k < nslots; k += NT) {
+    const int li = slots[k];
+    if (li == 0xffff) continue;
+    const uint2 ent = g.sorted[sp.y + li];
+    int w0[3], fm[3];
+    float f[3];
+    float2 ph;
+    decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+    const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+    if ((unsigned)lx >= (unsigned)T || (unsigned)ly >= (unsigned)T || (unsigned)lz >= (unsigned)T) {
+      atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+      continue;
+    }
+    float rx[J], ry[J], rz[J];
+    real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
+    real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
+    real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
+    float2 acc = make_float2(0.f, 0.f);
+    const TT* base = tile + (lz * PP + ly * E + lx);
+#pragma unroll
+    for (int jz = 0; jz < J; ++jz) {
+      const TT* pz = base + jz * PP;
+      float2 zacc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jy = 0; jy < J; ++jy) {
+        const TT* tp = pz + jy * E;
+        float2 row = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jx = 0; jx < J; ++jx) rmac(row, rx[jx], G::to_f2(tp[jx]));
+        rmac(zacc, ry[jy], row);
+      }
+      rmac(acc, rz[jz], zacc);
+    }
+    const float2 res = cmul(cscale(acc, inv_scale), ph);
+    out[ent.x] = res;
+    if (ent.y != kNoTwin) out[ent.y] = res;
+  }
+}
+
+template <int J, typename G>
+static cudaError_t launch_gather_v10_t(const InterpGeom& g, const void* grid, const int4* subs, int n_subs,
+                                       float2* out, cudaStream_t st) {
+  auto f = k_gather_v10<J, G>;
+  const size_t smem = v10_bytes<J>((int)sizeof(typename G::T));
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  f<<<n_subs, V10_NT, smem, st>>>(g, (const typename G::T*)grid, subs, out);
+  return cudaGetLastError();
+}
+
+template <int J>
+static cudaError_t launch_gather_v10_j(const InterpGeom& g, int dtype, const void* grid, const int4* subs,
+                                       int n_subs, float2* out, cudaStream_t st) {
+  switch (dtype) {
+    case 0: return launch_gather_v10_t<J, GridC64>(g, grid, subs, n_subs, out, st);
+    case 1: return launch_gather_v10_t<J, GridBF16>(g, grid, subs, n_subs, out, st);
+    case 2: return launch_gather_v10_t<J, GridF16>(g, grid, subs, n_subs, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+bool v10_supported(int T, int J, int S) {
+  return T == 8 && (J == 2 || J == 4 || J == 6 || J == 8) && S >= 1 && S <= 256;
+}
+
+cudaError_t launch_gather_sched(const InterpGeom& g, int grid_dtype, const void* grid, const int4* subs, int n_subs,
+                                float2* out, cudaStream_t st) {
+  if (!g.sched || !v10_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
+  switch (g.J) {
+    case 2: return launch_gather_v10_j<2>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 4: return launch_gather_v10_j<4>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 6: return launch_gather_v10_j<6>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 8: return launch_gather_v10_j<8>(g, grid_dtype, grid, subs, n_subs, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// spread 8: the real-weight fixed-point spread, thread per point, with the
+// plan's conflict schedule.  Persistent CTAs of 256 threads take subproblems
+// (at most 256 points) from a work counter:
+//  phase 1: thread i decodes point i, evaluates its real weights, folds
+//           e^{-i gamma (ux+uy+uz)/2} v into the z row and bounds its largest
+//           contribution; the CTA's largest bound fixes the exponent;
+//  phase 2: thread k serves slot k of the schedule: its point's J^3 taps, two
+//           int32 reductions each.  The 32 slots of a warp hold points with
+//           base offsets distinct modulo 32 cells (the tile's plane pitch is
+//           the subproblem's), so each reduction instruction is one
+//           wavefront, and no weight is broadcast;
+//           a subproblem of points at the origin (all alike) sums their
+//           z rows first and spreads the one point;
+//  flush:   the tile added to the grid; the inverse z pass applies the grid
+//           phase e^{+i gamma (kx+ky+kz)/2}.
+// ---------------------------------------------------------------------------
+constexpr int V8S_THREADS = 256, V8S_WARPS = V8S_THREADS / 32, V8S_MAX_PTS = 256;
+
+template <int J>
+struct V8SLayout {
+  static constexpr int E = 8 + J - 1, CS = 4 * J;  // floats per point: rx[J] ry[J] (v' rz)[J] as float2
+  static constexpr int PPMAX = E * E + kSpreadPitchCodes - 1, CELLS = E * PPMAX;
+  static constexpr size_t coef = 0;
+  static constexpr size_t mos = coef + (size_t)V8S_MAX_PTS * CS * sizeof(float);
+  static constexpr size_t tre = mos + V8S_MAX_PTS * sizeof(int);
+  static constexpr size_t tim = tre + (size_t)CELLS * sizeof(int);
+  static constexpr size_t red = tim + (size_t)CELLS * sizeof(int);  // [8 warps][2 J] floats, then [8] unsigned
+  static constexpr size_t nxt = red + (size_t)V8S_WARPS * (2 * J + 1) * sizeof(float);
+  static constexpr size_t bytes = (nxt + 2 * sizeof(int) + 15) / 16 * 16;
+};
+
+template <int J>
+__global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, const float2* __restrict__ in,
+                                                             const int4* __restrict__ subs, int n_subs,
+                                                             int* __restrict__ counter, float2* __restrict__ grid,
+                                                             float budget, float inv_budget) {
+  using Lay = V8SLayout<J>;
+  constexpr int T = 8, E = Lay::E, E2 = E * E, CS = Lay::CS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* coef = (float*)(smem_raw + Lay::coef);
+  int* mos = (int*)(smem_raw + Lay::mos);
+  int* tre = (int*)(smem_raw + Lay::tre);
+  int* tim = (int*)(smem_raw + Lay::tim);
+  float* vred = (float*)(smem_raw + Lay::red);                 // [warps][2 J]
+  unsigned* wred = (unsigned*)(vred + V8S_WARPS * 2 * J);      // [warps]
+  int* nxt = (int*)(smem_raw + Lay::nxt);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nT = g.nT, K = g.K;
+  const size_t KK = (size_t)K * K;
+  for (int i = tid; i < Lay::CELLS; i += V8S_THREADS) {
+    tre[i] = 0;
+    tim[i] = 0;
+  }
+  if (tid == 0) nxt[0] = atomicAdd(counter, 1);
+  __syncthreads();
+  int s = nxt[0], parity = 0;
+  while (s < n_subs) {
+    const int4 sp = subs[s];
+    const int4 sc = g.sched[s];
+    const bool uniform = (sp.w & 1) != 0;
+    const int PP = E2 + (sc.w >> 16), nslots = sc.w & 0xffff;
+    const int x0 = (sp.x % nT) * T, y0 = ((sp.x / nT) % nT) * T, z0 = (sp.x / (nT * nT)) * T;
+    // phase 1 (one point per thread: at most 256 points per subproblem)
+    unsigned bound = 0u;
+    float vz[2 * J];
+#pragma unroll
+    for (int q = 0; q < 2 * J; ++q) vz[q] = 0.f;
+    if (tid < sp.z) {
+      const uint2 ent = g.sorted[sp.y + tid];
+      int w0[3], fm[3];
+      float f[3];
+      float2 ph;
+      decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+      const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+      float* cp = coef + tid * CS;
+      int off = -1;
+      if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+        off = lz * PP + ly * E + lx;
+        float2 val = in[ent.x];
+        if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+        const float2 vp = cmulc(val, ph);  // e^{-i gamma sum u / 2} v
+        float rx[J], ry[J], rz[J];
+        real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
+        real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
+        real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
+        float mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+        for (int q = 0; q < J; ++q) {
+          mx = fmaxf(mx, fabsf(rx[q]));
+          my = fmaxf(my, fabsf(ry[q]));
+          mz = fmaxf(mz, fabsf(rz[q]));
+          vz[2 * q] = vp.x * rz[q];
+          vz[2 * q + 1] = vp.y * rz[q];
+        }
+        float4* c4 = (float4*)cp;
+#pragma unroll
+        for (int q = 0; q < J / 2; ++q) {
+          c4[q] = make_float4(rx[2 * q], rx[2 * q + 1], ry[2 * q], ry[2 * q + 1]);
+          c4[J / 2 + q] = make_float4(vz[4 * q], vz[4 * q + 1], vz[4 * q + 2], vz[4 * q + 3]);
+        }
+        bound = __float_as_uint(hypotf(val.x, val.y) * (mx * my * mz));
+      } else {
+        atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+      }
+      mos[tid] = off;
+    }
+    // the exponent: largest bound, or for points at the origin (summed before
+    // they are spread) the sum of the bounds
+    float bsum = 0.f;
+    unsigned bmax = 0u;
+    if (!uniform) {
+      const unsigned wb = __reduce_max_sync(0xffffffffu, bound);
+      if (lane == 0) wred[warp] = wb;
+    } else {
+      float b = __uint_as_float(bound);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+#pragma unroll
+      for (int q = 0; q < 2 * J; ++q) {
+        float v = vz[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) vred[warp * 2 * J + q] = v;
+      }
+      if (lane == 0) wred[warp] = __float_as_uint(b);
+    }
+    if (tid == 0) nxt[parity ^ 1] = atomicAdd(counter, 1);
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < V8S_WARPS; ++w) {
+      bmax = max(bmax, wred[w]);
+      bsum += __uint_as_float(wred[w]);
+    }
+    const unsigned bb = uniform ? __float_as_uint(bsum) : bmax;
+    const bool poison = bb > kBoundLimitBits;
+    int e_tile = kTileEmpty;
+    if (!poison && bb != 0u) {
+      e_tile = max((int)(bb >> 23) - 127 + ((bb & 0x7FFFFFu) ? 1 : 0), -100);
+      const float scl = budget * pow2f(-e_tile);
+      if (!uniform) {
+        const uint16_t* slots = g.sslots + sc.z;
+        for (int k = tid; k < nslots; k += V8S_THREADS) {
+          const int li = slots[k];
+          if (li == 0xffff) continue;
+          const int mo = mos[li];
+          if (mo < 0) continue;
+          const float4* c4 = (const float4*)(coef + li * CS);
+          float rx[J], ry[J], z[2 * J];
+#pragma unroll
+          for (int q = 0; q < J / 2; ++q) {
+            const float4 a = c4[q], b = c4[J / 2 + q];
+            rx[2 * q] = a.x;
+            rx[2 * q + 1] = a.y;
+            ry[2 * q] = a.z * scl;
+            ry[2 * q + 1] = a.w * scl;
+            z[4 * q] = b.x;
+            z[4 * q + 1] = b.y;
+            z[4 * q + 2] = b.z;
+            z[4 * q + 3] = b.w;
+          }
+          int* re = tre + mo;
+          int* im = tim + mo;
+#pragma unroll
+          for (int jy = 0; jy < J; ++jy) {
+#pragma unroll
+            for (int jx = 0; jx < J; ++jx) {
+              const float w = rx[jx] * ry[jy];
+              int* pr = re + jy * E + jx;
+              int* pi = im + jy * E + jx;
+#pragma unroll
+              for (int jz = 0; jz < J; ++jz) {
+                atomicAdd(pr + jz * PP, round_unit1(w, z[2 * jz]));
+                atomicAdd(pi + jz * PP, round_unit1(w, z[2 * jz + 1]));
+              }
+            }
+          }
+        }
+      } else {
+        // points at the origin: the summed z row, spread by thread per tap
+        float* vs = vred;  // [2 J] totals in the first row
+        __syncthreads();
+        if (tid < 2 * J) {
+          float t = 0.f;
+#pragma unroll
+          for (int w = 0; w < V8S_WARPS; ++w) t += vred[w * 2 * J + tid];
+          vs[V8S_WARPS * 2 * J - 2 * J + tid] = t;  // park the totals in the last row
+        }
+        __syncthreads();
+        const float* tot = vred + V8S_WARPS * 2 * J - 2 * J;
+        const float* c0 = coef;  // every point's weights are alike: take the first valid one
+        int mo = -1, p0 = 0;
+        for (int i = 0; i < sp.z; ++i)
+          if (mos[i] >= 0) {
+            mo = mos[i];
+            p0 = i;
+            break;
+          }
+        if (mo >= 0) {
+          c0 = coef + p0 * CS;
+          for (int t = tid; t < J * J * J; t += V8S_THREADS) {
+            const int jx = t % J, jy = (t / J) % J, jz = t / (J * J);
+            // rx[jx], ry[jy] from the packed row: float4 q holds rx[2q], rx[2q+1], ry[2q], ry[2q+1]
+            const float rxv = c0[4 * (jx / 2) + (jx & 1)], ryv = c0[4 * (jy / 2) + 2 + (jy & 1)];
+            const float w = rxv * ryv * scl;
+            const int o = mo + jz * PP + jy * E + jx;
+            atomicAdd(tre + o, round_unit1(w, tot[2 * jz]));
+            atomicAdd(tim + o, round_unit1(w, tot[2 * jz + 1]));
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int s_next = nxt[parity ^ 1];
+    // flush: the tile added to the grid (the inverse z pass applies the grid phase)
+    const float inv = e_tile == kTileEmpty ? 0.f : inv_budget * pow2f(e_tile);
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int c = tid; c < E2; c += V8S_THREADS) {
+      const int iy = c / E, ix = c - iy * E;
+      int gx = x0 + ix, gy = y0 + iy;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      float2* col = grid + (size_t)gy * K + gx;
+      int gz = z0;
+#pragma unroll
+      for (int iz = 0; iz < E; ++iz) {
+        const int idx = c + iz * PP;
+        const int a = tre[idx], b = tim[idx];
+        if ((a | b) != 0 || poison) {
+          tre[idx] = 0;
+          tim[idx] = 0;
+          const float2 v = poison ? make_float2(qnan, qnan) : make_float2((float)a * inv, (float)b * inv);
+          atomicAdd(col + (size_t)(gz >= K ? gz - K : gz) * KK, v);
+        }
+        ++gz;
+      }
+    }
+    parity ^= 1;
+    s = s_next;
+  }
+}
+
+bool v8s_supported(int T, int J, int S) {
+  if (T != 8 || S < 1 || S > V8S_MAX_PTS) return false;
+  size_t b = 0;
+  switch (J) {
+    case 2: b = V8SLayout<2>::bytes; break;
+    case 4: b = V8SLayout<4>::bytes; break;
+    case 6: b = V8SLayout<6>::bytes; break;
+    case 8: b = V8SLayout<8>::bytes; break;
+    default: return false;
+  }
+  return b <= (size_t)max_optin_smem();
+}
+
+template <int J>
+static cudaError_t launch_spread_v8_j(const InterpGeom& g, const float2* in, const int4* subs, int n_subs,
+                                      float2* grid, cudaStream_t st) {
+  auto f = k_spread_v8<J>;
+  const size_t smem = V8SLayout<J>::bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, V8S_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const float budget = ldexpf(1.f - 1.f / 1024.f, 22);  // at most 256 points per subproblem
+  e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  f<<<num_sms() * per_sm, V8S_THREADS, smem, st>>>(g, in, subs, n_subs, g.counter + 1, grid, budget, 1.f / budget);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spread_sched(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
+                                cudaStream_t st) {
+  if (!g.sched || !v8s_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
+  switch (g.J) {
+    case 2: return launch_spread_v8_j<2>(g, in, subs, n_subs, grid, st);
+    case 4: return launch_spread_v8_j<4>(g, in, subs, n_subs, grid, st);
+    case 6: return launch_spread_v8_j<6>(g, in, subs, n_subs, grid, st);
+    case 8: return launch_spread_v8_j<8>(g, in, subs, n_subs, grid, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace nufft

@@ -979,6 +979,7 @@ cudaError_t launch_spread(const InterpGeom& g, int variant, const float2* in, co
     return cudaGetLastError();
   }
   if (variant == 7) return launch_spread_real(g, in, subs, n_subs, grid, st);
+  if (variant == 8) return launch_spread_sched(g, in, subs, n_subs, grid, st);
   if (variant == 6 && v6s_supported(g.T, g.J, g.S)) {
     auto f = k_spread_v6;
     const size_t smem = V6SLayout::bytes;

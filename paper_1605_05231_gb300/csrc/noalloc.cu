@@ -91,6 +91,10 @@ extern "C" int nufft3d_adjoint_noalloc(nufft3d_plan pl, const void* lines_dev, v
   g.lp_bound = pl->d_lp_bound;
   g.poly = pl->poly;
   g.rpoly = pl->rpoly;
+  g.phase = pl->d_phase;
+  g.sched = pl->sched_ok ? pl->d_sched : nullptr;
+  g.gslots = pl->d_gslots;
+  g.sslots = pl->d_sslots;
 
   const float2* src = (const float2*)lines_dev;
   if (pl->do_line_fft) {
@@ -103,7 +107,7 @@ extern "C" int nufft3d_adjoint_noalloc(nufft3d_plan pl, const void* lines_dev, v
   if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, 2 * sizeof(int), st);
   if (e == cudaSuccess) e = nufft::launch_spread(g, pl->spread_variant, src, pl->d_sub, pl->n_sub, grid, st);
   nufft::ColPrune pz{};
-  if (nufft::spread_real(pl->spread_variant)) pz.phase = pl->d_phase;  // the grid phase of the real-weight spread
+  if (nufft::spread_real(pl->spread_variant)) pz.phase = pl->d_phase;  // the real-weight spread's grid phase
   if (e == cudaSuccess) e = nufft::launch_col_inv(K, grid, bufB, N, K, K, K, KK, K, KK, pl->d_twK, st, pz);
   if (e == cudaSuccess) e = nufft::launch_col_inv(K, bufB, bufA, N, N, K, KK, K, (long long)N * K, K, pl->d_twK, st);
   if (e == cudaSuccess) e = nufft::launch_row_adj(K, bufA, vol_dev, pl->complex_volume, pl->d_s, N, pl->d_twK, st);

@@ -9,6 +9,7 @@
 #include <complex>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -410,6 +411,8 @@ void free_plan(nufft3d_plan pl) {
                   pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound, pl->d_phase};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (void* q : {(void*)pl->d_sched, (void*)pl->d_gslots, (void*)pl->d_sslots})
+    if (q) cudaFree(q);
   for (cudaEvent_t e : pl->ev_fwd) cudaEventDestroy(e);
   for (cudaEvent_t e : pl->ev_adj) cudaEventDestroy(e);
   delete pl;
@@ -434,24 +437,242 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.lp_bound = pl->d_lp_bound;
   g.poly = pl->poly;
   g.rpoly = pl->rpoly;
+  g.phase = pl->d_phase;
+  g.sched = pl->sched_ok ? pl->d_sched : nullptr;
+  g.gslots = pl->d_gslots;
+  g.sslots = pl->d_sslots;
   g.tmap = pl->tmap_ok ? &pl->tmap_grid : nullptr;
   g.first_wait_polls = pl->first_wait_polls;
   return g;
+}
+
+// ---------------------------------------------------------------------------
+// Conflict schedules of the thread-per-point real-weight kernels (gather 10,
+// spread 8).  The points are fixed at plan time, so the plan decides, per
+// subproblem, the plane pitch of the shared-memory tile and which points run
+// side by side in a half-warp (gather: 16 lanes, 8-byte cells) or a warp
+// (spread: 32 lanes, 4-byte cells):
+//  * gather: lanes of a half-warp read the same tap of their points, one
+//    wavefront if the base offsets are distinct modulo 16 (cells) or equal
+//    (broadcast).  A group takes at most one distinct offset per residue class
+//    (all its points at that offset); the pitch minimises the lower bound
+//    max(ceil(n / 16), most distinct offsets in a class) on the groups.
+//  * spread: lanes of a warp add to the same tap of their points, one
+//    wavefront if the offsets are distinct modulo 32 (equal offsets collide),
+//    so a group holds at most one point per class: G = max(ceil(n / 32), the
+//    largest class) groups, classes dealt cyclically; the pitch minimises G.
+// The local first tap is recomputed here in FP64; should it differ from the
+// device's by a rounding near an integer, only the quality of the schedule
+// suffers, never the result (the kernels compute every offset themselves).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SchedOut {
+  std::vector<int4> sched;
+  std::vector<uint16_t> g, s;
+};
+
+void schedule_range(const nufft3d_plan pl, size_t s0, size_t s1, SchedOut& out) {
+  const int T = pl->T, J = pl->J, K = pl->K, E = T + J - 1, nT = pl->nT;
+  const uint32_t M = (uint32_t)pl->M;
+  std::vector<int> lx, ly, lz, off, order;
+  std::vector<int> cls_n(32), cls_first(32), cls_cur(32);
+  // one stamp per candidate marks the offsets seen (offsets < E * (E^2 + 32))
+  std::vector<unsigned> stamp((size_t)E * (E * E + nufft::kSpreadPitchCodes), 0u);
+  unsigned stamp_id = 0;
+  for (size_t si = s0; si < s1; ++si) {
+    const int4 sp = pl->h_sub[si];
+    const int n = sp.z;
+    const int ox = (sp.x % nT) * T, oy = ((sp.x / nT) % nT) * T, oz = (sp.x / (nT * nT)) * T;
+    lx.resize(n);
+    ly.resize(n);
+    lz.resize(n);
+    for (int i = 0; i < n; ++i) {
+      const uint32_t id = pl->h_sorted[(size_t)sp.y + i].x;
+      const uint32_t l = id / M, m = id - l * M;
+      const double r = (double)pl->h_rad[m].x + (double)pl->h_rad[m].y;
+      int* dst[3] = {&lx[i], &ly[i], &lz[i]};
+      const int org[3] = {ox, oy, oz};
+      for (int a = 0; a < 3; ++a) {
+        const double d = (double)pl->h_dir[(size_t)l * 3 + a].x + (double)pl->h_dir[(size_t)l * 3 + a].y;
+        long long f = (long long)std::floor(r * d) - J / 2 + 1;
+        f %= K;
+        if (f < 0) f += K;
+        long long loc = f - org[a];
+        if (loc < 0) loc += K;
+        *dst[a] = (int)std::min<long long>(std::max<long long>(loc, 0), T - 1);
+      }
+    }
+    int4 sc = make_int4((int)out.g.size(), 0, (int)out.s.size(), 0);
+    off.resize(n);
+    order.resize(n);
+    // gather: pitch by the lower bound, then greedy groups
+    {
+      int best = 0, best_lb = 1 << 30;
+      for (int code = 0; code < nufft::kGatherPitchCodes; ++code) {
+        const int PP = E * E + code;
+        ++stamp_id;
+        std::fill(cls_n.begin(), cls_n.begin() + 16, 0);
+        for (int i = 0; i < n; ++i) {
+          const int o = lx[i] + E * ly[i] + PP * lz[i];
+          if (stamp[o] != stamp_id) {  // a distinct offset of its class
+            stamp[o] = stamp_id;
+            cls_n[o & 15]++;
+          }
+        }
+        int lb = (n + 15) / 16;
+        for (int c = 0; c < 16; ++c) lb = std::max(lb, cls_n[c]);
+        if (lb < best_lb) {
+          best_lb = lb;
+          best = code;
+        }
+      }
+      const int PP = E * E + best;
+      for (int i = 0; i < n; ++i) off[i] = lx[i] + E * ly[i] + PP * lz[i];
+      for (int i = 0; i < n; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const int ca = off[a] & 15, cb = off[b] & 15;
+        return ca != cb ? ca < cb : off[a] < off[b];
+      });
+      // per class: [first, first + n) in `order`, cursor
+      std::fill(cls_n.begin(), cls_n.begin() + 16, 0);
+      for (int k = 0; k < n; ++k) cls_n[off[order[k]] & 15]++;
+      int acc = 0;
+      for (int c = 0; c < 16; ++c) {
+        cls_first[c] = acc;
+        cls_cur[c] = acc;
+        acc += cls_n[c];
+      }
+      int left = n, slots = 0;
+      std::vector<int> cls_idx(16);
+      while (left > 0) {
+        // classes by remaining points, largest first
+        for (int c = 0; c < 16; ++c) cls_idx[c] = c;
+        std::sort(cls_idx.begin(), cls_idx.end(), [&](int a, int b) {
+          const int ra = cls_first[a] + cls_n[a] - cls_cur[a], rb = cls_first[b] + cls_n[b] - cls_cur[b];
+          return ra != rb ? ra > rb : a < b;
+        });
+        int room = 16;
+        for (int q = 0; q < 16 && room > 0; ++q) {
+          const int c = cls_idx[q];
+          const int end = cls_first[c] + cls_n[c];
+          if (cls_cur[c] >= end) continue;
+          const int o = off[order[cls_cur[c]]];
+          while (room > 0 && cls_cur[c] < end && off[order[cls_cur[c]]] == o) {
+            out.g.push_back((uint16_t)order[cls_cur[c]++]);
+            --room;
+            --left;
+          }
+        }
+        for (; room > 0; --room) out.g.push_back(0xffff);
+        slots += 16;
+      }
+      sc.y = slots | (best << 16);
+    }
+    // spread (not for the points at the origin, which the kernel sums first)
+    if (!(sp.w & 1)) {
+      int best = 0, best_g = 1 << 30;
+      for (int code = 0; code < nufft::kSpreadPitchCodes; ++code) {
+        const int PP = E * E + code;
+        std::fill(cls_n.begin(), cls_n.end(), 0);
+        for (int i = 0; i < n; ++i) cls_n[(lx[i] + E * ly[i] + PP * lz[i]) & 31]++;
+        int G = (n + 31) / 32;
+        for (int c = 0; c < 32; ++c) G = std::max(G, cls_n[c]);
+        if (G < best_g) {
+          best_g = G;
+          best = code;
+        }
+      }
+      const int PP = E * E + best, G = best_g;
+      for (int i = 0; i < n; ++i) off[i] = (lx[i] + E * ly[i] + PP * lz[i]) & 31;
+      for (int i = 0; i < n; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return off[a] < off[b]; });
+      std::fill(cls_n.begin(), cls_n.end(), 0);
+      for (int i = 0; i < n; ++i) cls_n[off[i]]++;
+      // classes largest first, dealt cyclically over the G groups
+      std::vector<int> cidx(32);
+      for (int c = 0; c < 32; ++c) cidx[c] = c;
+      std::stable_sort(cidx.begin(), cidx.end(), [&](int a, int b) { return cls_n[a] > cls_n[b]; });
+      int acc = 0;
+      for (int c = 0; c < 32; ++c) {
+        cls_first[c] = acc;
+        acc += cls_n[c];
+      }
+      std::vector<int> fill((size_t)G, 0);
+      const size_t base = out.s.size();
+      out.s.resize(base + (size_t)G * 32, 0xffff);
+      int cur = 0;
+      for (int q = 0; q < 32; ++q) {
+        const int c = cidx[q];
+        for (int k = 0; k < cls_n[c]; ++k) {
+          out.s[base + (size_t)cur * 32 + fill[cur]] = (uint16_t)order[cls_first[c] + k];
+          fill[cur]++;
+          cur = cur + 1 == G ? 0 : cur + 1;
+        }
+      }
+      sc.w = (G * 32) | (best << 16);
+    }
+    out.sched.push_back(sc);
+  }
+}
+
+}  // namespace
+
+int build_schedules(nufft3d_plan pl, cudaStream_t st) {
+  for (void** q : {(void**)&pl->d_sched, (void**)&pl->d_gslots, (void**)&pl->d_sslots})
+    if (*q) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
+  pl->sched_ok = false;
+  if (!pl->real_ok || pl->T != 8 || pl->pts_per_sub > 256 || pl->h_sub.empty()) return NUFFT3D_OK;
+  const size_t ns = pl->h_sub.size();
+  unsigned nth = std::thread::hardware_concurrency();
+  nth = std::max(1u, std::min(nth, 32u));
+  if (ns < 4096) nth = 1;
+  std::vector<SchedOut> parts(nth);
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nth; ++t) {
+    const size_t a = ns * t / nth, b = ns * (t + 1) / nth;
+    if (nth == 1) schedule_range(pl, a, b, parts[t]);
+    else th.emplace_back([&, a, b, t] { schedule_range(pl, a, b, parts[t]); });
+  }
+  for (auto& x : th) x.join();
+  std::vector<int4> sched;
+  std::vector<uint16_t> gs, ss;
+  sched.reserve(ns);
+  for (auto& pt : parts) {
+    const int gb = (int)gs.size(), sb = (int)ss.size();
+    for (int4 v : pt.sched) sched.push_back(make_int4(v.x + gb, v.y, v.z + sb, v.w));
+    gs.insert(gs.end(), pt.g.begin(), pt.g.end());
+    ss.insert(ss.end(), pt.s.begin(), pt.s.end());
+  }
+  if (gs.size() > 0x7fffffffull || ss.size() > 0x7fffffffull) return NUFFT3D_OK;  // no schedule: variants 10 / 8 refuse
+  if (ss.empty()) ss.push_back(0xffff);
+  CK(upload(&pl->d_sched, sched, st));
+  CK(upload(&pl->d_gslots, gs, st));
+  CK(upload(&pl->d_sslots, ss, st));
+  CK(cudaStreamSynchronize(st));
+  pl->sched_ok = true;
+  return NUFFT3D_OK;
 }
 
 int build_subproblems(nufft3d_plan pl, int S, cudaStream_t st) {
   // subproblems of tiles holding more than S points (the dense centre of the
   // radial pattern) come first, so the persistent kernels finish balanced;
   // the rest follow in tile order (neighbouring tiles share halo cells in L2)
+  // the points at the origin of a bin (all alike) form subproblems of their
+  // own, flagged in .w bit 0
   std::vector<int4> heavy, light;
   const size_t nb = pl->bin_offsets.size() - 1;
   for (size_t b = 0; b < nb; ++b) {
     const long long a = pl->bin_offsets[b], e = pl->bin_offsets[b + 1];
+    const long long mid = a + (b < pl->bin_dc.size() ? pl->bin_dc[b] : 0);
     std::vector<int4>& dst = (e - a > S) ? heavy : light;
-    for (long long s0 = a; s0 < e; s0 += S) {
-      const int cnt = (int)std::min<long long>(S, e - s0);
-      dst.push_back(make_int4((int)b, (int)s0, cnt, 0));
-    }
+    for (long long s0 = a; s0 < mid; s0 += S)
+      dst.push_back(make_int4((int)b, (int)s0, (int)std::min<long long>(S, mid - s0), 1));
+    for (long long s0 = mid; s0 < e; s0 += S)
+      dst.push_back(make_int4((int)b, (int)s0, (int)std::min<long long>(S, e - s0), 0));
   }
   std::vector<int4> subs(heavy);
   subs.insert(subs.end(), light.begin(), light.end());
@@ -462,8 +683,9 @@ int build_subproblems(nufft3d_plan pl, int S, cudaStream_t st) {
   pl->n_sub = (int)subs.size();
   CK(upload(&pl->d_sub, subs, st));
   CK(cudaStreamSynchronize(st));
+  pl->h_sub.swap(subs);
   pl->pts_per_sub = S;
-  return NUFFT3D_OK;
+  return build_schedules(pl, st);
 }
 
 int sort_points(nufft3d_plan pl, cudaStream_t st) {
@@ -502,9 +724,21 @@ int sort_points(nufft3d_plan pl, cudaStream_t st) {
     std::vector<long long> pos(off.begin(), off.end() - 1);
     for (long long i = 0; i < P; ++i) sorted[pos[bins[i]]++] = make_uint2(pl->h_unique[i], pl->h_twin[i]);
   }
+  // within a bin, the points at the origin (radius 0: identical coordinates on
+  // every line) come first; the subproblems keep them apart from the others
+  pl->bin_dc.assign(nb, 0);
+  for (size_t b = 0; b < nb; ++b) {
+    auto at_origin = [&](const uint2& v) {
+      const float2 r = pl->h_rad[v.x % (uint32_t)pl->M];
+      return r.x == 0.f && r.y == 0.f;
+    };
+    auto it = std::stable_partition(sorted.begin() + off[b], sorted.begin() + off[b + 1], at_origin);
+    pl->bin_dc[b] = (int)(it - (sorted.begin() + off[b]));
+  }
   pl->bin_offsets.swap(off);
   CK(upload(&pl->d_sorted, sorted, st));
   CK(cudaStreamSynchronize(st));
+  pl->h_sorted.swap(sorted);
   return NUFFT3D_OK;
 }
 
@@ -545,6 +779,8 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   pl->nT = r.nT;
   pl->h_unique.swap(ids);
   pl->h_twin.swap(twin);
+  pl->h_dir = h.dir;
+  pl->h_rad = h.rad;
   pl->P_eval = (long long)pl->h_unique.size();
   pl->n_pairs = n_pairs;
   // defaults measured at 256^3: with the table, 256-thread gather CTAs, 512
@@ -574,6 +810,10 @@ int plan_create_impl(nufft3d_plan* out, const nufft3d_params* p, cudaStream_t st
   if (rc != NUFFT3D_OK) return rc;
   rc = build_subproblems(pl, S0, st);
   if (rc != NUFFT3D_OK) return rc;
+  // with exact coefficients the real-weight kernels are the defaults: the
+  // scheduled gather (10) and the warp-cooperative fixed-point spread (7)
+  if (pl->real_ok && pl->sched_ok && nufft::v10_supported(r.T, r.J, S0)) pl->gather_variant = 10;
+  if (pl->real_ok && nufft::v7s_supported(r.T, r.J, S0)) pl->spread_variant = 7;
   const size_t K3 = (size_t)r.K * r.K * r.K;
   CK(dalloc(&pl->d_grid, K3));
   if (r.grid_dtype == NUFFT3D_GRID_C64) {
@@ -849,7 +1089,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 9 || spread_variant < -1 || spread_variant > 7) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 10 || spread_variant < -1 || spread_variant > 8) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -872,6 +1112,9 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   if (sv == 6 && !nufft::v6s_supported(T, plan->J, S_new)) return NUFFT3D_ERR_UNSUPPORTED;
   if (gv == 9 && (!plan->real_ok || !nufft::v9_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 7 && (!plan->real_ok || !nufft::v7s_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
+  // the scheduled variants: real weights, T = 8, at most 256 points per subproblem
+  if (gv == 10 && (!plan->real_ok || !nufft::v10_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
+  if (sv == 8 && (!plan->real_ok || !nufft::v8s_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
   PLAN_DEVICE(plan);
   int rc = NUFFT3D_OK;
   CK(cudaStreamSynchronize(plan->last_stream));
@@ -890,6 +1133,12 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
     rc = build_subproblems(plan, S, (cudaStream_t)cuda_stream);
   } else if (S != plan->pts_per_sub) {
     rc = build_subproblems(plan, S, (cudaStream_t)cuda_stream);
+  }
+  if (rc == NUFFT3D_OK && (gv == 10 || sv == 8) && !plan->sched_ok) {
+    // no schedule could be built for this split: keep runnable variants
+    if (gv == 10) plan->gather_variant = nufft::v9_supported(plan->T, plan->J, plan->pts_per_sub) ? 9 : 0;
+    if (sv == 8) plan->spread_variant = 0;
+    return NUFFT3D_ERR_UNSUPPORTED;
   }
   return rc;
 }

@@ -50,7 +50,8 @@ def test_tiny_workload_exact_coefficients(cuda_lib):
     info = plan.info()
     assert info["exact_coeffs"] == 1
     assert 0.0 < info["coeff_fit_error"] < 1e-7, info["coeff_fit_error"]
-    assert info["spread_variant"] == 6 and info["points_per_subproblem"] == 256  # the exact-mode defaults
+    # the exact-mode defaults: scheduled real-weight gather, real-weight fixed-point spread
+    assert info["gather_variant"] == 10 and info["spread_variant"] == 7 and info["points_per_subproblem"] == 256
     p, a = _fwd_adj(plan, x, y)
     op = _oplan(w.n, dirs, w.m, w.k, w.j)
     ef = O.rel_l2(p, O.nufft_forward(x.astype(np.float64), op))

@@ -45,7 +45,8 @@ def _face_dirs(n_rand, seed):
     return np.concatenate([I.axis_directions(), -I.axis_directions(), near, I.random_directions(n_rand, seed)])
 
 
-@pytest.mark.parametrize("gv,sv", [(9, 7), (9, 6), (5, 7), (9, 3), (8, 7), (9, 0)])
+@pytest.mark.parametrize("gv,sv", [(9, 7), (9, 6), (5, 7), (9, 3), (8, 7), (9, 0), (10, 8), (10, 7), (9, 8), (5, 8),
+                                   (10, 3)])
 def test_real_variants_umbrella(cuda_lib, gv, sv):
     n = 32
     dirs = I.umbrella_directions(35, 20)
@@ -72,12 +73,15 @@ def test_real_variants_umbrella(cuda_lib, gv, sv):
     (16, 32, 32, 8, 128),     # J = 8
     (20, 64, 48, 2, 256),     # J = 2, M != K
 ])
-def test_real_variants_faces_shapes_and_taps(cuda_lib, n, k, m, j, pps):
+@pytest.mark.parametrize("sched", [False, True], ids=["rank", "sched"])
+def test_real_variants_faces_shapes_and_taps(cuda_lib, n, k, m, j, pps, sched):
+    """gather 9 / spread 7 (or 0), and the scheduled gather 10 / spread 8 (any J)."""
     dirs = _face_dirs(40, n + k)
     x = I.random_volume(n, 1).astype(np.float32)
     y = I.random_lines(dirs.shape[0], m, 2).astype(np.complex64)
     plan = _plan(cuda_lib, n, dirs, m, k, j)
-    plan.tune(9, 7 if j == 6 else 0, pps, 8)
+    gv, sv = (10, 8) if sched else (9, 7 if j == 6 else 0)
+    plan.tune(gv, sv, pps, 8)
     p, a = _run(plan, x, y)
     op = _oplan(n, dirs, m, k, j)
     ef = O.rel_l2(p, O.nufft_forward(x.astype(np.float64), op))
@@ -88,7 +92,7 @@ def test_real_variants_faces_shapes_and_taps(cuda_lib, n, k, m, j, pps):
 
     pr = O.nufft_forward(x.astype(np.float64), op, return_samples=True)
     plan_raw = _plan(cuda_lib, n, dirs, m, k, j, do_line_fft=False)
-    plan_raw.tune(9, 7 if j == 6 else 0, pps, 8)
+    plan_raw.tune(gv, sv, pps, 8)
     raw = plan_raw.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     assert np.max(np.abs(raw[:18, 0] - pr[:18, 0])) < TOL * np.max(np.abs(pr)), "face samples"
 
@@ -100,9 +104,10 @@ def test_real_variants_complex_volume_weights_raw_samples(cuda_lib):
     w = (rng.normal(size=2 * n) + 1j * rng.normal(size=2 * n)).astype(np.complex64)
     x = I.random_volume(n, 3, complex_values=True).astype(np.complex64)
     y = I.random_lines(dirs.shape[0], 2 * n, 4).astype(np.complex64)
-    for kw in (dict(weight=w), dict(do_line_fft=False)):
+    for kw, (gv, sv) in ((dict(weight=w), (9, 7)), (dict(do_line_fft=False), (9, 7)), (dict(weight=w), (10, 8)),
+                         (dict(do_line_fft=False), (10, 8))):
         plan = _plan(cuda_lib, n, dirs, complex_volume=True, **kw)
-        plan.tune(9, 7, 256, 8)
+        plan.tune(gv, sv, 256, 8)
         p, a = _run(plan, x, y)
         okw = dict(kw)
         if "weight" in okw:
@@ -113,14 +118,15 @@ def test_real_variants_complex_volume_weights_raw_samples(cuda_lib):
 
 
 @pytest.mark.parametrize("dtype,bound", [("bf16", 1e-3), ("fp16", 1e-4)])
-def test_real_gather_reduced_precision_grid(cuda_lib, dtype, bound):
+@pytest.mark.parametrize("gv,sv", [(9, 7), (10, 8)])
+def test_real_gather_reduced_precision_grid(cuda_lib, dtype, bound, gv, sv):
     """The phase is applied before the grid is rounded to bf16 / fp16."""
     w = I.workload("tiny32")
     dirs = w.directions()
     x = w.volume(np.float32)
     y = I.random_lines(dirs.shape[0], w.m, 3).astype(np.complex64)
     plan = _plan(cuda_lib, w.n, dirs, w.m, w.k, grid_dtype=dtype)
-    plan.tune(9, 7, 256, 8)
+    plan.tune(gv, sv, 256, 8)
     p, a = _run(plan, x, y)
     op = _oplan(w.n, dirs, w.m, w.k)
     ef = O.rel_l2(p, O.nufft_forward(x.astype(np.float64), op))
@@ -131,7 +137,7 @@ def test_real_gather_reduced_precision_grid(cuda_lib, dtype, bound):
 
 def test_real_variants_refused_with_a_table(cuda_lib):
     plan = cuda_lib.Plan(32, I.random_directions(10, 1))
-    for gv, sv in ((9, -1), (-1, 7)):
+    for gv, sv in ((9, -1), (-1, 7), (10, -1), (-1, 8)):
         with pytest.raises(cuda_lib.NufftError) as ei:
             plan.tune(gv, sv, 256, 8)
         assert ei.value.status == -4
@@ -147,10 +153,47 @@ def test_switching_between_real_and_complex_variants(cuda_lib):
     y = torch.from_numpy(I.random_lines(dirs.shape[0], 2 * n, 6).astype(np.complex64)).cuda()
     plan = _plan(cuda_lib, n, dirs)
     res = []
-    for gv, sv in ((5, 6), (9, 7), (5, 6), (9, 7)):
+    for gv, sv in ((5, 6), (9, 7), (5, 6), (10, 8), (9, 7), (10, 8)):
         plan.tune(gv, sv, 256, 8)
         res.append((plan.forward(x).clone(), plan.adjoint(y).clone()))
     assert plan.sync_status() == 0
     for p, a in res[1:]:
         assert float(torch.linalg.norm(p - res[0][0]) / torch.linalg.norm(res[0][0])) < 1e-5
         assert float(torch.linalg.norm(a - res[0][1]) / torch.linalg.norm(res[0][1])) < 1e-5
+
+
+def test_scheduled_variants_refuse_large_subproblems(cuda_lib):
+    """The schedules exist for subproblems of at most 256 points."""
+    plan = _plan(cuda_lib, 32, I.umbrella_directions(20, 10))
+    for gv, sv in ((10, -1), (-1, 8)):
+        with pytest.raises(cuda_lib.NufftError) as ei:
+            plan.tune(gv, sv, 512, 8)
+        assert ei.value.status == -4
+
+
+def test_scheduled_variants_mid_workload_sampled(cuda_lib):
+    """128^3 (K = 256, 180 x 128 lines of 256 samples): the scheduled pair on a
+    sample of lines forward, and the adjoint of a 48-line support element by
+    element, against the oracle; the dense centre (many subproblems per tile,
+    the 23,040 points at the origin) is exercised."""
+    import torch
+
+    w = I.workload("mid128")
+    dirs = w.directions()
+    x = w.volume(np.float32)
+    plan = _plan(cuda_lib, w.n, dirs, w.m, w.k)
+    plan.tune(10, 8, 256, 8)
+    p = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    sel = np.sort(np.random.default_rng(5).choice(dirs.shape[0], 48, replace=False))
+    op = _oplan(w.n, dirs, w.m, w.k)
+    assert O.rel_l2(p[sel], O.nufft_forward(x.astype(np.float64), op, lines=sel)) < TOL
+    ys = I.random_lines(sel.size, w.m, 6).astype(np.complex64)
+    y = np.zeros((dirs.shape[0], w.m), dtype=np.complex64)
+    y[sel] = ys
+    # the lines through the origin carry their q = 0 samples into the subproblems of points at the origin
+    a = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    ref = O.nufft_adjoint(ys.astype(np.complex128), _oplan(w.n, dirs[sel], w.m, w.k))
+    err = O.rel_l2(a, ref)
+    print(f"128^3 scheduled spread, 48-line support: adjoint rel-L2 {err:.2e}")
+    assert err < TOL

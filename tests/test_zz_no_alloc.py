@@ -33,14 +33,15 @@ def _noalloc(lib, plan, lines, out):
 @pytest.mark.parametrize("exact", [False, True], ids=["table", "exact"])
 def test_noalloc_adjoint_matches_adjoint_twice(cuda_lib, exact):
     """Both coefficient modes: the table with its default spread (FP32 tiles)
-    and the exact coefficients with theirs (fixed-point tiles shared by a CTA)."""
+    and the exact coefficients with theirs (real weights, fixed-point tiles
+    shared by a CTA, the grid phase applied as the tile is added to the grid)."""
     import torch
 
     lib = cuda_lib.load_library()
     w = I.workload("tiny32")
     dirs = w.directions()
     plan = cuda_lib.Plan(w.n, dirs, m=w.m, k=w.k, j=w.j, table_oversamp=w.table_oversamp, exact_coeffs=exact)
-    assert plan.info()["spread_variant"] == (6 if exact else 3)
+    assert plan.info()["spread_variant"] == (7 if exact else 3)
     for seed in (21, 22):
         y = torch.from_numpy(I.random_lines(dirs.shape[0], w.m, seed).astype(np.complex64)).cuda()
         ref = plan.adjoint(y).clone()
