@@ -478,50 +478,85 @@ cudaError_t launch_gather_sched(const InterpGeom& g, int grid_dtype, const void*
 
 // ---------------------------------------------------------------------------
 // spread 8: the real-weight fixed-point spread, thread per point, with the
-// plan's conflict schedule.  Persistent CTAs of 256 threads take subproblems
+// plan's conflict schedule.  Persistent CTAs of 128 threads take subproblems
 // (at most 256 points) from a work counter:
-//  phase 1: thread i decodes point i, evaluates its real weights, folds
-//           e^{-i gamma (ux+uy+uz)/2} v into the z row and bounds its largest
-//           contribution; the CTA's largest bound fixes the exponent;
-//  phase 2: thread k serves slot k of the schedule: its point's J^3 taps, two
-//           int32 reductions each.  The 32 slots of a warp hold points with
-//           base offsets distinct modulo 32 cells (the tile's plane pitch is
-//           the subproblem's), so each reduction instruction is one
-//           wavefront, and no weight is broadcast;
+//  phase 1: the CTA's exponent from the largest |v| B_p over its points, B_p
+//           = max|rho_x| max|rho_y| max|rho_z| of point p, kept by the plan
+//           (k_point_bounds, the kernels' own arithmetic);
+//  phase 2: thread k serves slot k of the schedule: it decodes its point,
+//           evaluates the real weights and folds e^{-i gamma (ux+uy+uz)/2} v
+//           into the z row in registers, then adds its J^3 taps, two int32
+//           reductions each.  The 32 slots of a warp hold points with base
+//           offsets distinct modulo 32 cells (the tile's plane pitch is the
+//           subproblem's), so every reduction instruction is one wavefront,
+//           and nothing is broadcast through shared memory;
 //           a subproblem of points at the origin (all alike) sums their
-//           z rows first and spreads the one point;
+//           values first and spreads the one point, thread per tap;
 //  flush:   the tile added to the grid; the inverse z pass applies the grid
 //           phase e^{+i gamma (kx+ky+kz)/2}.
+// With only the tile in shared memory, several CTAs share an SM, so one
+// waiting at a barrier leaves the SM to the others.
 // ---------------------------------------------------------------------------
-constexpr int V8S_THREADS = 256, V8S_WARPS = V8S_THREADS / 32, V8S_MAX_PTS = 256;
+constexpr int V8S_THREADS = 128, V8S_WARPS = V8S_THREADS / 32, V8S_MAX_PTS = 256;
 
 template <int J>
 struct V8SLayout {
-  static constexpr int E = 8 + J - 1, CS = 4 * J;  // floats per point: rx[J] ry[J] (v' rz)[J] as float2
+  static constexpr int E = 8 + J - 1;
   static constexpr int PPMAX = E * E + kSpreadPitchCodes - 1, CELLS = E * PPMAX;
-  static constexpr size_t coef = 0;
-  static constexpr size_t mos = coef + (size_t)V8S_MAX_PTS * CS * sizeof(float);
-  static constexpr size_t tre = mos + V8S_MAX_PTS * sizeof(int);
+  static constexpr size_t tre = 0;
   static constexpr size_t tim = tre + (size_t)CELLS * sizeof(int);
-  static constexpr size_t red = tim + (size_t)CELLS * sizeof(int);  // [8 warps][2 J] floats, then [8] unsigned
-  static constexpr size_t nxt = red + (size_t)V8S_WARPS * (2 * J + 1) * sizeof(float);
+  static constexpr size_t red = tim + (size_t)CELLS * sizeof(int);  // [warps] x 3 words
+  static constexpr size_t nxt = red + (size_t)V8S_WARPS * 3 * sizeof(float);
   static constexpr size_t bytes = (nxt + 2 * sizeof(int) + 15) / 16 * 16;
 };
 
+// B_p = max|rho_x| max|rho_y| max|rho_z| of every evaluated point, in the
+// order of the sorted point list (plan time).
 template <int J>
-__global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, const float2* __restrict__ in,
+__global__ void k_point_bounds(InterpGeom g, long long P, float* __restrict__ cb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  int w0[3], fm[3];
+  float f[3];
+  float2 ph;
+  decode_point_real<J>(g, g.sorted[i].x, w0, f, fm, ph);
+  float m = 1.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float r[J];
+    real_coeffs<J>(g.rpoly, f[a], fm[a], r);
+    float mx = 0.f;
+#pragma unroll
+    for (int q = 0; q < J; ++q) mx = fmaxf(mx, fabsf(r[q]));
+    m *= mx;
+  }
+  cb[i] = m;
+}
+
+cudaError_t launch_point_bounds(const InterpGeom& g, long long P, float* cb, cudaStream_t st) {
+  if (P == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((P + 255) / 256);
+  switch (g.J) {
+    case 2: k_point_bounds<2><<<blocks, 256, 0, st>>>(g, P, cb); break;
+    case 4: k_point_bounds<4><<<blocks, 256, 0, st>>>(g, P, cb); break;
+    case 6: k_point_bounds<6><<<blocks, 256, 0, st>>>(g, P, cb); break;
+    case 8: k_point_bounds<8><<<blocks, 256, 0, st>>>(g, P, cb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int J>
+__global__ void __launch_bounds__(V8S_THREADS, 8) k_spread_v8(InterpGeom g, const float2* __restrict__ in,
                                                              const int4* __restrict__ subs, int n_subs,
                                                              int* __restrict__ counter, float2* __restrict__ grid,
                                                              float budget, float inv_budget) {
   using Lay = V8SLayout<J>;
-  constexpr int T = 8, E = Lay::E, E2 = E * E, CS = Lay::CS;
+  constexpr int T = 8, E = Lay::E, E2 = E * E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* coef = (float*)(smem_raw + Lay::coef);
-  int* mos = (int*)(smem_raw + Lay::mos);
   int* tre = (int*)(smem_raw + Lay::tre);
   int* tim = (int*)(smem_raw + Lay::tim);
-  float* vred = (float*)(smem_raw + Lay::red);                 // [warps][2 J]
-  unsigned* wred = (unsigned*)(vred + V8S_WARPS * 2 * J);      // [warps]
+  float* red = (float*)(smem_raw + Lay::red);  // [warps][3]: bound (max or sum), sum of v' (uniform)
   int* nxt = (int*)(smem_raw + Lay::nxt);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nT = g.nT, K = g.K;
@@ -539,78 +574,45 @@ __global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, cons
     const bool uniform = (sp.w & 1) != 0;
     const int PP = E2 + (sc.w >> 16), nslots = sc.w & 0xffff;
     const int x0 = (sp.x % nT) * T, y0 = ((sp.x / nT) % nT) * T, z0 = (sp.x / (nT * nT)) * T;
-    // phase 1 (one point per thread: at most 256 points per subproblem)
-    unsigned bound = 0u;
-    float vz[2 * J];
-#pragma unroll
-    for (int q = 0; q < 2 * J; ++q) vz[q] = 0.f;
-    if (tid < sp.z) {
-      const uint2 ent = g.sorted[sp.y + tid];
-      int w0[3], fm[3];
-      float f[3];
-      float2 ph;
-      decode_point_real<J>(g, ent.x, w0, f, fm, ph);
-      const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
-      float* cp = coef + tid * CS;
-      int off = -1;
-      if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
-        off = lz * PP + ly * E + lx;
-        float2 val = in[ent.x];
-        if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
-        const float2 vp = cmulc(val, ph);  // e^{-i gamma sum u / 2} v
-        float rx[J], ry[J], rz[J];
-        real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
-        real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
-        real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
-        float mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll
-        for (int q = 0; q < J; ++q) {
-          mx = fmaxf(mx, fabsf(rx[q]));
-          my = fmaxf(my, fabsf(ry[q]));
-          mz = fmaxf(mz, fabsf(rz[q]));
-          vz[2 * q] = vp.x * rz[q];
-          vz[2 * q + 1] = vp.y * rz[q];
-        }
-        float4* c4 = (float4*)cp;
-#pragma unroll
-        for (int q = 0; q < J / 2; ++q) {
-          c4[q] = make_float4(rx[2 * q], rx[2 * q + 1], ry[2 * q], ry[2 * q + 1]);
-          c4[J / 2 + q] = make_float4(vz[4 * q], vz[4 * q + 1], vz[4 * q + 2], vz[4 * q + 3]);
-        }
-        bound = __float_as_uint(hypotf(val.x, val.y) * (mx * my * mz));
-      } else {
-        atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
-      }
-      mos[tid] = off;
+    // phase 1: the exponent (bounds are >= 0 or NaN: their bits order like the
+    // values, and a NaN wins); points at the origin are summed, so their bound
+    // is the sum, and their values are summed here too
+    float bmax = 0.f, bsum = 0.f;
+    float2 vsum = make_float2(0.f, 0.f);
+    for (int i = tid; i < sp.z; i += V8S_THREADS) {
+      const uint2 ent = g.sorted[sp.y + i];
+      float2 val = in[ent.x];
+      if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+      const float b = hypotf(val.x, val.y) * g.cbound[sp.y + i];
+      bmax = __uint_as_float(max(__float_as_uint(bmax), __float_as_uint(b)));
+      bsum += b;
+      vsum = cadd(vsum, val);  // points at the origin: phase 1, e^{0} = 1
     }
-    // the exponent: largest bound, or for points at the origin (summed before
-    // they are spread) the sum of the bounds
-    float bsum = 0.f;
-    unsigned bmax = 0u;
-    if (!uniform) {
-      const unsigned wb = __reduce_max_sync(0xffffffffu, bound);
-      if (lane == 0) wred[warp] = wb;
-    } else {
-      float b = __uint_as_float(bound);
+    {
+      const unsigned wb = __reduce_max_sync(0xffffffffu, __float_as_uint(bmax));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-#pragma unroll
-      for (int q = 0; q < 2 * J; ++q) {
-        float v = vz[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) vred[warp * 2 * J + q] = v;
+      for (int o = 16; o > 0; o >>= 1) {
+        bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+        vsum.x += __shfl_xor_sync(0xffffffffu, vsum.x, o);
+        vsum.y += __shfl_xor_sync(0xffffffffu, vsum.y, o);
       }
-      if (lane == 0) wred[warp] = __float_as_uint(b);
+      if (lane == 0) {
+        red[warp * 3] = uniform ? bsum : __uint_as_float(wb);
+        red[warp * 3 + 1] = vsum.x;
+        red[warp * 3 + 2] = vsum.y;
+      }
     }
     if (tid == 0) nxt[parity ^ 1] = atomicAdd(counter, 1);
     __syncthreads();
+    unsigned bb = 0u;
+    float2 vtot = make_float2(0.f, 0.f);
 #pragma unroll
     for (int w = 0; w < V8S_WARPS; ++w) {
-      bmax = max(bmax, wred[w]);
-      bsum += __uint_as_float(wred[w]);
+      if (uniform) bb = __float_as_uint(__uint_as_float(bb) + red[w * 3]);
+      else bb = max(bb, __float_as_uint(red[w * 3]));
+      vtot.x += red[w * 3 + 1];
+      vtot.y += red[w * 3 + 2];
     }
-    const unsigned bb = uniform ? __float_as_uint(bsum) : bmax;
     const bool poison = bb > kBoundLimitBits;
     int e_tile = kTileEmpty;
     if (!poison && bb != 0u) {
@@ -621,22 +623,31 @@ __global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, cons
         for (int k = tid; k < nslots; k += V8S_THREADS) {
           const int li = slots[k];
           if (li == 0xffff) continue;
-          const int mo = mos[li];
-          if (mo < 0) continue;
-          const float4* c4 = (const float4*)(coef + li * CS);
-          float rx[J], ry[J], z[2 * J];
-#pragma unroll
-          for (int q = 0; q < J / 2; ++q) {
-            const float4 a = c4[q], b = c4[J / 2 + q];
-            rx[2 * q] = a.x;
-            rx[2 * q + 1] = a.y;
-            ry[2 * q] = a.z * scl;
-            ry[2 * q + 1] = a.w * scl;
-            z[4 * q] = b.x;
-            z[4 * q + 1] = b.y;
-            z[4 * q + 2] = b.z;
-            z[4 * q + 3] = b.w;
+          const uint2 ent = g.sorted[sp.y + li];
+          int w0[3], fm[3];
+          float f[3];
+          float2 ph;
+          decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+          const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+          if ((unsigned)lx >= (unsigned)T || (unsigned)ly >= (unsigned)T || (unsigned)lz >= (unsigned)T) {
+            atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+            continue;
           }
+          float2 val = in[ent.x];
+          if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+          const float2 vp = cmulc(val, ph);  // e^{-i gamma sum u / 2} v
+          float rx[J], ry[J], rz[J];
+          real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
+          real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
+          real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
+          float z[2 * J];
+#pragma unroll
+          for (int q = 0; q < J; ++q) {
+            z[2 * q] = vp.x * rz[q];
+            z[2 * q + 1] = vp.y * rz[q];
+            ry[q] *= scl;
+          }
+          const int mo = lz * PP + ly * E + lx;
           int* re = tre + mo;
           int* im = tim + mo;
 #pragma unroll
@@ -654,37 +665,38 @@ __global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, cons
             }
           }
         }
-      } else {
-        // points at the origin: the summed z row, spread by thread per tap
-        float* vs = vred;  // [2 J] totals in the first row
-        __syncthreads();
-        if (tid < 2 * J) {
-          float t = 0.f;
-#pragma unroll
-          for (int w = 0; w < V8S_WARPS; ++w) t += vred[w * 2 * J + tid];
-          vs[V8S_WARPS * 2 * J - 2 * J + tid] = t;  // park the totals in the last row
-        }
-        __syncthreads();
-        const float* tot = vred + V8S_WARPS * 2 * J - 2 * J;
-        const float* c0 = coef;  // every point's weights are alike: take the first valid one
-        int mo = -1, p0 = 0;
-        for (int i = 0; i < sp.z; ++i)
-          if (mos[i] >= 0) {
-            mo = mos[i];
-            p0 = i;
-            break;
-          }
-        if (mo >= 0) {
-          c0 = coef + p0 * CS;
+      } else if (sp.z > 0) {
+        // points at the origin: u = 0 for every one (weights alike, no phase);
+        // the summed value is spread once, thread per tap
+        const uint2 ent = g.sorted[sp.y];
+        int w0[3], fm[3];
+        float f[3];
+        float2 ph;
+        decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+        const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+        if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+          const float2 vp = cmulc(vtot, ph);
+          float rx[J], ry[J], rz[J];
+          real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
+          real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
+          real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
+          const int mo = lz * PP + ly * E + lx;
           for (int t = tid; t < J * J * J; t += V8S_THREADS) {
             const int jx = t % J, jy = (t / J) % J, jz = t / (J * J);
-            // rx[jx], ry[jy] from the packed row: float4 q holds rx[2q], rx[2q+1], ry[2q], ry[2q+1]
-            const float rxv = c0[4 * (jx / 2) + (jx & 1)], ryv = c0[4 * (jy / 2) + 2 + (jy & 1)];
-            const float w = rxv * ryv * scl;
+            float wx = 0.f, wy = 0.f, wz = 0.f;
+#pragma unroll
+            for (int q = 0; q < J; ++q) {
+              wx = q == jx ? rx[q] : wx;
+              wy = q == jy ? ry[q] : wy;
+              wz = q == jz ? rz[q] : wz;
+            }
+            const float w = wx * wy * scl;
             const int o = mo + jz * PP + jy * E + jx;
-            atomicAdd(tre + o, round_unit1(w, tot[2 * jz]));
-            atomicAdd(tim + o, round_unit1(w, tot[2 * jz + 1]));
+            atomicAdd(tre + o, round_unit1(w, vp.x * wz));
+            atomicAdd(tim + o, round_unit1(w, vp.y * wz));
           }
+        } else if (tid == 0) {
+          atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
         }
       }
     }
@@ -752,7 +764,7 @@ static cudaError_t launch_spread_v8_j(const InterpGeom& g, const float2* in, con
 
 cudaError_t launch_spread_sched(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
                                 cudaStream_t st) {
-  if (!g.sched || !v8s_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
+  if (!g.sched || !g.cbound || !v8s_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
   switch (g.J) {
     case 2: return launch_spread_v8_j<2>(g, in, subs, n_subs, grid, st);
     case 4: return launch_spread_v8_j<4>(g, in, subs, n_subs, grid, st);
@@ -761,5 +773,4 @@ cudaError_t launch_spread_sched(const InterpGeom& g, const float2* in, const int
   }
   return cudaErrorInvalidValue;
 }
-
 }  // namespace nufft
