@@ -516,7 +516,7 @@ def run_ours(args):
     from paper_1605_05231_gb300 import fp32_fma_peak
 
     fp32_tflops, sms = fp32_fma_peak()
-    fixed_point = info["spread_variant"] in (5, 6)
+    fixed_point = info["spread_variant"] in (5, 6, 7, 8)
     work = stage_work(w.n, w.k, w.j, w.m, plan.n_dirs, info["evaluated_points"], 8 if fixed_point else 16)
     per_call = {}
     for side in ("forward", "adjoint"):

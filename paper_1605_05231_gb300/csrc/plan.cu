@@ -411,7 +411,7 @@ void free_plan(nufft3d_plan pl) {
                   pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound, pl->d_phase};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  for (void* q : {(void*)pl->d_sched, (void*)pl->d_gslots, (void*)pl->d_sslots, (void*)pl->d_cbound})
+  for (void* q : {(void*)pl->d_sched, (void*)pl->d_gslots, (void*)pl->d_sslots})
     if (q) cudaFree(q);
   for (cudaEvent_t e : pl->ev_fwd) cudaEventDestroy(e);
   for (cudaEvent_t e : pl->ev_adj) cudaEventDestroy(e);
@@ -441,7 +441,6 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.sched = pl->sched_ok ? pl->d_sched : nullptr;
   g.gslots = pl->d_gslots;
   g.sslots = pl->d_sslots;
-  g.cbound = pl->d_cbound;
   g.tmap = pl->tmap_ok ? &pl->tmap_grid : nullptr;
   g.first_wait_polls = pl->first_wait_polls;
   return g;
@@ -620,7 +619,7 @@ void schedule_range(const nufft3d_plan pl, size_t s0, size_t s1, SchedOut& out) 
 }  // namespace
 
 int build_schedules(nufft3d_plan pl, cudaStream_t st) {
-  for (void** q : {(void**)&pl->d_sched, (void**)&pl->d_gslots, (void**)&pl->d_sslots, (void**)&pl->d_cbound})
+  for (void** q : {(void**)&pl->d_sched, (void**)&pl->d_gslots, (void**)&pl->d_sslots})
     if (*q) {
       cudaFree(*q);
       *q = nullptr;
@@ -653,9 +652,6 @@ int build_schedules(nufft3d_plan pl, cudaStream_t st) {
   CK(upload(&pl->d_sched, sched, st));
   CK(upload(&pl->d_gslots, gs, st));
   CK(upload(&pl->d_sslots, ss, st));
-  // the per-point bounds of the scheduled spread, with the kernels' arithmetic
-  CK(dalloc(&pl->d_cbound, (size_t)pl->P_eval));
-  CK(nufft::launch_point_bounds(geom(pl), pl->P_eval, pl->d_cbound, st));
   CK(cudaStreamSynchronize(st));
   pl->sched_ok = true;
   return NUFFT3D_OK;
