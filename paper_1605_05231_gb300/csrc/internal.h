@@ -70,6 +70,7 @@ struct InterpGeom {
   const int4* sched = nullptr;        // per-subproblem conflict schedules (gather 10, spread 8), or null
   const uint16_t* gslots = nullptr;
   const uint16_t* sslots = nullptr;
+  const float* cbound = nullptr;      // per sorted point max|rho_x| max|rho_y| max|rho_z| (spread 8), or null
 };
 
 // Pruning of the column FFT passes to the cells the interpolation touches:
@@ -140,14 +141,17 @@ cudaError_t launch_gather_real(const InterpGeom& g, int grid_dtype, const void* 
 cudaError_t launch_spread_real(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
                                cudaStream_t st);
 // the variants with real weights and phases (they need the phased grid)
-inline bool gather_real(int variant) { return variant == 9 || variant == 10; }
+inline bool gather_real(int variant) { return variant == 9 || variant == 10 || variant == 11; }
 inline bool spread_real(int variant) { return variant == 7 || variant == 8; }
 bool v10_supported(int T, int J, int S);
 bool v8s_supported(int T, int J, int S);
 cudaError_t launch_gather_sched(const InterpGeom& g, int grid_dtype, const void* grid, const int4* subs, int n_subs,
                                 float2* out, cudaStream_t st);
+cudaError_t launch_gather_sched_pipelined(const InterpGeom& g, int grid_dtype, const void* grid, const int4* subs,
+                                          int n_subs, float2* out, cudaStream_t st);
 cudaError_t launch_spread_sched(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
                                 cudaStream_t st);
+cudaError_t launch_point_bounds(const InterpGeom& g, long long P, float* cb, cudaStream_t st);
 // plane pitches of the scheduled kernels' tiles: E^2 + code, code < 16 (gather) or < 32 (spread)
 constexpr int kGatherPitchCodes = 16, kSpreadPitchCodes = 32;
 
@@ -215,6 +219,7 @@ struct nufft3d_plan_s {
   int4* d_sched = nullptr;
   uint16_t* d_gslots = nullptr;
   uint16_t* d_sslots = nullptr;
+  float* d_cbound = nullptr;  // per sorted point: max|rho_x| max|rho_y| max|rho_z|
   bool sched_ok = false;
   cudaStream_t last_stream = nullptr;
   int first_wait_polls = -1;  // testing hook of nufft3d_plan_set_wait_limit (< 0: default)

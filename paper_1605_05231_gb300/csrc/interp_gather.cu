@@ -704,6 +704,7 @@ cudaError_t launch_gather(const InterpGeom& g, int variant, int grid_dtype, cons
   if (variant == 8) return launch_gather_tma(g, grid_dtype, grid, subs, n_subs, out, st);
   if (variant == 9) return launch_gather_real(g, grid_dtype, grid, subs, n_subs, out, st);
   if (variant == 10) return launch_gather_sched(g, grid_dtype, grid, subs, n_subs, out, st);
+  if (variant == 11) return launch_gather_sched_pipelined(g, grid_dtype, grid, subs, n_subs, out, st);
   if ((variant == 6 || variant == 7) && g.J == 6 && g.T == 8) {
     const int nt = variant == 7 ? 128 : 256;
     switch (grid_dtype) {

@@ -460,6 +460,152 @@ static cudaError_t launch_gather_v10_j(const InterpGeom& g, int dtype, const voi
   return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------
+// gather 11: gather 10 made persistent, with the next subproblem's tile
+// copied into a second shared-memory buffer by asynchronous copies
+// (cp.async, one cell per copy, at the subproblem's own plane pitch) while the
+// current subproblem is interpolated, so the staging latency is hidden.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async_cell(void* dst, const void* src, int bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <int J>
+__host__ __device__ inline size_t v11_tile_bytes(int elem) {
+  constexpr int E = 8 + J - 1;
+  return ((size_t)E * (E * E + kGatherPitchCodes - 1) * elem + 127) / 128 * 128;
+}
+
+template <int J, typename G>
+__global__ void __launch_bounds__(V10_NT, 5) k_gather_v11(InterpGeom g, const typename G::T* __restrict__ grid,
+                                                          const int4* __restrict__ subs, int n_subs,
+                                                          float2* __restrict__ out) {
+  typedef typename G::T TT;
+  constexpr int T = 8, NT = V10_NT, E = T + J - 1, E2 = E * E;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const size_t tb = v11_tile_bytes<J>((int)sizeof(TT));
+  const float inv_scale = lp_inv_scale<G>(g);
+  const int nT = g.nT, K = g.K;
+  // copy subproblem s's tile into buffer b
+  auto stage = [&](int s, int b) {
+    const int4 sp = subs[s];
+    const int PP = E2 + (g.sched[s].y >> 16);
+    const int x0 = (sp.x % nT) * T, y0 = ((sp.x / nT) % nT) * T, z0 = (sp.x / (nT * nT)) * T;
+    TT* tile = (TT*)(smem_raw + b * tb);
+    for (int r = threadIdx.x; r < E2 * E; r += NT) {
+      const int row = r / E, ix = r - row * E;
+      const int iz = row / E, iy = row - iz * E;
+      int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
+      gx -= gx >= K ? K : 0;
+      gy -= gy >= K ? K : 0;
+      gz -= gz >= K ? K : 0;
+      cp_async_cell(tile + iz * PP + iy * E + ix, grid + ((size_t)gz * K + gy) * K + gx, (int)sizeof(TT));
+    }
+  };
+  int b = 0;
+  if ((int)blockIdx.x < n_subs) stage(blockIdx.x, 0);
+  cp_async_commit();
+  for (int s = blockIdx.x; s < n_subs; s += gridDim.x, b ^= 1) {
+    const int nxt = s + gridDim.x;
+    if (nxt < n_subs) stage(nxt, b ^ 1);
+    cp_async_commit();
+    cp_async_wait1();  // this thread's copies of tile s have landed
+    __syncthreads();   // and everyone's
+    const int4 sp = subs[s];
+    const int4 sc = g.sched[s];
+    const int PP = E2 + (sc.y >> 16), nslots = sc.y & 0xffff;
+    const int x0 = (sp.x % nT) * T, y0 = ((sp.x / nT) % nT) * T, z0 = (sp.x / (nT * nT)) * T;
+    const TT* tile = (const TT*)(smem_raw + b * tb);
+    const uint16_t* slots = g.gslots + sc.x;
+    for (int k = threadIdx.x; k < nslots; k += NT) {
+      const int li = slots[k];
+      if (li == 0xffff) continue;
+      const uint2 ent = g.sorted[sp.y + li];
+      int w0[3], fm[3];
+      float f[3];
+      float2 ph;
+      decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+      const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+      if ((unsigned)lx >= (unsigned)T || (unsigned)ly >= (unsigned)T || (unsigned)lz >= (unsigned)T) {
+        atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+        continue;
+      }
+      float rx[J], ry[J], rz[J];
+      real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
+      real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
+      real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
+      float2 acc = make_float2(0.f, 0.f);
+      const TT* base = tile + (lz * PP + ly * E + lx);
+#pragma unroll
+      for (int jz = 0; jz < J; ++jz) {
+        const TT* pz = base + jz * PP;
+        float2 zacc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jy = 0; jy < J; ++jy) {
+          const TT* tp = pz + jy * E;
+          float2 row = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int jx = 0; jx < J; ++jx) rmac(row, rx[jx], G::to_f2(tp[jx]));
+          rmac(zacc, ry[jy], row);
+        }
+        rmac(acc, rz[jz], zacc);
+      }
+      const float2 res = cmul(cscale(acc, inv_scale), ph);
+      out[ent.x] = res;
+      if (ent.y != kNoTwin) out[ent.y] = res;
+    }
+    __syncthreads();  // buffer b is refilled two subproblems on
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <int J, typename G>
+static cudaError_t launch_gather_v11_t(const InterpGeom& g, const void* grid, const int4* subs, int n_subs,
+                                       float2* out, cudaStream_t st) {
+  auto f = k_gather_v11<J, G>;
+  const size_t smem = 2 * v11_tile_bytes<J>((int)sizeof(typename G::T));
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (n_subs == 0) return cudaSuccess;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, V10_NT, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const long long want = (long long)num_sms() * per_sm;
+  const int n_cta = (int)(want < n_subs ? want : n_subs);
+  f<<<n_cta, V10_NT, smem, st>>>(g, (const typename G::T*)grid, subs, n_subs, out);
+  return cudaGetLastError();
+}
+
+template <int J>
+static cudaError_t launch_gather_v11_j(const InterpGeom& g, int dtype, const void* grid, const int4* subs,
+                                       int n_subs, float2* out, cudaStream_t st) {
+  switch (dtype) {
+    case 0: return launch_gather_v11_t<J, GridC64>(g, grid, subs, n_subs, out, st);
+    case 1: return launch_gather_v11_t<J, GridBF16>(g, grid, subs, n_subs, out, st);
+    case 2: return launch_gather_v11_t<J, GridF16>(g, grid, subs, n_subs, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gather_sched_pipelined(const InterpGeom& g, int grid_dtype, const void* grid, const int4* subs,
+                                          int n_subs, float2* out, cudaStream_t st) {
+  if (!g.sched || !v10_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
+  switch (g.J) {
+    case 2: return launch_gather_v11_j<2>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 4: return launch_gather_v11_j<4>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 6: return launch_gather_v11_j<6>(g, grid_dtype, grid, subs, n_subs, out, st);
+    case 8: return launch_gather_v11_j<8>(g, grid_dtype, grid, subs, n_subs, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 bool v10_supported(int T, int J, int S) {
   return T == 8 && (J == 2 || J == 4 || J == 6 || J == 8) && S >= 1 && S <= 256;
 }
@@ -478,25 +624,26 @@ cudaError_t launch_gather_sched(const InterpGeom& g, int grid_dtype, const void*
 
 // ---------------------------------------------------------------------------
 // spread 8: the real-weight fixed-point spread, thread per point, with the
-// plan's conflict schedule.  Persistent CTAs of 256 threads take subproblems
+// plan's conflict schedule.  Persistent CTAs of 128 threads take subproblems
 // (at most 256 points) from a work counter:
-//  phase 1: thread k serves slot k of the schedule (a point, or nothing): it
-//           decodes its point, evaluates the real weights, folds
-//           e^{-i gamma (ux+uy+uz)/2} v into the z row and keeps them in
-//           registers, with its contributions' bound |v| max|rx| max|ry|
-//           max|rz|; the CTA's largest bound fixes the exponent;
-//  phase 2: every thread adds its point's J^3 taps, two int32 reductions
-//           each.  The 32 slots of a warp hold points with base offsets
-//           distinct modulo 32 cells (the tile's plane pitch is the
+//  phase 1: the CTA's exponent from the largest |v| B_p over its points, B_p
+//           = max|rho_x| max|rho_y| max|rho_z| of point p, kept by the plan
+//           (k_point_bounds, the kernels' own arithmetic);
+//  phase 2: thread k serves slot k of the schedule: it decodes its point,
+//           evaluates the real weights and folds e^{-i gamma (ux+uy+uz)/2} v
+//           into the z row in registers, then adds its J^3 taps, two int32
+//           reductions each.  The 32 slots of a warp hold points with base
+//           offsets distinct modulo 32 cells (the tile's plane pitch is the
 //           subproblem's), so every reduction instruction is one wavefront,
-//           and nothing is broadcast through shared memory.  Slots beyond the
-//           first 256 (rare) are decoded again in phase 2;
+//           and nothing is broadcast through shared memory;
 //           a subproblem of points at the origin (all alike) sums their
 //           values first and spreads the one point, thread per tap;
 //  flush:   the tile added to the grid; the inverse z pass applies the grid
 //           phase e^{+i gamma (kx+ky+kz)/2}.
+// With only the tile in shared memory, several CTAs share an SM, so one
+// waiting at a barrier leaves the SM to the others.
 // ---------------------------------------------------------------------------
-constexpr int V8S_THREADS = 256, V8S_WARPS = V8S_THREADS / 32, V8S_MAX_PTS = 256;
+constexpr int V8S_THREADS = 128, V8S_WARPS = V8S_THREADS / 32, V8S_MAX_PTS = 256;
 
 template <int J>
 struct V8SLayout {
@@ -509,81 +656,17 @@ struct V8SLayout {
   static constexpr size_t bytes = (nxt + 2 * sizeof(int) + 15) / 16 * 16;
 };
 
-// one slot's point: decoded, weighted, its tile offset (-1: none) and bound
+// B_p = max|rho_x| max|rho_y| max|rho_z| of every evaluated point, in the
+// order of the sorted point list (plan time).
 template <int J>
-struct V8Point {
-  float rx[J], ry[J], z[2 * J];
-  int mo;
-  float bound;
-};
-
-template <int J>
-__device__ __forceinline__ void v8_load_point(const InterpGeom& g, const float2* __restrict__ in, uint2 ent, int x0,
-                                              int y0, int z0, int PP, V8Point<J>& pt) {
-  constexpr int T = 8, E = 8 + J - 1;
+__global__ void k_point_bounds(InterpGeom g, long long P, float* __restrict__ cb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
   int w0[3], fm[3];
   float f[3];
   float2 ph;
-  decode_point_real<J>(g, ent.x, w0, f, fm, ph);
-  const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
-  pt.mo = -1;
-  pt.bound = 0.f;
-  if ((unsigned)lx >= (unsigned)T || (unsigned)ly >= (unsigned)T || (unsigned)lz >= (unsigned)T) {
-    atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
-    return;
-  }
-  float2 val = in[ent.x];
-  if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
-  const float2 vp = cmulc(val, ph);  // e^{-i gamma sum u / 2} v
-  float rz[J];
-  real_coeffs<J>(g.rpoly, f[0], fm[0], pt.rx);
-  real_coeffs<J>(g.rpoly, f[1], fm[1], pt.ry);
-  real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
-  float mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll
-  for (int q = 0; q < J; ++q) {
-    mx = fmaxf(mx, fabsf(pt.rx[q]));
-    my = fmaxf(my, fabsf(pt.ry[q]));
-    mz = fmaxf(mz, fabsf(rz[q]));
-    pt.z[2 * q] = vp.x * rz[q];
-    pt.z[2 * q + 1] = vp.y * rz[q];
-  }
-  pt.mo = lz * PP + ly * E + lx;
-  pt.bound = hypotf(val.x, val.y) * (mx * my * mz);
-}
-
-template <int J>
-__device__ __forceinline__ void v8_spread_point(const V8Point<J>& pt, float scl, int* tre, int* tim, int PP) {
-  constexpr int E = 8 + J - 1;
-  int* re = tre + pt.mo;
-  int* im = tim + pt.mo;
-#pragma unroll
-  for (int jy = 0; jy < J; ++jy) {
-    const float wy = pt.ry[jy] * scl;
-#pragma unroll
-    for (int jx = 0; jx < J; ++jx) {
-      const float w = pt.rx[jx] * wy;
-      int* pr = re + jy * E + jx;
-      int* pi = im + jy * E + jx;
-#pragma unroll
-      for (int jz = 0; jz < J; ++jz) {
-        atomicAdd(pr + jz * PP, round_unit1(w, pt.z[2 * jz]));
-        atomicAdd(pi + jz * PP, round_unit1(w, pt.z[2 * jz + 1]));
-      }
-    }
-  }
-}
-
-// the bound alone of one slot's point (slots handled a second time later)
-template <int J>
-__device__ __forceinline__ unsigned v8_point_bound(const InterpGeom& g, const float2* __restrict__ in, uint2 ent) {
-  int w0[3], fm[3];
-  float f[3];
-  float2 ph;
-  decode_point_real<J>(g, ent.x, w0, f, fm, ph);
-  float2 val = in[ent.x];
-  if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
-  float m = hypotf(val.x, val.y);
+  decode_point_real<J>(g, g.sorted[i].x, w0, f, fm, ph);
+  float m = 1.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float r[J];
@@ -593,11 +676,24 @@ __device__ __forceinline__ unsigned v8_point_bound(const InterpGeom& g, const fl
     for (int q = 0; q < J; ++q) mx = fmaxf(mx, fabsf(r[q]));
     m *= mx;
   }
-  return __float_as_uint(m);
+  cb[i] = m;
+}
+
+cudaError_t launch_point_bounds(const InterpGeom& g, long long P, float* cb, cudaStream_t st) {
+  if (P == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((P + 255) / 256);
+  switch (g.J) {
+    case 2: k_point_bounds<2><<<blocks, 256, 0, st>>>(g, P, cb); break;
+    case 4: k_point_bounds<4><<<blocks, 256, 0, st>>>(g, P, cb); break;
+    case 6: k_point_bounds<6><<<blocks, 256, 0, st>>>(g, P, cb); break;
+    case 8: k_point_bounds<8><<<blocks, 256, 0, st>>>(g, P, cb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 template <int J>
-__global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, const float2* __restrict__ in,
+__global__ void __launch_bounds__(V8S_THREADS, 8) k_spread_v8(InterpGeom g, const float2* __restrict__ in,
                                                              const int4* __restrict__ subs, int n_subs,
                                                              int* __restrict__ counter, float2* __restrict__ grid,
                                                              float budget, float inv_budget) {
@@ -606,7 +702,7 @@ __global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, cons
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* tre = (int*)(smem_raw + Lay::tre);
   int* tim = (int*)(smem_raw + Lay::tim);
-  float* red = (float*)(smem_raw + Lay::red);  // [warps][3]: bound (max or sum), sum of v (points at the origin)
+  float* red = (float*)(smem_raw + Lay::red);  // [warps][3]: bound (max or sum), sum of v' (uniform)
   int* nxt = (int*)(smem_raw + Lay::nxt);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nT = g.nT, K = g.K;
@@ -624,45 +720,28 @@ __global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, cons
     const bool uniform = (sp.w & 1) != 0;
     const int PP = E2 + (sc.w >> 16), nslots = sc.w & 0xffff;
     const int x0 = (sp.x % nT) * T, y0 = ((sp.x / nT) % nT) * T, z0 = (sp.x / (nT * nT)) * T;
-    const uint16_t* slots = g.sslots + sc.z;
-    // phase 1: this thread's first slot in registers, the bounds of all its
-    // slots (bounds are >= 0 or NaN: their bits order like the values, and a
-    // NaN wins); points at the origin (every one at u = 0: weights alike, no
-    // phase) are summed instead, and so are their bounds
-    V8Point<J> pt;
-    pt.mo = -1;
-    unsigned bmax = 0u;
-    float bsum = 0.f;
+    // phase 1: the exponent (bounds are >= 0 or NaN: their bits order like the
+    // values, and a NaN wins); points at the origin are summed, so their bound
+    // is the sum, and their values are summed here too
+    float bmax = 0.f, bsum = 0.f;
     float2 vsum = make_float2(0.f, 0.f);
-    if (!uniform) {
-      if (tid < nslots) {
-        const int li = slots[tid];
-        if (li != 0xffff) {
-          v8_load_point<J>(g, in, g.sorted[sp.y + li], x0, y0, z0, PP, pt);
-          bmax = __float_as_uint(pt.bound);
-        }
-      }
-      for (int k = tid + V8S_THREADS; k < nslots; k += V8S_THREADS) {
-        const int li = slots[k];
-        if (li != 0xffff) bmax = max(bmax, v8_point_bound<J>(g, in, g.sorted[sp.y + li]));
-      }
-    } else {
-      for (int i = tid; i < sp.z; i += V8S_THREADS) {
-        const uint2 ent = g.sorted[sp.y + i];
-        float2 val = in[ent.x];
-        if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
-        bsum += hypotf(val.x, val.y);
-        vsum = cadd(vsum, val);
-      }
+    for (int i = tid; i < sp.z; i += V8S_THREADS) {
+      const uint2 ent = g.sorted[sp.y + i];
+      float2 val = in[ent.x];
+      if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+      const float b = hypotf(val.x, val.y) * g.cbound[sp.y + i];
+      bmax = __uint_as_float(max(__float_as_uint(bmax), __float_as_uint(b)));
+      bsum += b;
+      vsum = cadd(vsum, val);  // points at the origin: phase 1, e^{0} = 1
+    }
+    {
+      const unsigned wb = __reduce_max_sync(0xffffffffu, __float_as_uint(bmax));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
         vsum.x += __shfl_xor_sync(0xffffffffu, vsum.x, o);
         vsum.y += __shfl_xor_sync(0xffffffffu, vsum.y, o);
       }
-    }
-    {
-      const unsigned wb = __reduce_max_sync(0xffffffffu, bmax);
       if (lane == 0) {
         red[warp * 3] = uniform ? bsum : __uint_as_float(wb);
         red[warp * 3 + 1] = vsum.x;
@@ -672,45 +751,13 @@ __global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, cons
     if (tid == 0) nxt[parity ^ 1] = atomicAdd(counter, 1);
     __syncthreads();
     unsigned bb = 0u;
-    float btot = 0.f;
     float2 vtot = make_float2(0.f, 0.f);
 #pragma unroll
     for (int w = 0; w < V8S_WARPS; ++w) {
-      bb = max(bb, __float_as_uint(red[w * 3]));
-      btot += red[w * 3];
+      if (uniform) bb = __float_as_uint(__uint_as_float(bb) + red[w * 3]);
+      else bb = max(bb, __float_as_uint(red[w * 3]));
       vtot.x += red[w * 3 + 1];
       vtot.y += red[w * 3 + 2];
-    }
-    if (uniform) {
-      // one point carrying the summed value, with the weights of the first
-      bb = 0u;
-      if (sp.z > 0) {
-        int w0[3], fm[3];
-        float f[3];
-        float2 ph;
-        decode_point_real<J>(g, g.sorted[sp.y].x, w0, f, fm, ph);
-        const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
-        if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
-          float rz[J];
-          real_coeffs<J>(g.rpoly, f[0], fm[0], pt.rx);
-          real_coeffs<J>(g.rpoly, f[1], fm[1], pt.ry);
-          real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
-          const float2 vp = cmulc(vtot, ph);
-          float mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll
-          for (int q = 0; q < J; ++q) {
-            mx = fmaxf(mx, fabsf(pt.rx[q]));
-            my = fmaxf(my, fabsf(pt.ry[q]));
-            mz = fmaxf(mz, fabsf(rz[q]));
-            pt.z[2 * q] = vp.x * rz[q];
-            pt.z[2 * q + 1] = vp.y * rz[q];
-          }
-          pt.mo = lz * PP + ly * E + lx;
-          bb = __float_as_uint(btot * (mx * my * mz));
-        } else if (tid == 0) {
-          atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
-        }
-      }
     }
     const bool poison = bb > kBoundLimitBits;
     int e_tile = kTileEmpty;
@@ -718,29 +765,84 @@ __global__ void __launch_bounds__(V8S_THREADS, 3) k_spread_v8(InterpGeom g, cons
       e_tile = max((int)(bb >> 23) - 127 + ((bb & 0x7FFFFFu) ? 1 : 0), -100);
       const float scl = budget * pow2f(-e_tile);
       if (!uniform) {
-        if (pt.mo >= 0) v8_spread_point<J>(pt, scl, tre, tim, PP);
-        for (int k = tid + V8S_THREADS; k < nslots; k += V8S_THREADS) {
+        const uint16_t* slots = g.sslots + sc.z;
+        for (int k = tid; k < nslots; k += V8S_THREADS) {
           const int li = slots[k];
           if (li == 0xffff) continue;
-          v8_load_point<J>(g, in, g.sorted[sp.y + li], x0, y0, z0, PP, pt);
-          if (pt.mo >= 0) v8_spread_point<J>(pt, scl, tre, tim, PP);
-        }
-      } else if (pt.mo >= 0) {
-        // the summed point, thread per tap
-        for (int t = tid; t < J * J * J; t += V8S_THREADS) {
-          const int jx = t % J, jy = (t / J) % J, jz = t / (J * J);
-          float wx = 0.f, wy = 0.f, zr = 0.f, zi = 0.f;
+          const uint2 ent = g.sorted[sp.y + li];
+          int w0[3], fm[3];
+          float f[3];
+          float2 ph;
+          decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+          const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+          if ((unsigned)lx >= (unsigned)T || (unsigned)ly >= (unsigned)T || (unsigned)lz >= (unsigned)T) {
+            atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+            continue;
+          }
+          float2 val = in[ent.x];
+          if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
+          const float2 vp = cmulc(val, ph);  // e^{-i gamma sum u / 2} v
+          float rx[J], ry[J], rz[J];
+          real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
+          real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
+          real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
+          float z[2 * J];
 #pragma unroll
           for (int q = 0; q < J; ++q) {
-            wx = q == jx ? pt.rx[q] : wx;
-            wy = q == jy ? pt.ry[q] : wy;
-            zr = q == jz ? pt.z[2 * q] : zr;
-            zi = q == jz ? pt.z[2 * q + 1] : zi;
+            z[2 * q] = vp.x * rz[q];
+            z[2 * q + 1] = vp.y * rz[q];
+            ry[q] *= scl;
           }
-          const float w = wx * wy * scl;
-          const int o = pt.mo + jz * PP + jy * E + jx;
-          atomicAdd(tre + o, round_unit1(w, zr));
-          atomicAdd(tim + o, round_unit1(w, zi));
+          const int mo = lz * PP + ly * E + lx;
+          int* re = tre + mo;
+          int* im = tim + mo;
+#pragma unroll
+          for (int jy = 0; jy < J; ++jy) {
+#pragma unroll
+            for (int jx = 0; jx < J; ++jx) {
+              const float w = rx[jx] * ry[jy];
+              int* pr = re + jy * E + jx;
+              int* pi = im + jy * E + jx;
+#pragma unroll
+              for (int jz = 0; jz < J; ++jz) {
+                atomicAdd(pr + jz * PP, round_unit1(w, z[2 * jz]));
+                atomicAdd(pi + jz * PP, round_unit1(w, z[2 * jz + 1]));
+              }
+            }
+          }
+        }
+      } else if (sp.z > 0) {
+        // points at the origin: u = 0 for every one (weights alike, no phase);
+        // the summed value is spread once, thread per tap
+        const uint2 ent = g.sorted[sp.y];
+        int w0[3], fm[3];
+        float f[3];
+        float2 ph;
+        decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+        const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
+        if ((unsigned)lx < (unsigned)T && (unsigned)ly < (unsigned)T && (unsigned)lz < (unsigned)T) {
+          const float2 vp = cmulc(vtot, ph);
+          float rx[J], ry[J], rz[J];
+          real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
+          real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
+          real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
+          const int mo = lz * PP + ly * E + lx;
+          for (int t = tid; t < J * J * J; t += V8S_THREADS) {
+            const int jx = t % J, jy = (t / J) % J, jz = t / (J * J);
+            float wx = 0.f, wy = 0.f, wz = 0.f;
+#pragma unroll
+            for (int q = 0; q < J; ++q) {
+              wx = q == jx ? rx[q] : wx;
+              wy = q == jy ? ry[q] : wy;
+              wz = q == jz ? rz[q] : wz;
+            }
+            const float w = wx * wy * scl;
+            const int o = mo + jz * PP + jy * E + jx;
+            atomicAdd(tre + o, round_unit1(w, vp.x * wz));
+            atomicAdd(tim + o, round_unit1(w, vp.y * wz));
+          }
+        } else if (tid == 0) {
+          atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
         }
       }
     }
@@ -808,7 +910,7 @@ static cudaError_t launch_spread_v8_j(const InterpGeom& g, const float2* in, con
 
 cudaError_t launch_spread_sched(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
                                 cudaStream_t st) {
-  if (!g.sched || !v8s_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
+  if (!g.sched || !g.cbound || !v8s_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
   switch (g.J) {
     case 2: return launch_spread_v8_j<2>(g, in, subs, n_subs, grid, st);
     case 4: return launch_spread_v8_j<4>(g, in, subs, n_subs, grid, st);

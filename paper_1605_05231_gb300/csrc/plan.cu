@@ -411,7 +411,7 @@ void free_plan(nufft3d_plan pl) {
                   pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound, pl->d_phase};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  for (void* q : {(void*)pl->d_sched, (void*)pl->d_gslots, (void*)pl->d_sslots})
+  for (void* q : {(void*)pl->d_sched, (void*)pl->d_gslots, (void*)pl->d_sslots, (void*)pl->d_cbound})
     if (q) cudaFree(q);
   for (cudaEvent_t e : pl->ev_fwd) cudaEventDestroy(e);
   for (cudaEvent_t e : pl->ev_adj) cudaEventDestroy(e);
@@ -441,6 +441,7 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.sched = pl->sched_ok ? pl->d_sched : nullptr;
   g.gslots = pl->d_gslots;
   g.sslots = pl->d_sslots;
+  g.cbound = pl->d_cbound;
   g.tmap = pl->tmap_ok ? &pl->tmap_grid : nullptr;
   g.first_wait_polls = pl->first_wait_polls;
   return g;
@@ -619,7 +620,7 @@ void schedule_range(const nufft3d_plan pl, size_t s0, size_t s1, SchedOut& out) 
 }  // namespace
 
 int build_schedules(nufft3d_plan pl, cudaStream_t st) {
-  for (void** q : {(void**)&pl->d_sched, (void**)&pl->d_gslots, (void**)&pl->d_sslots})
+  for (void** q : {(void**)&pl->d_sched, (void**)&pl->d_gslots, (void**)&pl->d_sslots, (void**)&pl->d_cbound})
     if (*q) {
       cudaFree(*q);
       *q = nullptr;
@@ -652,6 +653,9 @@ int build_schedules(nufft3d_plan pl, cudaStream_t st) {
   CK(upload(&pl->d_sched, sched, st));
   CK(upload(&pl->d_gslots, gs, st));
   CK(upload(&pl->d_sslots, ss, st));
+  // the per-point bounds of the scheduled spread, with the kernels' arithmetic
+  CK(dalloc(&pl->d_cbound, (size_t)pl->P_eval));
+  CK(nufft::launch_point_bounds(geom(pl), pl->P_eval, pl->d_cbound, st));
   CK(cudaStreamSynchronize(st));
   pl->sched_ok = true;
   return NUFFT3D_OK;
@@ -1089,7 +1093,7 @@ int nufft3d_plan_info(nufft3d_plan plan, int* out) {
 int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant, int points_per_subproblem,
                       int tile_edge, void* cuda_stream) {
   if (!plan) return NUFFT3D_ERR_ARG;
-  if (gather_variant < -1 || gather_variant > 10 || spread_variant < -1 || spread_variant > 8) return NUFFT3D_ERR_ARG;
+  if (gather_variant < -1 || gather_variant > 11 || spread_variant < -1 || spread_variant > 8) return NUFFT3D_ERR_ARG;
   if (points_per_subproblem < 0 || tile_edge < 0) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (tile_edge != 4 && tile_edge != 8 && tile_edge != 16)) return NUFFT3D_ERR_ARG;
   if (tile_edge > 0 && (plan->K % tile_edge != 0 || tile_edge + plan->J - 1 > plan->K)) return NUFFT3D_ERR_UNSUPPORTED;
@@ -1113,7 +1117,8 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   if (gv == 9 && (!plan->real_ok || !nufft::v9_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 7 && (!plan->real_ok || !nufft::v7s_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
   // the scheduled variants: real weights, T = 8, at most 256 points per subproblem
-  if (gv == 10 && (!plan->real_ok || !nufft::v10_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
+  if ((gv == 10 || gv == 11) && (!plan->real_ok || !nufft::v10_supported(T, plan->J, S_new)))
+    return NUFFT3D_ERR_UNSUPPORTED;
   if (sv == 8 && (!plan->real_ok || !nufft::v8s_supported(T, plan->J, S_new))) return NUFFT3D_ERR_UNSUPPORTED;
   PLAN_DEVICE(plan);
   int rc = NUFFT3D_OK;
@@ -1134,9 +1139,9 @@ int nufft3d_plan_tune(nufft3d_plan plan, int gather_variant, int spread_variant,
   } else if (S != plan->pts_per_sub) {
     rc = build_subproblems(plan, S, (cudaStream_t)cuda_stream);
   }
-  if (rc == NUFFT3D_OK && (gv == 10 || sv == 8) && !plan->sched_ok) {
+  if (rc == NUFFT3D_OK && (gv == 10 || gv == 11 || sv == 8) && !plan->sched_ok) {
     // no schedule could be built for this split: keep runnable variants
-    if (gv == 10) plan->gather_variant = nufft::v9_supported(plan->T, plan->J, plan->pts_per_sub) ? 9 : 0;
+    if (gv == 10 || gv == 11) plan->gather_variant = nufft::v9_supported(plan->T, plan->J, plan->pts_per_sub) ? 9 : 0;
     if (sv == 8) plan->spread_variant = 0;
     return NUFFT3D_ERR_UNSUPPORTED;
   }

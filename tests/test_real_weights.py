@@ -46,7 +46,7 @@ def _face_dirs(n_rand, seed):
 
 
 @pytest.mark.parametrize("gv,sv", [(9, 7), (9, 6), (5, 7), (9, 3), (8, 7), (9, 0), (10, 8), (10, 7), (9, 8), (5, 8),
-                                   (10, 3)])
+                                   (10, 3), (11, 7), (11, 8)])
 def test_real_variants_umbrella(cuda_lib, gv, sv):
     n = 32
     dirs = I.umbrella_directions(35, 20)
@@ -73,14 +73,15 @@ def test_real_variants_umbrella(cuda_lib, gv, sv):
     (16, 32, 32, 8, 128),     # J = 8
     (20, 64, 48, 2, 256),     # J = 2, M != K
 ])
-@pytest.mark.parametrize("sched", [False, True], ids=["rank", "sched"])
+@pytest.mark.parametrize("sched", [0, 1, 2], ids=["rank", "sched", "pipelined"])
 def test_real_variants_faces_shapes_and_taps(cuda_lib, n, k, m, j, pps, sched):
-    """gather 9 / spread 7 (or 0), and the scheduled gather 10 / spread 8 (any J)."""
+    """gather 9 / spread 7 (or 0), the scheduled gather 10 / spread 8 and the
+    pipelined scheduled gather 11 (any J)."""
     dirs = _face_dirs(40, n + k)
     x = I.random_volume(n, 1).astype(np.float32)
     y = I.random_lines(dirs.shape[0], m, 2).astype(np.complex64)
     plan = _plan(cuda_lib, n, dirs, m, k, j)
-    gv, sv = (10, 8) if sched else (9, 7 if j == 6 else 0)
+    gv, sv = ((9, 7 if j == 6 else 0), (10, 8), (11, 8))[sched]
     plan.tune(gv, sv, pps, 8)
     p, a = _run(plan, x, y)
     op = _oplan(n, dirs, m, k, j)
@@ -118,7 +119,7 @@ def test_real_variants_complex_volume_weights_raw_samples(cuda_lib):
 
 
 @pytest.mark.parametrize("dtype,bound", [("bf16", 1e-3), ("fp16", 1e-4)])
-@pytest.mark.parametrize("gv,sv", [(9, 7), (10, 8)])
+@pytest.mark.parametrize("gv,sv", [(9, 7), (10, 8), (11, 7)])
 def test_real_gather_reduced_precision_grid(cuda_lib, dtype, bound, gv, sv):
     """The phase is applied before the grid is rounded to bf16 / fp16."""
     w = I.workload("tiny32")
@@ -137,7 +138,7 @@ def test_real_gather_reduced_precision_grid(cuda_lib, dtype, bound, gv, sv):
 
 def test_real_variants_refused_with_a_table(cuda_lib):
     plan = cuda_lib.Plan(32, I.random_directions(10, 1))
-    for gv, sv in ((9, -1), (-1, 7), (10, -1), (-1, 8)):
+    for gv, sv in ((9, -1), (-1, 7), (10, -1), (-1, 8), (11, -1)):
         with pytest.raises(cuda_lib.NufftError) as ei:
             plan.tune(gv, sv, 256, 8)
         assert ei.value.status == -4
@@ -165,7 +166,7 @@ def test_switching_between_real_and_complex_variants(cuda_lib):
 def test_scheduled_variants_refuse_large_subproblems(cuda_lib):
     """The schedules exist for subproblems of at most 256 points."""
     plan = _plan(cuda_lib, 32, I.umbrella_directions(20, 10))
-    for gv, sv in ((10, -1), (-1, 8)):
+    for gv, sv in ((10, -1), (-1, 8), (11, -1)):
         with pytest.raises(cuda_lib.NufftError) as ei:
             plan.tune(gv, sv, 512, 8)
         assert ei.value.status == -4
