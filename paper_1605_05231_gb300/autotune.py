@@ -16,6 +16,10 @@ from .binding import NufftError
 
 # (gather variant, spread variant, points per subproblem, tile edge)
 CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
+    (10, 7, 256, 8),
+    (11, 7, 256, 8),
+    (10, 8, 256, 8),
+    (9, 7, 256, 8),
     (5, 6, 256, 8),
     (8, 6, 256, 8),
     (3, 6, 256, 8),
