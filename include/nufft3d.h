@@ -322,7 +322,8 @@ int nufft3d_host_pipeline_destroy(nufft3d_host_pipeline pipe);
  * item i, vols[i] -> lines[i] (forward) then lines[i] -> vols_out[i]
  * (adjoint), all device buffers laid out as for a single plan.  The first
  * call captures the whole sequence into one CUDA graph (items dealt to up to
- * 8 worker streams forked from cuda_stream) and every call replays it with a
+ * 12 worker streams forked from cuda_stream, largest items first to the least
+ * loaded stream) and every call replays it with a
  * single graph launch on cuda_stream; passing different buffers, or calling
  * nufft3d_batch_invalidate (after re-tuning an item plan), captures again.
  * Item plans are reachable with nufft3d_batch_item for tuning; they must not

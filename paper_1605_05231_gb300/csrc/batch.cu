@@ -1,9 +1,11 @@
 // Batches of independent projector problems of mixed sizes.  A batch owns one
 // plan per item.  Its forward + adjoint over all items is captured once into a
-// CUDA graph: items are dealt round-robin to worker streams forked from the
-// caller's stream, so small problems run concurrently, and every later call
+// CUDA graph: items are dealt, largest first, to the least loaded of up to 12
+// worker streams forked from the caller's stream, so small problems run
+// concurrently, and every later call
 // replays the whole sequence with one cudaGraphLaunch.  The graph is captured
 // again only when the caller passes different buffers.
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -23,7 +25,7 @@ struct nufft3d_batch_s {
 
 namespace {
 
-constexpr int kMaxWorkerStreams = 8;
+constexpr int kMaxWorkerStreams = 12;
 
 int cuda_rc(cudaError_t e) {
   if (e == cudaSuccess) return NUFFT3D_OK;
@@ -52,8 +54,21 @@ int capture(nufft3d_batch b, const void* const* vols, void* const* lines, void* 
   int rc = NUFFT3D_OK;
   e = cudaEventRecord(b->fork, st);
   for (int s = 0; s < ns && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->streams[s], b->fork, 0);
-  for (int i = 0; i < n && e == cudaSuccess && rc == NUFFT3D_OK; ++i) {
-    cudaStream_t ws = b->streams[i % ns];
+  // items dealt largest first to the least loaded worker stream (work taken as
+  // the evaluated points plus the grid cells), so the streams finish together
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto work = [&](int i) {
+    const nufft3d_plan p = b->plans[i];
+    return (double)p->P_eval + (double)p->K * p->K * p->K;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work(a) > work(c); });
+  std::vector<double> load(ns, 0.0);
+  for (int q = 0; q < n && e == cudaSuccess && rc == NUFFT3D_OK; ++q) {
+    const int i = order[q];
+    const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[w] += work(i);
+    cudaStream_t ws = b->streams[w];
     rc = nufft::plan_forward_enqueue(b->plans[i], vols[i], lines[i], ws);
     if (rc == NUFFT3D_OK) rc = nufft::plan_adjoint_enqueue(b->plans[i], lines[i], vols_out[i], ws);
   }

@@ -71,7 +71,27 @@ struct InterpGeom {
   const uint16_t* gslots = nullptr;
   const uint16_t* sslots = nullptr;
   const float* cbound = nullptr;      // per sorted point max|rho_x| max|rho_y| max|rho_z| (spread 8), or null
+  const int* box = nullptr;           // per subproblem, the tile cells its taps can reach (TileBox), or null
 };
+
+// The part of a subproblem's E^3 tile its taps can reach, from the plan:
+// origin and extent per axis (the whole tile without a plan box).
+struct TileBox {
+  int ox, ex, oy, ey, oz, ez;
+};
+__host__ __device__ inline TileBox unpack_box(const int* box, int s, int E) {
+  TileBox b{0, E, 0, E, 0, E};
+  if (box) {
+    const int c = box[s];
+    b.ox = c & 15;
+    b.ex = (c >> 4) & 31;
+    b.oy = (c >> 9) & 15;
+    b.ey = (c >> 13) & 31;
+    b.oz = (c >> 18) & 15;
+    b.ez = (c >> 22) & 31;
+  }
+  return b;
+}
 
 // Pruning of the column FFT passes to the cells the interpolation touches:
 // the ball |k| <= R in centred grid frequencies (R = K/2 + (J/2) sqrt 3 + 1
@@ -220,6 +240,7 @@ struct nufft3d_plan_s {
   uint16_t* d_gslots = nullptr;
   uint16_t* d_sslots = nullptr;
   float* d_cbound = nullptr;  // per sorted point: max|rho_x| max|rho_y| max|rho_z|
+  int* d_box = nullptr;       // per subproblem: packed TileBox
   bool sched_ok = false;
   cudaStream_t last_stream = nullptr;
   int first_wait_polls = -1;  // testing hook of nufft3d_plan_set_wait_limit (< 0: default)

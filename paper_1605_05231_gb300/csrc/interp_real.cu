@@ -310,16 +310,21 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, cons
     // flush: the tile added to the grid (the inverse z pass applies the grid phase)
     const float inv = e_tile == kTileEmpty ? 0.f : inv_budget * pow2f(e_tile);
     const float qnan = __int_as_float(0x7fc00000);
-    for (int c = tid; c < E2; c += V7S_THREADS) {
-      const int iy = c / E, ix = c - iy * E;
+    // only the plan's box of the tile can hold values
+    const TileBox tb = unpack_box(g.box, s, E);
+    const float inv_ex = 1.f / (float)tb.ex;
+    for (int cc = tid; cc < tb.ex * tb.ey; cc += V7S_THREADS) {
+      const int r = (int)(((float)cc + 0.5f) * inv_ex);
+      const int ix = tb.ox + cc - r * tb.ex, iy = tb.oy + r, c = iy * E + ix;
       int gx = x0 + ix, gy = y0 + iy;
       gx -= gx >= K ? K : 0;
       gy -= gy >= K ? K : 0;
       float2* col = grid + (size_t)gy * K + gx;
-      int gz = z0;
+      int gz = z0 + tb.oz;
 #pragma unroll
-      for (int iz = 0; iz < E; ++iz) {
-        const int idx = c + iz * E2;
+      for (int t = 0; t < E; ++t) {
+        if (t >= tb.ez) break;
+        const int idx = c + (tb.oz + t) * E2;
         const int a = tre[idx], b = tim[idx];
         if ((a | b) != 0 || poison) {
           tre[idx] = 0;
@@ -387,9 +392,13 @@ __global__ void __launch_bounds__(V10_NT, 8) k_gather_v10(InterpGeom g, const ty
   const int4 sc = g.sched[blockIdx.x];
   const int PP = E2 + (sc.y >> 16), nslots = sc.y & 0xffff;
   const int x0 = (sp.x % nT) * T, y0 = ((sp.x / nT) % nT) * T, z0 = (sp.x / (nT * nT)) * T;
-  for (int r = threadIdx.x; r < E2 * E; r += NT) {
-    const int row = r / E, ix = r - row * E;
-    const int iz = row / E, iy = row - iz * E;
+  // only the cells the subproblem's taps can reach are staged (the plan's box;
+  // the quotients below are exact: (r + 1/2) / e is at least 1/(2e) from an integer)
+  const TileBox bx = unpack_box(g.box, blockIdx.x, E);
+  const float inv_ex = 1.f / (float)bx.ex, inv_ey = 1.f / (float)bx.ey;
+  for (int r = threadIdx.x; r < bx.ex * bx.ey * bx.ez; r += NT) {
+    const int row = (int)(((float)r + 0.5f) * inv_ex), ix = bx.ox + r - row * bx.ex;
+    const int rz = (int)(((float)row + 0.5f) * inv_ey), iy = bx.oy + row - rz * bx.ey, iz = bx.oz + rz;
     int gx = x0 + ix, gy = y0 + iy, gz = z0 + iz;
     gx -= gx >= K ? K : 0;
     gy -= gy >= K ? K : 0;
@@ -851,16 +860,21 @@ __global__ void __launch_bounds__(V8S_THREADS, 8) k_spread_v8(InterpGeom g, cons
     // flush: the tile added to the grid (the inverse z pass applies the grid phase)
     const float inv = e_tile == kTileEmpty ? 0.f : inv_budget * pow2f(e_tile);
     const float qnan = __int_as_float(0x7fc00000);
-    for (int c = tid; c < E2; c += V8S_THREADS) {
-      const int iy = c / E, ix = c - iy * E;
+    // only the plan's box of the tile can hold values
+    const TileBox bx = unpack_box(g.box, s, E);
+    const float inv_ex = 1.f / (float)bx.ex;
+    for (int cc = tid; cc < bx.ex * bx.ey; cc += V8S_THREADS) {
+      const int r = (int)(((float)cc + 0.5f) * inv_ex);
+      const int ix = bx.ox + cc - r * bx.ex, iy = bx.oy + r, c = iy * E + ix;
       int gx = x0 + ix, gy = y0 + iy;
       gx -= gx >= K ? K : 0;
       gy -= gy >= K ? K : 0;
       float2* col = grid + (size_t)gy * K + gx;
-      int gz = z0;
+      int gz = z0 + bx.oz;
 #pragma unroll
-      for (int iz = 0; iz < E; ++iz) {
-        const int idx = c + iz * PP;
+      for (int t = 0; t < E; ++t) {
+        if (t >= bx.ez) break;
+        const int idx = c + (bx.oz + t) * PP;
         const int a = tre[idx], b = tim[idx];
         if ((a | b) != 0 || poison) {
           tre[idx] = 0;

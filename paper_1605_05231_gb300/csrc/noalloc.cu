@@ -96,6 +96,7 @@ extern "C" int nufft3d_adjoint_noalloc(nufft3d_plan pl, const void* lines_dev, v
   g.gslots = pl->d_gslots;
   g.sslots = pl->d_sslots;
   g.cbound = pl->d_cbound;
+  g.box = pl->sched_ok ? pl->d_box : nullptr;
 
   const float2* src = (const float2*)lines_dev;
   if (pl->do_line_fft) {

@@ -411,7 +411,7 @@ void free_plan(nufft3d_plan pl) {
                   pl->d_lines, pl->d_err, pl->d_counter, pl->d_lp_bound, pl->d_phase};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  for (void* q : {(void*)pl->d_sched, (void*)pl->d_gslots, (void*)pl->d_sslots, (void*)pl->d_cbound})
+  for (void* q : {(void*)pl->d_sched, (void*)pl->d_gslots, (void*)pl->d_sslots, (void*)pl->d_cbound, (void*)pl->d_box})
     if (q) cudaFree(q);
   for (cudaEvent_t e : pl->ev_fwd) cudaEventDestroy(e);
   for (cudaEvent_t e : pl->ev_adj) cudaEventDestroy(e);
@@ -442,6 +442,7 @@ InterpGeom geom(const nufft3d_plan pl) {
   g.gslots = pl->d_gslots;
   g.sslots = pl->d_sslots;
   g.cbound = pl->d_cbound;
+  g.box = pl->sched_ok ? pl->d_box : nullptr;
   g.tmap = pl->tmap_ok ? &pl->tmap_grid : nullptr;
   g.first_wait_polls = pl->first_wait_polls;
   return g;
@@ -471,7 +472,32 @@ namespace {
 struct SchedOut {
   std::vector<int4> sched;
   std::vector<uint16_t> g, s;
+  std::vector<int> box;
 };
+
+// The cells a subproblem's taps can reach: per axis [min first tap, max first
+// tap + J - 1] of its points, widened by one cell on each side (the first taps
+// here are FP64 floors and may differ by one from the device's near an
+// integer), clipped to the E^3 tile.  Packed as (origin 4 bits, extent 5 bits)
+// per axis, x in the low bits.
+int pack_box(const std::vector<int>& lx, const std::vector<int>& ly, const std::vector<int>& lz, int n, int J, int E) {
+  int code = 0;
+  const std::vector<int>* ax[3] = {&lx, &ly, &lz};
+  for (int a = 0; a < 3; ++a) {
+    int mn = E, mx = -1;
+    for (int i = 0; i < n; ++i) {
+      mn = std::min(mn, (*ax[a])[i]);
+      mx = std::max(mx, (*ax[a])[i]);
+    }
+    int o = 0, e = E;
+    if (n > 0) {
+      o = std::max(0, mn - 1);
+      e = std::min(E, mx + J + 1) - o;
+    }
+    code |= (o | (e << 4)) << (9 * a);
+  }
+  return code;
+}
 
 void schedule_range(const nufft3d_plan pl, size_t s0, size_t s1, SchedOut& out) {
   const int T = pl->T, J = pl->J, K = pl->K, E = T + J - 1, nT = pl->nT;
@@ -504,6 +530,7 @@ void schedule_range(const nufft3d_plan pl, size_t s0, size_t s1, SchedOut& out) 
         *dst[a] = (int)std::min<long long>(std::max<long long>(loc, 0), T - 1);
       }
     }
+    out.box.push_back(pack_box(lx, ly, lz, n, J, E));
     int4 sc = make_int4((int)out.g.size(), 0, (int)out.s.size(), 0);
     off.resize(n);
     order.resize(n);
@@ -620,7 +647,8 @@ void schedule_range(const nufft3d_plan pl, size_t s0, size_t s1, SchedOut& out) 
 }  // namespace
 
 int build_schedules(nufft3d_plan pl, cudaStream_t st) {
-  for (void** q : {(void**)&pl->d_sched, (void**)&pl->d_gslots, (void**)&pl->d_sslots, (void**)&pl->d_cbound})
+  for (void** q : {(void**)&pl->d_sched, (void**)&pl->d_gslots, (void**)&pl->d_sslots, (void**)&pl->d_cbound,
+                   (void**)&pl->d_box})
     if (*q) {
       cudaFree(*q);
       *q = nullptr;
@@ -641,18 +669,22 @@ int build_schedules(nufft3d_plan pl, cudaStream_t st) {
   for (auto& x : th) x.join();
   std::vector<int4> sched;
   std::vector<uint16_t> gs, ss;
+  std::vector<int> box;
   sched.reserve(ns);
+  box.reserve(ns);
   for (auto& pt : parts) {
     const int gb = (int)gs.size(), sb = (int)ss.size();
     for (int4 v : pt.sched) sched.push_back(make_int4(v.x + gb, v.y, v.z + sb, v.w));
     gs.insert(gs.end(), pt.g.begin(), pt.g.end());
     ss.insert(ss.end(), pt.s.begin(), pt.s.end());
+    box.insert(box.end(), pt.box.begin(), pt.box.end());
   }
   if (gs.size() > 0x7fffffffull || ss.size() > 0x7fffffffull) return NUFFT3D_OK;  // no schedule: variants 10 / 8 refuse
   if (ss.empty()) ss.push_back(0xffff);
   CK(upload(&pl->d_sched, sched, st));
   CK(upload(&pl->d_gslots, gs, st));
   CK(upload(&pl->d_sslots, ss, st));
+  CK(upload(&pl->d_box, box, st));
   // the per-point bounds of the scheduled spread, with the kernels' arithmetic
   CK(dalloc(&pl->d_cbound, (size_t)pl->P_eval));
   CK(nufft::launch_point_bounds(geom(pl), pl->P_eval, pl->d_cbound, st));
