@@ -310,21 +310,16 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, cons
     // flush: the tile added to the grid (the inverse z pass applies the grid phase)
     const float inv = e_tile == kTileEmpty ? 0.f : inv_budget * pow2f(e_tile);
     const float qnan = __int_as_float(0x7fc00000);
-    // only the plan's box of the tile can hold values
-    const TileBox tb = unpack_box(g.box, s, E);
-    const float inv_ex = 1.f / (float)tb.ex;
-    for (int cc = tid; cc < tb.ex * tb.ey; cc += V7S_THREADS) {
-      const int r = (int)(((float)cc + 0.5f) * inv_ex);
-      const int ix = tb.ox + cc - r * tb.ex, iy = tb.oy + r, c = iy * E + ix;
+    for (int c = tid; c < E2; c += V7S_THREADS) {
+      const int iy = c / E, ix = c - iy * E;
       int gx = x0 + ix, gy = y0 + iy;
       gx -= gx >= K ? K : 0;
       gy -= gy >= K ? K : 0;
       float2* col = grid + (size_t)gy * K + gx;
-      int gz = z0 + tb.oz;
+      int gz = z0;
 #pragma unroll
-      for (int t = 0; t < E; ++t) {
-        if (t >= tb.ez) break;
-        const int idx = c + (tb.oz + t) * E2;
+      for (int iz = 0; iz < E; ++iz) {
+        const int idx = c + iz * E2;
         const int a = tre[idx], b = tim[idx];
         if ((a | b) != 0 || poison) {
           tre[idx] = 0;
