@@ -336,6 +336,16 @@ int nufft3d_batch_item(nufft3d_batch batch, int i, nufft3d_plan* plan);
 int nufft3d_batch_forward_adjoint(nufft3d_batch batch, const void* const* vols, void* const* lines,
                                   void* const* vols_out, void* cuda_stream);
 int nufft3d_batch_invalidate(nufft3d_batch batch);
+/* Grouped launches (on by default): items that share N, K and J and run the
+ * exact-coefficient default kernels (scheduled gather 10, real-weight spread
+ * 7, complex64 grid) are captured as groups of up to 32.  Their FFT passes and
+ * line DFTs still run per item on the worker streams, but each group's
+ * interpolation is one gather launch over all its items' subproblems and one
+ * persistent spread launch whose CTAs take (item, subproblem) work from a
+ * single counter, so small items no longer leave the GPU idle at their tails.
+ * on = 0 captures every item's whole sequence separately.  The next call
+ * captures again. */
+int nufft3d_batch_set_grouping(nufft3d_batch batch, int on);
 int nufft3d_batch_destroy(nufft3d_batch batch);
 
 #ifdef __cplusplus

@@ -35,6 +35,7 @@ EXPORTS = (
     "nufft3d_batch_item",
     "nufft3d_batch_forward_adjoint",
     "nufft3d_batch_invalidate",
+    "nufft3d_batch_set_grouping",
     "nufft3d_batch_destroy",
     "nufft3d_fourier_slice_weights",
     "nufft3d_polar_resample",
@@ -103,6 +104,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.nufft3d_batch_item.argtypes = [vp, i, ctypes.POINTER(vp)]
     lib.nufft3d_batch_forward_adjoint.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.nufft3d_batch_invalidate.argtypes = [vp]
+    lib.nufft3d_batch_set_grouping.argtypes = [vp, i]
     lib.nufft3d_batch_destroy.argtypes = [vp]
     lib.nufft3d_workspace_bytes.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
     lib.nufft3d_plan_sync_status.argtypes = [vp, ip]
@@ -436,6 +438,10 @@ class Batch:
     def invalidate(self):
         """Capture the graph again on the next call (after re-tuning item plans)."""
         _check(self.lib.nufft3d_batch_invalidate(self._handle), "nufft3d_batch_invalidate")
+
+    def set_grouping(self, on: bool):
+        """Grouped interpolation launches across items of equal N, K, J (default on)."""
+        _check(self.lib.nufft3d_batch_set_grouping(self._handle, int(bool(on))), "nufft3d_batch_set_grouping")
 
     def forward_adjoint(self, vols, lines, vols_out, stream=None):
         n = len(self.items)

@@ -13,6 +13,10 @@
 
 struct nufft3d_batch_s {
   std::vector<nufft3d_plan> plans;
+  bool grouping = true;                   // grouped interpolation launches (see capture)
+  std::vector<nufft::GroupItem*> d_items;  // per group of the last capture, device copies
+  std::vector<int*> d_counters;           // per group: the spread's work counter
+  std::vector<cudaEvent_t> evs;           // events of the last capture
   int device = 0;
   cudaStream_t cap = nullptr;  // capture origin (the legacy stream cannot be captured)
   std::vector<cudaStream_t> streams;
@@ -32,8 +36,18 @@ int cuda_rc(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? NUFFT3D_ERR_NOMEM : NUFFT3D_ERR_CUDA;
 }
 
+void free_capture_resources(nufft3d_batch b) {
+  for (auto* p : b->d_items) cudaFree(p);
+  for (auto* p : b->d_counters) cudaFree(p);
+  for (cudaEvent_t e : b->evs) cudaEventDestroy(e);
+  b->d_items.clear();
+  b->d_counters.clear();
+  b->evs.clear();
+}
+
 void free_batch(nufft3d_batch b) {
   if (!b) return;
+  free_capture_resources(b);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
@@ -44,28 +58,168 @@ void free_batch(nufft3d_batch b) {
   delete b;
 }
 
+// A plan whose interpolation can join a group launch: exact coefficients with
+// the scheduled gather (10) and the real-weight spread (7) on complex64 grids.
+bool groupable(const nufft3d_plan p) {
+  return p->real_ok && p->sched_ok && p->gather_variant == 10 && p->spread_variant == 7 &&
+         p->grid_dtype == NUFFT3D_GRID_C64 && p->T == 8 && p->J == 6 && p->pts_per_sub <= 256;
+}
+
+nufft::GroupItem group_item(const nufft3d_plan p, void* lines) {
+  nufft::GroupItem it{};
+  it.pg = nufft::PointGeom{p->K, p->M, p->d_dir, p->d_rad};
+  it.sorted = p->d_sorted;
+  it.subs = p->d_sub;
+  it.n_subs = p->n_sub;
+  it.sched = p->d_sched;
+  it.gslots = p->d_gslots;
+  it.box = p->d_box;
+  it.err = p->d_err;
+  it.grid = p->d_grid;
+  it.lines = (float2*)lines;
+  it.adj_in = p->do_line_fft ? p->d_lines : (const float2*)lines;
+  it.adj_grid = p->d_grid_adj;
+  return it;
+}
+
+// The whole forward + adjoint of every item, recorded as one CUDA graph.
+// Plans that share N, K and J (and run the default exact-coefficient kernels)
+// form groups of up to kMaxGroupItems: their FFT passes and line DFTs run per
+// plan on the worker streams, but their interpolation is one launch per group
+// for the gather and one persistent launch for the spread, whose CTAs pull
+// (plan, subproblem) work items from a single counter.  Other plans run their
+// whole sequence on a worker stream.
 int capture(nufft3d_batch b, const void* const* vols, void* const* lines, void* const* vols_out,
             cudaStream_t launch_st) {
   const int n = (int)b->plans.size();
   cudaStream_t st = b->cap;
   const int ns = (int)b->streams.size();
-  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  free_capture_resources(b);
+  // groups
+  std::vector<std::vector<int>> groups;
+  std::vector<int> single;
+  {
+    std::vector<bool> used(n, false);
+    for (int i = 0; i < n; ++i) {
+      if (used[i]) continue;
+      const nufft3d_plan p = b->plans[i];
+      if (!b->grouping || !groupable(p)) {
+        single.push_back(i);
+        continue;
+      }
+      std::vector<int> grp{i};
+      used[i] = true;
+      for (int k = i + 1; k < n && (int)grp.size() < nufft::kMaxGroupItems; ++k) {
+        const nufft3d_plan q = b->plans[k];
+        if (!used[k] && groupable(q) && q->N == p->N && q->K == p->K && q->J == p->J) {
+          grp.push_back(k);
+          used[k] = true;
+        }
+      }
+      if (grp.size() == 1) {
+        single.push_back(i);
+      } else {
+        groups.push_back(grp);
+      }
+    }
+  }
+  // the group tables, uploaded before the capture
+  std::vector<nufft::GroupParams> gps(groups.size());
+  cudaError_t e = cudaSuccess;
+  for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
+    const auto& grp = groups[gi];
+    const nufft3d_plan p0 = b->plans[grp[0]];
+    nufft::GroupParams& gp = gps[gi];
+    gp = nufft::GroupParams{};
+    gp.rpoly = p0->rpoly;
+    gp.K = p0->K;
+    gp.nT = p0->nT;
+    gp.n_items = (int)grp.size();
+    std::vector<nufft::GroupItem> items;
+    int acc = 0;
+    for (size_t k = 0; k < grp.size(); ++k) {
+      gp.work_begin[k] = acc;
+      acc += b->plans[grp[k]]->n_sub;
+      items.push_back(group_item(b->plans[grp[k]], lines[grp[k]]));
+    }
+    gp.work_begin[grp.size()] = acc;
+    nufft::GroupItem* d = nullptr;
+    int* c = nullptr;
+    e = cudaMalloc((void**)&d, items.size() * sizeof(nufft::GroupItem));
+    if (e == cudaSuccess) b->d_items.push_back(d);
+    if (e == cudaSuccess) e = cudaMemcpy(d, items.data(), items.size() * sizeof(nufft::GroupItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c, sizeof(int));
+    if (e == cudaSuccess) b->d_counters.push_back(c);
+  }
+  if (e != cudaSuccess) return cuda_rc(e);
+  auto new_event = [&](cudaEvent_t* ev) {
+    cudaError_t r = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (r == cudaSuccess) b->evs.push_back(*ev);
+    return r;
+  };
+  e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_rc(e);
   int rc = NUFFT3D_OK;
   e = cudaEventRecord(b->fork, st);
   for (int s = 0; s < ns && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->streams[s], b->fork, 0);
-  // items dealt largest first to the least loaded worker stream (work taken as
-  // the evaluated points plus the grid cells), so the streams finish together
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
+  // the groups: item j on worker stream (g + j) mod ns, group launches on the
+  // stream of the group's first item
+  std::vector<double> load(ns, 0.0);
   auto work = [&](int i) {
     const nufft3d_plan p = b->plans[i];
     return (double)p->P_eval + (double)p->K * p->K * p->K;
   };
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work(a) > work(c); });
-  std::vector<double> load(ns, 0.0);
-  for (int q = 0; q < n && e == cudaSuccess && rc == NUFFT3D_OK; ++q) {
-    const int i = order[q];
+  for (size_t gi = 0; gi < groups.size() && e == cudaSuccess && rc == NUFFT3D_OK; ++gi) {
+    const auto& grp = groups[gi];
+    const int m = (int)grp.size();
+    std::vector<cudaStream_t> ws(m);
+    for (int j = 0; j < m; ++j) {
+      const int w = (int)((gi + (size_t)j) % (size_t)ns);
+      ws[j] = b->streams[w];
+      load[w] += work(grp[j]);
+    }
+    cudaStream_t gs = ws[0];
+    // stage 1: everything before the gather, per plan
+    for (int j = 0; j < m && rc == NUFFT3D_OK && e == cudaSuccess; ++j) {
+      rc = nufft::plan_forward_parts(b->plans[grp[j]], vols[grp[j]], lines[grp[j]], ws[j], 1);
+      cudaEvent_t ev;
+      if (rc == NUFFT3D_OK) e = new_event(&ev);
+      if (e == cudaSuccess && j > 0) e = cudaEventRecord(ev, ws[j]);
+      if (e == cudaSuccess && j > 0) e = cudaStreamWaitEvent(gs, ev, 0);
+    }
+    if (rc != NUFFT3D_OK || e != cudaSuccess) break;
+    e = nufft::launch_group_gather(gps[gi], b->d_items[gi], gs);
+    cudaEvent_t g1, g2;
+    if (e == cudaSuccess) e = new_event(&g1);
+    if (e == cudaSuccess) e = cudaEventRecord(g1, gs);
+    // stage 2: the forward line DFTs and the adjoint line DFTs, per plan
+    for (int j = 0; j < m && rc == NUFFT3D_OK && e == cudaSuccess; ++j) {
+      if (j > 0) e = cudaStreamWaitEvent(ws[j], g1, 0);
+      if (e != cudaSuccess) break;
+      const nufft3d_plan p = b->plans[grp[j]];
+      rc = nufft::plan_forward_parts(p, vols[grp[j]], lines[grp[j]], ws[j], 4);
+      if (rc == NUFFT3D_OK) rc = nufft::plan_adjoint_parts(p, lines[grp[j]], vols_out[grp[j]], ws[j], 1);
+      cudaEvent_t ev;
+      if (rc == NUFFT3D_OK) e = new_event(&ev);
+      if (e == cudaSuccess && j > 0) e = cudaEventRecord(ev, ws[j]);
+      if (e == cudaSuccess && j > 0) e = cudaStreamWaitEvent(gs, ev, 0);
+    }
+    if (rc != NUFFT3D_OK || e != cudaSuccess) break;
+    e = nufft::launch_group_spread(gps[gi], b->d_items[gi], b->d_counters[gi], gs);
+    if (e == cudaSuccess) e = new_event(&g2);
+    if (e == cudaSuccess) e = cudaEventRecord(g2, gs);
+    // stage 3: the inverse FFT passes, per plan
+    for (int j = 0; j < m && rc == NUFFT3D_OK && e == cudaSuccess; ++j) {
+      if (j > 0) e = cudaStreamWaitEvent(ws[j], g2, 0);
+      if (e == cudaSuccess)
+        rc = nufft::plan_adjoint_parts(b->plans[grp[j]], lines[grp[j]], vols_out[grp[j]], ws[j], 4);
+    }
+  }
+  // the other items: largest first to the least loaded worker stream (work
+  // taken as the evaluated points plus the grid cells)
+  std::stable_sort(single.begin(), single.end(), [&](int a, int c) { return work(a) > work(c); });
+  for (size_t q = 0; q < single.size() && e == cudaSuccess && rc == NUFFT3D_OK; ++q) {
+    const int i = single[q];
     const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     load[w] += work(i);
     cudaStream_t ws = b->streams[w];
@@ -176,6 +330,13 @@ int nufft3d_batch_forward_adjoint(nufft3d_batch b, const void* const* vols, void
     b->key = key;
   }
   return cuda_rc(cudaGraphLaunch(b->exec, st));
+}
+
+int nufft3d_batch_set_grouping(nufft3d_batch b, int on) {
+  if (!b) return NUFFT3D_ERR_ARG;
+  b->grouping = on != 0;
+  b->key.clear();
+  return NUFFT3D_OK;
 }
 
 int nufft3d_batch_invalidate(nufft3d_batch b) {

@@ -74,6 +74,33 @@ struct InterpGeom {
   const int* box = nullptr;           // per subproblem, the tile cells its taps can reach (TileBox), or null
 };
 
+// What decoding a point needs: the grid edge, the samples per line and the
+// lines' directions and radii (InterpGeom has the same members).
+struct PointGeom {
+  int K, M;
+  const float2* dir;
+  const float2* rad;
+};
+
+// One item of a group of plans that share N, K and J (and so the coefficient
+// polynomials, the phase table and the tiling), as the grouped interpolation
+// kernels of a batch see it.
+struct GroupItem {
+  PointGeom pg;
+  const uint2* sorted;
+  const int4* subs;
+  int n_subs;
+  int sub_begin;          // first global work item of this plan
+  const int4* sched;
+  const uint16_t* gslots;
+  const int* box;
+  int* err;
+  const float2* grid;     // forward grid (gather)
+  float2* lines;          // forward output (gather)
+  const float2* adj_in;   // adjoint line-DFT output (spread)
+  float2* adj_grid;       // adjoint grid (spread)
+};
+
 // The part of a subproblem's E^3 tile its taps can reach, from the plan:
 // origin and extent per axis (the whole tile without a plan box).
 struct TileBox {
@@ -143,6 +170,19 @@ bool v2_supported(int T, int J, int L);
 // enqueue a plan's forward / adjoint on a stream (no argument checks; used by batches)
 int plan_forward_enqueue(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st);
 int plan_adjoint_enqueue(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st);
+// parts of a call (bit 0: before the interpolation, 1: the interpolation, 2: after it)
+int plan_forward_parts(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st, int parts);
+int plan_adjoint_parts(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st, int parts);
+// one launch over a group of plans sharing N, K and J (the scheduled gather,
+// variant 10, and the real-weight spread, variant 7; complex64 grids)
+constexpr int kMaxGroupItems = 32;
+struct GroupParams {
+  RealPoly rpoly;
+  int K, nT, n_items;
+  int work_begin[kMaxGroupItems + 1];  // first work item of every plan, then the total
+};
+cudaError_t launch_group_gather(const GroupParams& gp, const GroupItem* items, cudaStream_t st);
+cudaError_t launch_group_spread(const GroupParams& gp, const GroupItem* items, int* counter, cudaStream_t st);
 bool v3_supported(int T, int J, int S);
 bool v3_two_copy_supported(int T, int J, int S);
 bool v8_supported(int T, int J, int S, int elem);

@@ -37,8 +37,8 @@ __device__ __forceinline__ void decode_point(const InterpGeom& g, uint32_t id, i
 // taps whose unwrapped index k lies outside [-K/2, K/2) (their grid cell holds
 // the phase of k -/+ K, which differs by a sign), and the point's phase
 // e^{i gamma (ux + uy + uz) / 2} = e^{i pi (ux + uy + uz) / K}.
-template <int J>
-__device__ __forceinline__ void decode_point_real(const InterpGeom& g, uint32_t id, int (&w0)[3], float (&f)[3],
+template <int J, class Geom>
+__device__ __forceinline__ void decode_point_real(const Geom& g, uint32_t id, int (&w0)[3], float (&f)[3],
                                                   int (&flip)[3], float2& phase) {
   const int l = (int)(id / (uint32_t)g.M);
   const int m = (int)(id - (uint32_t)l * (uint32_t)g.M);

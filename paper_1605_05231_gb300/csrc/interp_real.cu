@@ -22,6 +22,13 @@
 
 namespace nufft {
 
+// the plan of work item w of a group (the group's prefix table of work items)
+__device__ __forceinline__ int group_item_of(const GroupParams& gp, int w) {
+  int it = 0;
+  while (it + 1 < gp.n_items && w >= gp.work_begin[it + 1]) ++it;
+  return it;
+}
+
 // ---------------------------------------------------------------------------
 // gather 9
 // ---------------------------------------------------------------------------
@@ -201,10 +208,52 @@ struct V7SLayout {
   static constexpr size_t bytes = (nxt + 2 * sizeof(int) + 15) / 16 * 16;
 };
 
-__global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, const float2* __restrict__ in,
-                                                             const int4* __restrict__ subs, int n_subs,
-                                                             int* __restrict__ counter,
-                                                             float2* __restrict__ grid, float budget,
+// Where a spread CTA finds its subproblem: one plan, or a group of plans (as
+// for the scheduled gather).
+struct SpreadWork {
+  PointGeom pg;
+  const uint2* sorted;
+  int* err;
+  int4 sp;
+  const float2* in;
+  float2* grid;
+};
+
+struct GroupSpreadSrc {
+  GroupParams gp;
+  const GroupItem* items;
+  __device__ __forceinline__ const RealPoly& rpoly() const { return gp.rpoly; }
+  __device__ __forceinline__ void at(int w, SpreadWork& k) const {
+    const int it = group_item_of(gp, w);
+    const GroupItem& I = items[it];
+    k.pg = I.pg;
+    k.sorted = I.sorted;
+    k.err = I.err;
+    k.sp = I.subs[w - gp.work_begin[it]];
+    k.in = I.adj_in;
+    k.grid = I.adj_grid;
+  }
+};
+
+struct PlanSpreadSrc {
+  InterpGeom g;
+  const int4* subs;
+  const float2* in;
+  float2* grid;
+  __device__ __forceinline__ const RealPoly& rpoly() const { return g.rpoly; }
+  __device__ __forceinline__ void at(int w, SpreadWork& k) const {
+    k.pg = PointGeom{g.K, g.M, g.dir, g.rad};
+    k.sorted = g.sorted;
+    k.err = g.err;
+    k.sp = subs[w];
+    k.in = in;
+    k.grid = grid;
+  }
+};
+
+template <class Src>
+__global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(const Src src, int n_subs, int nT,
+                                                             int* __restrict__ counter, float budget,
                                                              float inv_budget) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using Lay = V7SLayout;
@@ -216,8 +265,6 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, cons
   unsigned* wmax = (unsigned*)(smem_raw + Lay::wmax);
   int* nxt = (int*)(smem_raw + Lay::nxt);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nT = g.nT, K = g.K;
-  const size_t KK = (size_t)K * K;
   for (int i = tid; i < E3; i += V7S_THREADS) {
     tre[i] = 0;
     tim[i] = 0;
@@ -229,16 +276,22 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, cons
   __syncthreads();
   int s = nxt[0], parity = 0;
   while (s < n_subs) {
-    const int4 sp = subs[s];
+    SpreadWork wk;
+    src.at(s, wk);
+    const int K = wk.pg.K;
+    const size_t KK = (size_t)K * K;
+    const float2* __restrict__ in = wk.in;
+    float2* __restrict__ grid = wk.grid;
+    const int4 sp = wk.sp;
     const int bx = sp.x % nT, by = (sp.x / nT) % nT, bz = sp.x / (nT * nT);
     const int x0 = bx * T, y0 = by * T, z0 = bz * T;
     unsigned bound = 0u;
     for (int i = tid; i < sp.z; i += V7S_THREADS) {
-      const uint2 ent = g.sorted[sp.y + i];
+      const uint2 ent = wk.sorted[sp.y + i];
       int w0[3], fm[3];
       float f[3];
       float2 ph;
-      decode_point_real<6>(g, ent.x, w0, f, fm, ph);
+      decode_point_real<6>(wk.pg, ent.x, w0, f, fm, ph);
       const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
       float4* c4 = (float4*)(coef + i * V7S_CSTRIDE);
       int off = 0;
@@ -248,9 +301,9 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, cons
         if (ent.y != kNoTwin) val = cadd(val, in[ent.y]);
         const float2 vp = cmulc(val, ph);  // e^{-i gamma sum u / 2} v
         float rx[6], ry[6], rz[6];
-        real_coeffs<6>(g.rpoly, f[0], fm[0], rx);
-        real_coeffs<6>(g.rpoly, f[1], fm[1], ry);
-        real_coeffs<6>(g.rpoly, f[2], fm[2], rz);
+        real_coeffs<6>(src.rpoly(), f[0], fm[0], rx);
+        real_coeffs<6>(src.rpoly(), f[1], fm[1], ry);
+        real_coeffs<6>(src.rpoly(), f[2], fm[2], rz);
         float mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
@@ -266,7 +319,7 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(InterpGeom g, cons
           c4[3 + q] = make_float4(vp.x * rz[2 * q], vp.y * rz[2 * q], vp.x * rz[2 * q + 1], vp.y * rz[2 * q + 1]);
         bound = max(bound, __float_as_uint(hypotf(val.x, val.y) * (mx * my * mz)));
       } else {
-        atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+        atomicExch(wk.err, (int)DEVCHK_TILE_RANGE);
 #pragma unroll
         for (int q = 0; q < 6; ++q) c4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -342,7 +395,7 @@ bool v7s_supported(int T, int J, int S) {
 cudaError_t launch_spread_real(const InterpGeom& g, const float2* in, const int4* subs, int n_subs, float2* grid,
                                cudaStream_t st) {
   if (!v7s_supported(g.T, g.J, g.S)) return cudaErrorInvalidValue;
-  auto f = k_spread_v7;
+  auto f = k_spread_v7<PlanSpreadSrc>;
   const size_t smem = V7SLayout::bytes;
   cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -354,7 +407,8 @@ cudaError_t launch_spread_real(const InterpGeom& g, const float2* in, const int4
   const float budget = ldexpf(1.f - 1.f / 1024.f, 22);  // at most 256 points per subproblem
   e = cudaMemsetAsync(g.counter + 1, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  f<<<num_sms() * per_sm, V7S_THREADS, smem, st>>>(g, in, subs, n_subs, g.counter + 1, grid, budget, 1.f / budget);
+  const PlanSpreadSrc src{g, subs, in, grid};
+  f<<<num_sms() * per_sm, V7S_THREADS, smem, st>>>(src, n_subs, g.nT, g.counter + 1, budget, 1.f / budget);
   return cudaGetLastError();
 }
 
@@ -374,22 +428,81 @@ __host__ __device__ inline size_t v10_bytes(int elem) {
   return ((size_t)E * (E * E + kGatherPitchCodes - 1) * elem + 15) / 16 * 16;
 }
 
-template <int J, typename G>
-__global__ void __launch_bounds__(V10_NT, 8) k_gather_v10(InterpGeom g, const typename G::T* __restrict__ grid,
-                                                          const int4* __restrict__ subs, float2* __restrict__ out) {
+// Where a scheduled-gather CTA finds its subproblem: one plan (work item w is
+// subproblem w), or a group of plans sharing N, K and J (work items numbered
+// across the plans; the plan of item w is found in the group's prefix table).
+struct GatherWork {
+  PointGeom pg;
+  const uint2* sorted;
+  int* err;
+  int4 sp, sc;
+  const int* box;
+  int box_i;
+  const uint16_t* gslots;
+  const void* grid;
+  float2* out;
+};
+
+struct PlanGatherSrc {
+  InterpGeom g;
+  const int4* subs;
+  const void* grid;
+  float2* out;
+  __device__ __forceinline__ const RealPoly& rpoly() const { return g.rpoly; }
+  __device__ __forceinline__ void at(int w, GatherWork& k) const {
+    k.pg = PointGeom{g.K, g.M, g.dir, g.rad};
+    k.sorted = g.sorted;
+    k.err = g.err;
+    k.sp = subs[w];
+    k.sc = g.sched[w];
+    k.box = g.box;
+    k.box_i = w;
+    k.gslots = g.gslots;
+    k.grid = grid;
+    k.out = out;
+  }
+};
+
+struct GroupGatherSrc {
+  GroupParams gp;
+  const GroupItem* items;
+  __device__ __forceinline__ const RealPoly& rpoly() const { return gp.rpoly; }
+  __device__ __forceinline__ void at(int w, GatherWork& k) const {
+    const int it = group_item_of(gp, w);
+    const GroupItem& I = items[it];
+    const int l = w - gp.work_begin[it];
+    k.pg = I.pg;
+    k.sorted = I.sorted;
+    k.err = I.err;
+    k.sp = I.subs[l];
+    k.sc = I.sched[l];
+    k.box = I.box;
+    k.box_i = l;
+    k.gslots = I.gslots;
+    k.grid = I.grid;
+    k.out = I.lines;
+  }
+};
+
+template <int J, typename G, class Src>
+__global__ void __launch_bounds__(V10_NT, 8) k_gather_v10(const Src src, int nT, float inv_scale_in,
+                                                          const float* __restrict__ lp_bound) {
   typedef typename G::T TT;
   constexpr int T = 8, NT = V10_NT, E = T + J - 1, E2 = E * E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TT* tile = (TT*)smem_raw;
-  const float inv_scale = lp_inv_scale<G>(g);
-  const int nT = g.nT, K = g.K;
-  const int4 sp = subs[blockIdx.x];
-  const int4 sc = g.sched[blockIdx.x];
+  float inv_scale = inv_scale_in;
+  if constexpr (G::kLowPrecision) inv_scale = 1.f / lp_scale_from_bound(*lp_bound);
+  GatherWork wk;
+  src.at(blockIdx.x, wk);
+  const int K = wk.pg.K;
+  const TT* __restrict__ grid = (const TT*)wk.grid;
+  const int4 sp = wk.sp, sc = wk.sc;
   const int PP = E2 + (sc.y >> 16), nslots = sc.y & 0xffff;
   const int x0 = (sp.x % nT) * T, y0 = ((sp.x / nT) % nT) * T, z0 = (sp.x / (nT * nT)) * T;
   // only the cells the subproblem's taps can reach are staged (the plan's box;
   // the quotients below are exact: (r + 1/2) / e is at least 1/(2e) from an integer)
-  const TileBox bx = unpack_box(g.box, blockIdx.x, E);
+  const TileBox bx = unpack_box(wk.box, wk.box_i, E);
   const float inv_ex = 1.f / (float)bx.ex, inv_ey = 1.f / (float)bx.ey;
   for (int r = threadIdx.x; r < bx.ex * bx.ey * bx.ez; r += NT) {
     const int row = (int)(((float)r + 0.5f) * inv_ex), ix = bx.ox + r - row * bx.ex;
@@ -401,24 +514,25 @@ __global__ void __launch_bounds__(V10_NT, 8) k_gather_v10(InterpGeom g, const ty
     tile[iz * PP + iy * E + ix] = grid[((size_t)gz * K + gy) * K + gx];
   }
   __syncthreads();
-  const uint16_t* slots = g.gslots + sc.x;
+  const uint16_t* slots = wk.gslots + sc.x;
+  float2* __restrict__ out = wk.out;
   for (int k = threadIdx.x; k < nslots; k += NT) {
     const int li = slots[k];
     if (li == 0xffff) continue;
-    const uint2 ent = g.sorted[sp.y + li];
+    const uint2 ent = wk.sorted[sp.y + li];
     int w0[3], fm[3];
     float f[3];
     float2 ph;
-    decode_point_real<J>(g, ent.x, w0, f, fm, ph);
+    decode_point_real<J>(wk.pg, ent.x, w0, f, fm, ph);
     const int lx = w0[0] - x0, ly = w0[1] - y0, lz = w0[2] - z0;
     if ((unsigned)lx >= (unsigned)T || (unsigned)ly >= (unsigned)T || (unsigned)lz >= (unsigned)T) {
-      atomicExch(g.err, (int)DEVCHK_TILE_RANGE);
+      atomicExch(wk.err, (int)DEVCHK_TILE_RANGE);
       continue;
     }
     float rx[J], ry[J], rz[J];
-    real_coeffs<J>(g.rpoly, f[0], fm[0], rx);
-    real_coeffs<J>(g.rpoly, f[1], fm[1], ry);
-    real_coeffs<J>(g.rpoly, f[2], fm[2], rz);
+    real_coeffs<J>(src.rpoly(), f[0], fm[0], rx);
+    real_coeffs<J>(src.rpoly(), f[1], fm[1], ry);
+    real_coeffs<J>(src.rpoly(), f[2], fm[2], rz);
     float2 acc = make_float2(0.f, 0.f);
     const TT* base = tile + (lz * PP + ly * E + lx);
 #pragma unroll
@@ -444,12 +558,13 @@ __global__ void __launch_bounds__(V10_NT, 8) k_gather_v10(InterpGeom g, const ty
 template <int J, typename G>
 static cudaError_t launch_gather_v10_t(const InterpGeom& g, const void* grid, const int4* subs, int n_subs,
                                        float2* out, cudaStream_t st) {
-  auto f = k_gather_v10<J, G>;
+  auto f = k_gather_v10<J, G, PlanGatherSrc>;
   const size_t smem = v10_bytes<J>((int)sizeof(typename G::T));
   cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (n_subs == 0) return cudaSuccess;
-  f<<<n_subs, V10_NT, smem, st>>>(g, (const typename G::T*)grid, subs, out);
+  const PlanGatherSrc src{g, subs, grid, out};
+  f<<<n_subs, V10_NT, smem, st>>>(src, g.nT, 1.f, g.lp_bound);
   return cudaGetLastError();
 }
 
@@ -928,4 +1043,38 @@ cudaError_t launch_spread_sched(const InterpGeom& g, const float2* in, const int
   }
   return cudaErrorInvalidValue;
 }
+// ---------------------------------------------------------------------------
+// a group of plans (one batch launch each for the gather and the spread)
+// ---------------------------------------------------------------------------
+cudaError_t launch_group_gather(const GroupParams& gp, const GroupItem* items, cudaStream_t st) {
+  auto f = k_gather_v10<6, GridC64, GroupGatherSrc>;
+  const size_t smem = v10_bytes<6>(8);
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int total = gp.work_begin[gp.n_items];
+  if (total == 0) return cudaSuccess;
+  const GroupGatherSrc src{gp, items};
+  f<<<total, V10_NT, smem, st>>>(src, gp.nT, 1.f, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_spread(const GroupParams& gp, const GroupItem* items, int* counter, cudaStream_t st) {
+  auto f = k_spread_v7<GroupSpreadSrc>;
+  const size_t smem = V7SLayout::bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int total = gp.work_begin[gp.n_items];
+  if (total == 0) return cudaSuccess;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, V7S_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const float budget = ldexpf(1.f - 1.f / 1024.f, 22);  // at most 256 points per subproblem
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const GroupSpreadSrc src{gp, items};
+  f<<<num_sms() * per_sm, V7S_THREADS, smem, st>>>(src, total, gp.nT, counter, budget, 1.f / budget);
+  return cudaGetLastError();
+}
+
 }  // namespace nufft

@@ -899,19 +899,26 @@ nufft::ColPrune prune(const nufft3d_plan pl, int mode) {
   return p;
 }
 
-int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st) {
+// The stages of a call, in three parts (bit 0: before the interpolation, bit 1:
+// the interpolation, bit 2: after it); a batch runs the interpolation of a
+// group of plans as one launch and the other parts per plan.  Only a whole
+// call is timed.
+constexpr int kAllParts = 7;
+
+int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st, int parts = kAllParts) {
   const int N = pl->N, K = pl->K;
   const long long KK = (long long)K * K;
-  StageClock clk(pl->ev_fwd, pl->timing_slots, pl->fwd_calls, FWD_STAGES, st);
+  int no_slots = 0, no_calls = 0;
+  StageClock clk(pl->ev_fwd, parts == kAllParts ? pl->timing_slots : no_slots,
+                 parts == kAllParts ? pl->fwd_calls : no_calls, FWD_STAGES, st);
   CK(clk.mark(-1));
+  if (parts & 1) {
   if (pl->grid_dtype != NUFFT3D_GRID_C64)
     CK(nufft::launch_abs_bound(vol, pl->complex_volume, pl->d_s, N, pl->d_lp_bound, st));
   CK(nufft::launch_row_fwd(K, vol, pl->complex_volume, pl->d_bufA, pl->d_s, N, pl->d_twK, st));
   CK(clk.mark(0));
   CK(nufft::launch_col_fwd(K, pl->d_bufA, pl->d_bufB, N, N, K, (long long)N * K, K, KK, K, pl->d_twK, st));
   CK(clk.mark(1));
-  const void* grid = pl->d_grid;
-  float inv_scale = 1.f;
   nufft::ColPrune pzf = prune(pl, 2);
   if (nufft::gather_real(pl->gather_variant)) pzf.phase = pl->d_phase;
   if (pl->grid_dtype == NUFFT3D_GRID_C64) {
@@ -919,29 +926,35 @@ int forward_impl(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st)
   } else {
     CK(nufft::launch_col_fwd_lp(K, pl->grid_dtype, pl->d_bufB, pl->d_grid_lp, N, K, K, K, KK, K, KK, pl->d_twK,
                                 pl->d_lp_bound, st, pzf));
-    grid = pl->d_grid_lp;
   }
   CK(clk.mark(2));
-  InterpGeom g = geom(pl);
-  CK(nufft::launch_gather(g, pl->gather_variant, pl->grid_dtype, grid, inv_scale, pl->d_sub, pl->n_sub,
-                          (float2*)lines, st));
+  }
+  if (parts & 2) {
+    const void* grid = pl->grid_dtype == NUFFT3D_GRID_C64 ? (const void*)pl->d_grid : pl->d_grid_lp;
+    InterpGeom g = geom(pl);
+    CK(nufft::launch_gather(g, pl->gather_variant, pl->grid_dtype, grid, 1.f, pl->d_sub, pl->n_sub,
+                            (float2*)lines, st));
+  }
   CK(clk.mark(3));
-  if (pl->do_line_fft)
+  if ((parts & 4) && pl->do_line_fft)
     CK(nufft::launch_line(pl->M, true, (const float2*)lines, (float2*)lines, pl->D, pl->d_weight, pl->d_twM, st,
                           pl->d_line_weight));
   CK(clk.mark(4));
   return NUFFT3D_OK;
 }
 
-int adjoint_impl(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st) {
+int adjoint_impl(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st, int parts = kAllParts) {
   const int N = pl->N, K = pl->K;
   const long long KK = (long long)K * K;
   const float2* src = (const float2*)lines;
-  StageClock clk(pl->ev_adj, pl->timing_slots, pl->adj_calls, ADJ_STAGES, st);
+  int no_slots = 0, no_calls = 0;
+  StageClock clk(pl->ev_adj, parts == kAllParts ? pl->timing_slots : no_slots,
+                 parts == kAllParts ? pl->adj_calls : no_calls, ADJ_STAGES, st);
   CK(clk.mark(-1));
   if (pl->do_line_fft) {
-    CK(nufft::launch_line(pl->M, false, src, pl->d_lines, pl->D, pl->d_weight, pl->d_twM, st,
-                          pl->d_line_weight));
+    if (parts & 1)
+      CK(nufft::launch_line(pl->M, false, src, pl->d_lines, pl->D, pl->d_weight, pl->d_twM, st,
+                            pl->d_line_weight));
     src = pl->d_lines;
   }
   CK(clk.mark(0));
@@ -949,12 +962,15 @@ int adjoint_impl(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st)
   // cell it reads, and nothing outside the touched ball is ever written.  A
   // call that stopped between the spread and that pass left it dirty.
   float2* ag = pl->d_grid_adj ? pl->d_grid_adj : pl->d_grid;
-  if (pl->adj_dirty) CK(cudaMemsetAsync(ag, 0, (size_t)K * KK * sizeof(float2), st));
+  if ((parts & 1) && pl->adj_dirty) CK(cudaMemsetAsync(ag, 0, (size_t)K * KK * sizeof(float2), st));
   CK(clk.mark(1));
-  InterpGeom g = geom(pl);
-  pl->adj_dirty = true;
-  CK(nufft::launch_spread(g, pl->spread_variant, src, pl->d_sub, pl->n_sub, ag, st));
+  if (parts & 2) {
+    InterpGeom g = geom(pl);
+    pl->adj_dirty = true;
+    CK(nufft::launch_spread(g, pl->spread_variant, src, pl->d_sub, pl->n_sub, ag, st));
+  }
   CK(clk.mark(2));
+  if (!(parts & 4)) return NUFFT3D_OK;
   nufft::ColPrune pz = prune(pl, 2);
   pz.consume = 1;
   if (nufft::spread_real(pl->spread_variant)) pz.phase = pl->d_phase;
@@ -975,6 +991,14 @@ namespace nufft {
 int plan_forward_enqueue(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st) {
   pl->last_stream = st;
   return forward_impl(pl, vol, lines, st);
+}
+int plan_forward_parts(nufft3d_plan pl, const void* vol, void* lines, cudaStream_t st, int parts) {
+  pl->last_stream = st;
+  return forward_impl(pl, vol, lines, st, parts);
+}
+int plan_adjoint_parts(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st, int parts) {
+  pl->last_stream = st;
+  return adjoint_impl(pl, lines, vol, st, parts);
 }
 int plan_adjoint_enqueue(nufft3d_plan pl, const void* lines, void* vol, cudaStream_t st) {
   pl->last_stream = st;

@@ -134,3 +134,67 @@ def test_batch_recaptures_on_new_buffers(cuda_lib):
     for o, o2 in zip(outs, outs2):
         assert _rel(o2, o) < 1e-6
     b.close()
+
+
+@pytest.fixture(scope="module")
+def grouped_run(cuda_lib):
+    """Nine items (three each at 64^3, 128^3, 192^3) with exact coefficients:
+    the default kernels, so the items of each size form one group whose gather
+    and spread are single launches over all three plans."""
+    import torch
+
+    works = [w for w in I.batched_workloads() if w.n == 64][:3] + \
+            [w for w in I.batched_workloads() if w.n == 128][:3] + \
+            [w for w in I.batched_workloads() if w.n == 192][:3]
+    items = [dict(n=w.n, dirs=w.directions(), m=w.m, k=w.k, j=w.j, exact_coeffs=True) for w in works]
+    b = cuda_lib.Batch(items)
+    assert all((p.info()["gather_variant"], p.info()["spread_variant"]) == (10, 7) for p in b.items)
+    vols = [torch.from_numpy(w.volume(np.float32)).cuda() for w in works]
+    lines = [torch.empty((p.n_dirs, p.m), dtype=torch.complex64, device="cuda") for p in b.items]
+    outs = [torch.empty_like(v) for v in vols]
+    b.forward_adjoint(vols, lines, outs)
+    b.forward_adjoint(vols, lines, outs)  # replay
+    torch.cuda.synchronize()
+    yield b, works, vols, lines, outs
+    b.close()
+
+
+def test_grouped_batch_matches_direct_path_and_ungrouped(cuda_lib, grouped_run):
+    import torch
+
+    b, works, vols, lines, outs = grouped_run
+    for p, v, l, o in zip(b.items, vols, lines, outs):
+        assert p.sync_status() == 0
+        ref_l = p.forward(v)
+        ref_o = p.adjoint(ref_l)
+        assert _rel(l, ref_l) < 1e-6
+        assert _rel(o, ref_o) < 1e-6
+    b.set_grouping(False)
+    lines2 = [torch.empty_like(l) for l in lines]
+    outs2 = [torch.empty_like(o) for o in outs]
+    b.forward_adjoint(vols, lines2, outs2)
+    torch.cuda.synchronize()
+    for l, o, l2, o2 in zip(lines, outs, lines2, outs2):
+        assert _rel(l2, l) < 1e-6 and _rel(o2, o) < 1e-6
+    b.set_grouping(True)
+
+
+def test_grouped_batch_items_match_oracle(cuda_lib, grouped_run):
+    """One item of each size: the grouped forward on 8 sampled lines, and the
+    adjoint of the grouped graph's own forward output checked through the
+    dot-product identity, against the FP64 oracle's exact-coefficient variant."""
+    import torch
+
+    b, works, vols, lines, outs = grouped_run
+    for i in (0, 3, 6):
+        w = works[i]
+        dirs = w.directions()
+        sel = np.sort(np.random.default_rng(3000 + i).choice(dirs.shape[0], 8, replace=False))
+        op = O.OraclePlan(w.n, w.k, w.j, 0, dirs, w.m)
+        ref = O.nufft_forward(vols[i].cpu().numpy().astype(np.float64), op, lines=sel)
+        assert O.rel_l2(lines[i].cpu().numpy()[sel], ref) < TOL, i
+        # <A x, A x> = <x, A^H A x>: the graph's adjoint of its own forward
+        Ax = lines[i].to(torch.complex128)
+        lhs = float(torch.sum(torch.abs(Ax) ** 2))
+        rhs = float(torch.sum(outs[i].to(torch.float64) * vols[i].to(torch.float64)))
+        assert abs(lhs - rhs) / lhs < 1e-6, (i, lhs, rhs)
