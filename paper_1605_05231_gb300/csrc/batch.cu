@@ -13,7 +13,7 @@
 
 struct nufft3d_batch_s {
   std::vector<nufft3d_plan> plans;
-  bool grouping = true;                   // grouped interpolation launches (see capture)
+  bool grouping = false;                  // grouped interpolation launches (see capture)
   std::vector<nufft::GroupItem*> d_items;  // per group of the last capture, device copies
   std::vector<int*> d_counters;           // per group: the spread's work counter
   std::vector<cudaEvent_t> evs;           // events of the last capture
@@ -21,6 +21,8 @@ struct nufft3d_batch_s {
   cudaStream_t cap = nullptr;  // capture origin (the legacy stream cannot be captured)
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> join;
+  std::vector<cudaStream_t> gstreams;  // one per group of the last capture (kept for reuse)
+  std::vector<cudaEvent_t> gjoin;
   cudaEvent_t fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -51,6 +53,8 @@ void free_batch(nufft3d_batch b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (cudaStream_t s : b->gstreams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->gjoin) cudaEventDestroy(e);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -151,6 +155,15 @@ int capture(nufft3d_batch b, const void* const* vols, void* const* lines, void* 
     if (e == cudaSuccess) e = cudaMalloc((void**)&c, sizeof(int));
     if (e == cudaSuccess) b->d_counters.push_back(c);
   }
+  // a stream and a join event per group, made before the capture
+  for (size_t gi = b->gstreams.size(); gi < groups.size() && e == cudaSuccess; ++gi) {
+    cudaStream_t gst;
+    cudaEvent_t gev;
+    e = cudaStreamCreateWithFlags(&gst, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->gstreams.push_back(gst);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&gev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->gjoin.push_back(gev);
+  }
   if (e != cudaSuccess) return cuda_rc(e);
   auto new_event = [&](cudaEvent_t* ev) {
     cudaError_t r = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
@@ -162,58 +175,76 @@ int capture(nufft3d_batch b, const void* const* vols, void* const* lines, void* 
   int rc = NUFFT3D_OK;
   e = cudaEventRecord(b->fork, st);
   for (int s = 0; s < ns && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->streams[s], b->fork, 0);
-  // the groups: item j on worker stream (g + j) mod ns, group launches on the
-  // stream of the group's first item
+  // the groups, stage by stage across groups (so that no group's later stage
+  // sits in a worker stream's queue ahead of another group's earlier stage):
+  // items dealt round-robin over the worker streams, each group's two
+  // interpolation launches on a group stream of its own
   std::vector<double> load(ns, 0.0);
   auto work = [&](int i) {
     const nufft3d_plan p = b->plans[i];
     return (double)p->P_eval + (double)p->K * p->K * p->K;
   };
-  for (size_t gi = 0; gi < groups.size() && e == cudaSuccess && rc == NUFFT3D_OK; ++gi) {
+  const size_t ng = groups.size();
+  for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi) e = cudaStreamWaitEvent(b->gstreams[gi], b->fork, 0);
+  std::vector<std::vector<cudaStream_t>> ws(ng);
+  {
+    int next = 0;
+    for (size_t gi = 0; gi < ng; ++gi)
+      for (int i : groups[gi]) {
+        ws[gi].push_back(b->streams[next]);
+        load[next] += work(i);
+        next = (next + 1) % ns;
+      }
+  }
+  // each group's per-item stage `part` on the worker streams, then the group
+  // stream waits for all of them
+  auto stage = [&](size_t gi, cudaEvent_t after, auto&& body) {
     const auto& grp = groups[gi];
-    const int m = (int)grp.size();
-    std::vector<cudaStream_t> ws(m);
-    for (int j = 0; j < m; ++j) {
-      const int w = (int)((gi + (size_t)j) % (size_t)ns);
-      ws[j] = b->streams[w];
-      load[w] += work(grp[j]);
-    }
-    cudaStream_t gs = ws[0];
-    // stage 1: everything before the gather, per plan
-    for (int j = 0; j < m && rc == NUFFT3D_OK && e == cudaSuccess; ++j) {
-      rc = nufft::plan_forward_parts(b->plans[grp[j]], vols[grp[j]], lines[grp[j]], ws[j], 1);
-      cudaEvent_t ev;
-      if (rc == NUFFT3D_OK) e = new_event(&ev);
-      if (e == cudaSuccess && j > 0) e = cudaEventRecord(ev, ws[j]);
-      if (e == cudaSuccess && j > 0) e = cudaStreamWaitEvent(gs, ev, 0);
-    }
-    if (rc != NUFFT3D_OK || e != cudaSuccess) break;
-    e = nufft::launch_group_gather(gps[gi], b->d_items[gi], gs);
-    cudaEvent_t g1, g2;
-    if (e == cudaSuccess) e = new_event(&g1);
-    if (e == cudaSuccess) e = cudaEventRecord(g1, gs);
-    // stage 2: the forward line DFTs and the adjoint line DFTs, per plan
-    for (int j = 0; j < m && rc == NUFFT3D_OK && e == cudaSuccess; ++j) {
-      if (j > 0) e = cudaStreamWaitEvent(ws[j], g1, 0);
+    for (size_t j = 0; j < grp.size() && rc == NUFFT3D_OK && e == cudaSuccess; ++j) {
+      if (after) e = cudaStreamWaitEvent(ws[gi][j], after, 0);
       if (e != cudaSuccess) break;
-      const nufft3d_plan p = b->plans[grp[j]];
-      rc = nufft::plan_forward_parts(p, vols[grp[j]], lines[grp[j]], ws[j], 4);
-      if (rc == NUFFT3D_OK) rc = nufft::plan_adjoint_parts(p, lines[grp[j]], vols_out[grp[j]], ws[j], 1);
+      rc = body(b->plans[grp[j]], grp[j], ws[gi][j]);
       cudaEvent_t ev;
       if (rc == NUFFT3D_OK) e = new_event(&ev);
-      if (e == cudaSuccess && j > 0) e = cudaEventRecord(ev, ws[j]);
-      if (e == cudaSuccess && j > 0) e = cudaStreamWaitEvent(gs, ev, 0);
+      if (e == cudaSuccess) e = cudaEventRecord(ev, ws[gi][j]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->gstreams[gi], ev, 0);
     }
-    if (rc != NUFFT3D_OK || e != cudaSuccess) break;
-    e = nufft::launch_group_spread(gps[gi], b->d_items[gi], b->d_counters[gi], gs);
-    if (e == cudaSuccess) e = new_event(&g2);
-    if (e == cudaSuccess) e = cudaEventRecord(g2, gs);
-    // stage 3: the inverse FFT passes, per plan
-    for (int j = 0; j < m && rc == NUFFT3D_OK && e == cudaSuccess; ++j) {
-      if (j > 0) e = cudaStreamWaitEvent(ws[j], g2, 0);
+  };
+  std::vector<cudaEvent_t> g1(ng, nullptr), g2(ng, nullptr);
+  // stage 1: everything before the gather, per plan
+  for (size_t gi = 0; gi < ng; ++gi)
+    stage(gi, nullptr, [&](nufft3d_plan p, int i, cudaStream_t w) {
+      return nufft::plan_forward_parts(p, vols[i], lines[i], w, 1);
+    });
+  for (size_t gi = 0; gi < ng && e == cudaSuccess && rc == NUFFT3D_OK; ++gi) {
+    e = nufft::launch_group_gather(gps[gi], b->d_items[gi], b->gstreams[gi]);
+    if (e == cudaSuccess) e = new_event(&g1[gi]);
+    if (e == cudaSuccess) e = cudaEventRecord(g1[gi], b->gstreams[gi]);
+  }
+  // stage 2: the forward line DFTs and the adjoint line DFTs, per plan
+  for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi)
+    stage(gi, g1[gi], [&](nufft3d_plan p, int i, cudaStream_t w) {
+      int r = nufft::plan_forward_parts(p, vols[i], lines[i], w, 4);
+      if (r == NUFFT3D_OK) r = nufft::plan_adjoint_parts(p, lines[i], vols_out[i], w, 1);
+      return r;
+    });
+  for (size_t gi = 0; gi < ng && e == cudaSuccess && rc == NUFFT3D_OK; ++gi) {
+    e = nufft::launch_group_spread(gps[gi], b->d_items[gi], b->d_counters[gi], b->gstreams[gi]);
+    if (e == cudaSuccess) e = new_event(&g2[gi]);
+    if (e == cudaSuccess) e = cudaEventRecord(g2[gi], b->gstreams[gi]);
+  }
+  // stage 3: the inverse FFT passes, per plan
+  for (size_t gi = 0; gi < ng && e == cudaSuccess && rc == NUFFT3D_OK; ++gi) {
+    const auto& grp = groups[gi];
+    for (size_t j = 0; j < grp.size() && rc == NUFFT3D_OK && e == cudaSuccess; ++j) {
+      e = cudaStreamWaitEvent(ws[gi][j], g2[gi], 0);
       if (e == cudaSuccess)
-        rc = nufft::plan_adjoint_parts(b->plans[grp[j]], lines[grp[j]], vols_out[grp[j]], ws[j], 4);
+        rc = nufft::plan_adjoint_parts(b->plans[grp[j]], lines[grp[j]], vols_out[grp[j]], ws[gi][j], 4);
     }
+  }
+  for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+    e = cudaEventRecord(b->gjoin[gi], b->gstreams[gi]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->gjoin[gi], 0);
   }
   // the other items: largest first to the least loaded worker stream (work
   // taken as the evaluated points plus the grid cells)

@@ -138,9 +138,10 @@ def test_batch_recaptures_on_new_buffers(cuda_lib):
 
 @pytest.fixture(scope="module")
 def grouped_run(cuda_lib):
-    """Nine items (three each at 64^3, 128^3, 192^3) with exact coefficients:
-    the default kernels, so the items of each size form one group whose gather
-    and spread are single launches over all three plans."""
+    """Nine items (three each at 64^3, 128^3, 192^3) with exact coefficients
+    and grouping switched on: the default kernels, so the items of each size
+    form one group whose gather and spread are single launches over all three
+    plans."""
     import torch
 
     works = [w for w in I.batched_workloads() if w.n == 64][:3] + \
@@ -148,6 +149,7 @@ def grouped_run(cuda_lib):
             [w for w in I.batched_workloads() if w.n == 192][:3]
     items = [dict(n=w.n, dirs=w.directions(), m=w.m, k=w.k, j=w.j, exact_coeffs=True) for w in works]
     b = cuda_lib.Batch(items)
+    b.set_grouping(True)
     assert all((p.info()["gather_variant"], p.info()["spread_variant"]) == (10, 7) for p in b.items)
     vols = [torch.from_numpy(w.volume(np.float32)).cuda() for w in works]
     lines = [torch.empty((p.n_dirs, p.m), dtype=torch.complex64, device="cuda") for p in b.items]
