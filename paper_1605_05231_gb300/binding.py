@@ -39,6 +39,12 @@ EXPORTS = (
     "nufft3d_batch_destroy",
     "nufft3d_fourier_slice_weights",
     "nufft3d_polar_resample",
+    "nufft3d_polar_nufft_create",
+    "nufft3d_polar_nufft_info",
+    "nufft3d_polar_nufft_prepare",
+    "nufft3d_polar_nufft_gather",
+    "nufft3d_polar_nufft_resample",
+    "nufft3d_polar_nufft_destroy",
     "nufft3d_fp32_fma_peak",
     "nufft3d_host_pipeline_create",
     "nufft3d_host_forward_adjoint",
@@ -119,6 +125,12 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.nufft3d_plan_stage_times.argtypes = [vp, fp, fp, ip]
     lib.nufft3d_fourier_slice_weights.argtypes = [i, i, ctypes.c_double, i, fp, fp]
     lib.nufft3d_polar_resample.argtypes = [vp, i, i, i, vp, ctypes.c_longlong, i, vp, vp]
+    lib.nufft3d_polar_nufft_create.argtypes = [ctypes.POINTER(vp), i, i, i, i]
+    lib.nufft3d_polar_nufft_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+    lib.nufft3d_polar_nufft_prepare.argtypes = [vp, vp, vp]
+    lib.nufft3d_polar_nufft_gather.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
+    lib.nufft3d_polar_nufft_resample.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp]
+    lib.nufft3d_polar_nufft_destroy.argtypes = [vp]
     lib.nufft3d_fp32_fma_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ip, vp]
     lib.nufft3d_host_pipeline_create.argtypes = [vp, ctypes.POINTER(vp)]
     lib.nufft3d_host_forward_adjoint.argtypes = [vp, vp, vp, vp]
@@ -217,6 +229,85 @@ def polar_resample(grid, targets, J: int = 3, out=None, stream=None):
         ctypes.c_void_p(grid.data_ptr()), int(n_phi), int(n_theta), int(n_s), ctypes.c_void_p(targets.data_ptr()),
         int(n), int(J), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, grid.device)), "nufft3d_polar_resample")
     return out
+
+
+class PolarNufft:
+    """NUFFT-based resampling of the polar Radon grid (Eqs. 2.8-2.11;
+    nufft3d_polar_nufft_*): x~ ~= T_sparse F P F^-1 x on a (n_phi, n_theta,
+    n_s) complex64 grid, all axes periodic, K = 2n per axis, J taps.  The
+    plan holds the oversampled spectrum of the last prepared grid."""
+
+    def __init__(self, n_phi: int, n_theta: int, n_s: int, J: int = 6):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self.lib.nufft3d_polar_nufft_create(ctypes.byref(h), int(n_phi), int(n_theta), int(n_s), int(J)),
+               "nufft3d_polar_nufft_create")
+        self._handle = h
+        self.shape = (int(n_phi), int(n_theta), int(n_s))
+        self.J = int(J)
+
+    def info(self):
+        wb = ctypes.c_longlong(0)
+        fe = ctypes.c_double(0.0)
+        _check(self.lib.nufft3d_polar_nufft_info(self._handle, ctypes.byref(wb), ctypes.byref(fe)),
+               "nufft3d_polar_nufft_info")
+        return {"workspace_bytes": int(wb.value), "fit_error": float(fe.value)}
+
+    def _grid(self, grid):
+        import torch
+
+        if grid.dtype != torch.complex64 or tuple(grid.shape) != self.shape or not grid.is_cuda \
+                or not grid.is_contiguous():
+            raise ValueError(f"grid must be a contiguous complex64 CUDA tensor of shape {self.shape}")
+        return grid
+
+    def _targets_out(self, targets, out, device):
+        import torch
+
+        if targets.dtype != torch.float32 or targets.dim() != 2 or targets.shape[1] != 3 or not targets.is_cuda \
+                or not targets.is_contiguous() or targets.device != device:
+            raise ValueError("targets must be a contiguous float32 (P, 3) CUDA tensor on the grid's device")
+        n = targets.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.complex64, device=device)
+        elif out.dtype != torch.complex64 or tuple(out.shape) != (n,) or not out.is_contiguous() \
+                or out.device != device:
+            raise ValueError("out must be a contiguous complex64 (P,) tensor on the targets' device")
+        return n, out
+
+    def prepare(self, grid, stream=None):
+        """F P F^-1 of grid into the plan's oversampled spectrum."""
+        g = self._grid(grid)
+        _check(self.lib.nufft3d_polar_nufft_prepare(self._handle, ctypes.c_void_p(g.data_ptr()),
+                                                    _stream_ptr(stream, g.device)), "nufft3d_polar_nufft_prepare")
+
+    def gather(self, targets, out=None, stream=None):
+        """T_sparse of the last prepared spectrum at targets (P, 3) = (u_s, u_theta, u_phi)."""
+        n, out = self._targets_out(targets, out, targets.device)
+        _check(self.lib.nufft3d_polar_nufft_gather(self._handle, ctypes.c_void_p(targets.data_ptr()), int(n),
+                                                   ctypes.c_void_p(out.data_ptr()),
+                                                   _stream_ptr(stream, targets.device)), "nufft3d_polar_nufft_gather")
+        return out
+
+    def resample(self, grid, targets, out=None, stream=None):
+        g = self._grid(grid)
+        n, out = self._targets_out(targets, out, g.device)
+        _check(self.lib.nufft3d_polar_nufft_resample(self._handle, ctypes.c_void_p(g.data_ptr()),
+                                                     ctypes.c_void_p(targets.data_ptr()), int(n),
+                                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, g.device)),
+               "nufft3d_polar_nufft_resample")
+        return out
+
+    def close(self):
+        if getattr(self, "_handle", None):
+            self.lib.nufft3d_polar_nufft_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def workspace_bytes(**kw) -> int:

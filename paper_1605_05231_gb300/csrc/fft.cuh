@@ -1,4 +1,4 @@
-// Shared-memory Stockham FFT (mixed radix 2/3/4/8) for W interleaved columns.
+// Shared-memory Stockham FFT (mixed radix 2/3/4/5/8) for W interleaved columns.
 //
 // Element i of column c lives at buf[i * pitch + c]; all NT threads of the
 // CTA cooperate.  Each stage reads every butterfly input into registers,
@@ -16,11 +16,21 @@ namespace nufft {
 
 __host__ __device__ constexpr int c_ilog2(int x) { int r = 0; while (x > 1) { x >>= 1; ++r; } return r; }
 __host__ __device__ constexpr int c_count3(int L) { int c = 0; while (L % 3 == 0) { L /= 3; ++c; } return c; }
-__host__ __device__ constexpr int c_pow2part(int L) { while (L % 3 == 0) L /= 3; return L; }
-__host__ __device__ constexpr int fft_num_stages(int L) { return c_count3(L) + (c_ilog2(c_pow2part(L)) + 2) / 3; }
+__host__ __device__ constexpr int c_count5(int L) { int c = 0; while (L % 5 == 0) { L /= 5; ++c; } return c; }
+__host__ __device__ constexpr int c_pow2part(int L) {
+  while (L % 3 == 0) L /= 3;
+  while (L % 5 == 0) L /= 5;
+  return L;
+}
+// stages: the radix-5 ones first, then radix 3, then the power of two as one
+// radix-2 or radix-4 stage (if its exponent is not a multiple of 3) and radix 8
+__host__ __device__ constexpr int fft_num_stages(int L) {
+  return c_count5(L) + c_count3(L) + (c_ilog2(c_pow2part(L)) + 2) / 3;
+}
 __host__ __device__ constexpr int fft_stage_radix(int L, int s) {
-  return s < c_count3(L) ? 3
-         : ((c_ilog2(c_pow2part(L)) % 3 != 0 && s == c_count3(L))
+  return s < c_count5(L)                 ? 5
+         : s < c_count5(L) + c_count3(L) ? 3
+         : ((c_ilog2(c_pow2part(L)) % 3 != 0 && s == c_count5(L) + c_count3(L))
                 ? (c_ilog2(c_pow2part(L)) % 3 == 1 ? 2 : 4)
                 : 8);
 }
@@ -108,6 +118,33 @@ template <>
 __device__ __forceinline__ void small_dft<3, false>(float2* v) { dft3<false>(v); }
 template <>
 __device__ __forceinline__ void small_dft<3, true>(float2* v) { dft3<true>(v); }
+
+// 5-point DFT: with t1 = v1 + v4, t2 = v2 + v3, d1 = v1 - v4, d2 = v2 - v3,
+// y0 = v0 + t1 + t2, y1,4 = v0 + c1 t1 + c2 t2 -+ i (s1 d1 + s2 d2),
+// y2,3 = v0 + c2 t1 + c1 t2 -+ i (s2 d1 - s1 d2) (forward; the inverse swaps
+// the signs of i), c_k = cos(2 pi k / 5), s_k = sin(2 pi k / 5)
+template <bool INV>
+__device__ __forceinline__ void dft5(float2* v) {
+  const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+  const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+  const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  const float2 d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
+  const float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+  const float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+  const float2 b1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+  const float2 b2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+  // -i b (forward) or +i b (inverse)
+  const float2 m1 = mul_mi<INV>(b1), m2 = mul_mi<INV>(b2);
+  v[0] = cadd(v[0], cadd(t1, t2));
+  v[1] = cadd(a1, m1);
+  v[4] = csub(a1, m1);
+  v[2] = cadd(a2, m2);
+  v[3] = csub(a2, m2);
+}
+template <>
+__device__ __forceinline__ void small_dft<5, false>(float2* v) { dft5<false>(v); }
+template <>
+__device__ __forceinline__ void small_dft<5, true>(float2* v) { dft5<true>(v); }
 
 template <int L, int R, int NS, int W, int NT, bool INV>
 __device__ __forceinline__ void stockham_stage(float2* buf, int pitch, const float2* __restrict__ tw) {

@@ -163,3 +163,171 @@ def test_planted_unshifted_inverse_dft_fails(monkeypatch):
     out = R.exact_resample(x, t)
     monkeypatch.undo()
     assert np.max(np.abs(out - R.kernel_resample(x, t))) > 1e-2
+
+
+# ---- the library: argument checks without a GPU -----------------------------
+
+def test_library_refuses_unsupported_sizes():
+    import ctypes
+
+    from paper_1605_05231_gb300 import binding
+
+    lib = binding.load_library()
+    h = ctypes.c_void_p()
+    # sizes outside the supported set and odd J are refused before any device call
+    assert lib.nufft3d_polar_nufft_create(ctypes.byref(h), 11, 12, 16, 6) == -4
+    assert lib.nufft3d_polar_nufft_create(ctypes.byref(h), 10, 12, 1024, 6) == -4
+    assert lib.nufft3d_polar_nufft_create(ctypes.byref(h), 10, 12, 16, 5) == -4
+    assert lib.nufft3d_polar_nufft_create(ctypes.byref(h), 0, 12, 16, 6) == -1
+    assert lib.nufft3d_polar_nufft_create(None, 10, 12, 16, 6) == -1
+    assert lib.nufft3d_polar_nufft_destroy(None) == -1
+
+
+# ---- GPU parity -------------------------------------------------------------
+# The CUDA path computes in FP32 with the coefficients fitted to 1e-7; the
+# oracle follows the same steps in FP64 with exact coefficients, on the same
+# FP32 targets.  FP32 rounding through three n-point and three 2n-point FFTs
+# and the J^3 sum gives a few 1e-7 relative; the bar is 1e-5 rel-L2 and, per
+# element, 1e-5 of the output's RMS plus the oracle's own min-max bound where
+# the exact form is the reference.
+
+RTOL = 1e-5
+
+
+def _gpu_resample(cuda_lib, x, t, J=6, plan=None):
+    import torch
+
+    p = plan or cuda_lib.PolarNufft(*x.shape, J=J)
+    xd = torch.from_numpy(np.ascontiguousarray(x).astype(np.complex64)).cuda()
+    td = torch.from_numpy(np.ascontiguousarray(t).astype(np.float32)).cuda()
+    out = p.resample(xd, td)
+    torch.cuda.synchronize()
+    if plan is None:
+        p.close()
+    return out.cpu().numpy().astype(np.complex128)
+
+
+def _check(got, want):
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < RTOL, rel
+    rms = np.sqrt(np.mean(np.abs(want) ** 2))
+    assert np.max(np.abs(got - want)) < 10 * RTOL * rms
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [(10, 12, 16), (20, 24, 32), (40, 12, 10), (90, 64, 128)])
+@pytest.mark.parametrize("J", [4, 6, 8])
+def test_gpu_matches_oracle(cuda_lib, shape, J):
+    x = _grid(shape, 21)
+    t = _targets(3001, shape, 22).astype(np.float32).astype(np.float64)
+    got = _gpu_resample(cuda_lib, x, t, J)
+    _check(got, R.nufft_resample(x, t, J=J))
+
+
+@pytest.mark.gpu
+def test_gpu_against_exact_form_within_bound(cuda_lib):
+    shape = (20, 24, 32)
+    x = _grid(shape, 23)
+    t = _targets(2000, shape, 24).astype(np.float32).astype(np.float64)
+    got = _gpu_resample(cuda_lib, x, t)
+    exact = R.exact_resample(x, t)
+    bound = R.minmax_error_bound(x, t)
+    rms = np.sqrt(np.mean(np.abs(exact) ** 2))
+    assert np.all(np.abs(got - exact) <= bound + 2e-6 * rms)
+
+
+@pytest.mark.gpu
+def test_gpu_wrap_integer_and_far_targets(cuda_lib):
+    shape = (10, 12, 16)
+    x = _grid(shape, 25)
+    n_phi, n_theta, n_s = shape
+    ints = _integer_targets(shape)
+    # every axis periodic: targets one to three periods away, negative ones,
+    # and targets on the wrap boundary of the oversampled grid (u = n/2, n)
+    far = ints + np.array([3 * n_s, -2 * n_theta, 5 * n_phi], dtype=np.float64)
+    edge = np.array([[n_s / 2, n_theta / 2, n_phi / 2], [n_s, n_theta, n_phi], [-0.25, -0.5, -0.75],
+                     [n_s - 0.5, n_theta - 1e-3, n_phi - 0.5], [0.0, 0.0, 0.0]], dtype=np.float64)
+    t = np.concatenate([ints, far, edge]).astype(np.float32).astype(np.float64)
+    got = _gpu_resample(cuda_lib, x, t)
+    _check(got, R.nufft_resample(x, t))
+    # grid reproduction at the integer targets, within the min-max error
+    rms = np.sqrt(np.mean(np.abs(x) ** 2))
+    assert np.max(np.abs(got[:len(ints)] - _at(x, ints))) < 1e-4 * rms
+
+
+@pytest.mark.gpu
+def test_gpu_ragged_counts_nan_and_gather_reuse(cuda_lib):
+    import torch
+
+    shape = (20, 24, 32)
+    x = _grid(shape, 27)
+    p = cuda_lib.PolarNufft(*shape)
+    assert p.info()["fit_error"] < 1e-7
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    p.prepare(xd)
+    for n in (0, 1, 255, 257, 4099):
+        t = _targets(n, shape, 30 + n).astype(np.float32)
+        out = p.gather(torch.from_numpy(t).cuda().reshape(n, 3))
+        torch.cuda.synchronize()
+        if n:
+            _check(out.cpu().numpy().astype(np.complex128), R.nufft_resample(x, t.astype(np.float64)))
+    bad = torch.tensor([[np.nan, 1.0, 1.0], [1.0, np.inf, 1.0], [1.0, 1.0, 2.0 ** 23], [1.0, 2.0, 3.0]],
+                       dtype=torch.float32, device="cuda")
+    out = p.gather(bad).cpu().numpy()
+    assert np.all(np.isnan(out[:3].real)) and np.isfinite(out[3].real)
+    p.close()
+
+
+@pytest.mark.gpu
+def test_gpu_full_size_trigonometric_polynomial(cuda_lib):
+    """The 360 x 256 x 512 polar grid of the 256^3 workload holding a band-
+    limited trigonometric polynomial, resampled onto the grid shifted by
+    (0.37, 0.21, 0.43) cells: Eq. 2.8's exact value is the polynomial itself at
+    every one of the 47 M targets; the fast form stays within J = 6's min-max
+    error."""
+    import torch
+
+    from paper_1605_05231_gb300 import inputs as I
+
+    shape = (360, 256, 512)
+    m = (-31, 17, -180)
+    dev = torch.device("cuda")
+    kp = torch.arange(shape[0], device=dev, dtype=torch.float64)
+    kt = torch.arange(shape[1], device=dev, dtype=torch.float64)
+    ks = torch.arange(shape[2], device=dev, dtype=torch.float64)
+    ph = (m[0] * kp / shape[0])[:, None, None] + (m[1] * kt / shape[1])[None, :, None] + \
+        (m[2] * ks / shape[2])[None, None, :]
+    x = torch.exp(-2j * np.pi * ph).to(torch.complex64)
+    del ph
+    t = I.shifted_polar_targets(shape, (0.37, 0.21, 0.43), device=dev)
+    p = cuda_lib.PolarNufft(*shape)
+    out = p.resample(x, t)
+    td = t.double()
+    want = torch.exp(-2j * np.pi * (m[0] * td[:, 2] / shape[0] + m[1] * td[:, 1] / shape[1] +
+                                    m[2] * td[:, 0] / shape[2]))
+    err = (out.to(torch.complex128) - want).abs()
+    # per axis the min-max error of one frequency stays below 4.2e-6 at these
+    # m (J = 6, K = 2n); three axes and FP32 rounding stay below 2e-5
+    assert float(err.max()) < 2e-5
+    p.close()
+
+
+@pytest.mark.gpu
+def test_gpu_full_size_sampled_against_exact(cuda_lib):
+    """Seeded normal data on the full 360 x 256 x 512 grid: 48 sampled targets
+    of the shifted grid against Eq. 2.8 evaluated directly in FP64."""
+    import torch
+
+    from paper_1605_05231_gb300 import inputs as I
+
+    shape = (360, 256, 512)
+    x = _grid(shape, 31)
+    t = I.shifted_polar_targets(shape, (0.37, 0.21, 0.43))
+    idx = np.random.default_rng(32).choice(t.shape[0], 48, replace=False)
+    p = cuda_lib.PolarNufft(*shape)
+    out = p.resample(torch.from_numpy(x.astype(np.complex64)).cuda(), torch.from_numpy(t).cuda())
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+    p.close()
+    want = R.exact_resample(x, t[idx].astype(np.float64), chunk=8)
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < RTOL, rel
