@@ -1,0 +1,143 @@
+"""Per-view reverse Grangeat step (Sec. 2.2.2, Fig. 2.15; C3a-C3d of Sec. 2.4).
+
+CPU pins of the oracle (oracle/reverse_grangeat.py):
+- the radial DFT of a delta is the closed-form phasor, and the post-weights
+  scale the samples before it;
+- the 2D Fourier slice theorem: the radial DFT of the column sums (alpha = 0)
+  and row sums (alpha = pi/2) of an image equals its 2D DFT along the line;
+- the exact adjoint NUDFT equals the transpose of the 2D DFT computed by
+  np.fft.fft2 at on-grid frequencies;
+- the fast 2D NUFFT forward / adjoint satisfy the adjoint identity, and the
+  fast forward stays within the min-max bound of the exact type-2 sum;
+- the fast adjoint stays within the per-pixel bound of the exact adjoint,
+  for the whole C3a-C3d chain over several views;
+- planted mistakes (sine and cosine swapped, the DFT sign flipped) fail.
+"""
+import numpy as np
+import pytest
+
+from oracle import reverse_grangeat as G
+
+
+def _angles(L):
+    return np.pi * (np.arange(L) + 0.5) / L
+
+
+def test_radial_dft_of_a_delta_and_post_weights():
+    M = 24
+    L = 3
+    y = np.zeros((L, M))
+    w = np.full((L, M), 2.5)
+    t0 = [0, 7, 23]
+    for l, t in enumerate(t0):
+        y[l, t] = 1.0
+    Y = G.line_spectra(y, w)
+    q = np.arange(M) - M // 2
+    for l, t in enumerate(t0):
+        want = 2.5 * np.exp(-2j * np.pi * q * (t - M // 2) / M)
+        np.testing.assert_allclose(Y[l], want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,M", [(8, 16), (12, 12), (10, 32)])
+def test_fourier_slice_theorem_axis_aligned(N, M):
+    rng = np.random.default_rng(1)
+    f = rng.normal(size=(N, N))
+    n = np.arange(N) - N // 2
+    # offsets s = t - M/2 cover the centred box: t = n + M/2
+    R = np.zeros((2, M))
+    R[0, n + M // 2] = f.sum(axis=0)   # alpha = 0: lines x = s, column sums
+    R[1, n + M // 2] = f.sum(axis=1)   # alpha = pi/2: lines y = s, row sums
+    Y = G.line_spectra(R, np.ones_like(R))
+    rho = (np.arange(M) - M // 2) / M
+    # the 2D DFT (e^{-i}) of f on the two lines
+    Fx = np.exp(-2j * np.pi * np.outer(rho, n)) @ f.sum(axis=0)
+    Fy = np.exp(-2j * np.pi * np.outer(rho, n)) @ f.sum(axis=1)
+    np.testing.assert_allclose(Y[0], Fx, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(Y[1], Fy, rtol=0, atol=1e-10)
+    # and the full 2D DFT through the library routine, at on-grid rho = k/N
+    F = np.fft.fft2(np.fft.ifftshift(f))         # index k <-> frequency k/N
+    if M % N == 0:
+        k = (np.arange(M) - M // 2) * N // M
+        on = ((np.arange(M) - M // 2) * N) % M == 0
+        np.testing.assert_allclose(Y[0][on], F[0, k[on] % N], rtol=0, atol=1e-10)
+        np.testing.assert_allclose(Y[1][on], F[k[on] % N, 0], rtol=0, atol=1e-10)
+
+
+def test_exact_adjoint_is_transpose_of_fft2():
+    # angles 0 and pi/2 with M = N put every sample on the N-point DFT grid
+    N = 8
+    M = N
+    ang = np.array([0.0, np.pi / 2])
+    rng = np.random.default_rng(2)
+    Y = rng.normal(size=(2, M)) + 1j * rng.normal(size=(2, M))
+    x = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    z = G.adjoint_nudft_2d(Y, ang, N)
+    F = np.fft.fft2(np.fft.ifftshift(x))
+    k = np.arange(M) - M // 2
+    Ax = np.concatenate([F[0, k % N], F[k % N, 0]])   # (A x)_p = sum_n x[n] e^{-i omega_p . n}
+    np.testing.assert_allclose(np.vdot(Y.ravel(), Ax), np.vdot(z, x), rtol=1e-12)
+
+
+@pytest.mark.parametrize("N,J", [(12, 5), (16, 5), (16, 4)])
+def test_fast_forward_adjoint_identity_and_bound(N, J):
+    rng = np.random.default_rng(3)
+    L, M = 7, 2 * N
+    nu = G.Nufft2D(N, J)
+    u = G.polar_u(_angles(L), M, 2 * N)
+    x = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    Yp = rng.normal(size=L * M) + 1j * rng.normal(size=L * M)
+    fx = nu.forward(x, u)
+    np.testing.assert_allclose(np.vdot(Yp, fx), np.vdot(nu.adjoint(Yp, u), x), rtol=1e-12)
+    # the fast forward against the exact type-2 sum, within ||x|| E_p
+    n = np.arange(N) - N // 2
+    w = 2 * np.pi * u / (2 * N)
+    exact = np.einsum("pa,pb,ab->p", np.exp(-1j * np.outer(w[:, 1], n)), np.exp(-1j * np.outer(w[:, 0], n)), x)
+    assert np.all(np.abs(fx - exact) <= np.linalg.norm(x) * nu.error_bound(u) * (1 + 1e-6) + 1e-12)
+
+
+def test_chain_fast_within_pixel_bound():
+    rng = np.random.default_rng(4)
+    N, L, M, V = 16, 10, 32, 3
+    ang = _angles(L)
+    y = rng.normal(size=(V, L, M))
+    wpost = rng.uniform(0.5, 1.5, (V, L, M))
+    wpre = rng.uniform(0.5, 1.5, (V, N, N))
+    fast = G.reverse_grangeat(y, wpost, wpre, ang, N)
+    exact = G.reverse_grangeat(y, wpost, wpre, ang, N, exact=True)
+    for v in range(V):
+        Y = G.line_spectra(y[v], wpost[v])
+        bound = G.pixel_error_bound(Y, ang, N) * wpre[v].max()
+        assert np.max(np.abs(fast[v] - exact[v])) <= bound
+    # J = 5 with twofold oversampling: about 1e-4 relative at most
+    assert np.linalg.norm(fast - exact) / np.linalg.norm(exact) < 3e-4
+
+
+def test_planted_swapped_axes_fails(monkeypatch):
+    rng = np.random.default_rng(5)
+    N, L, M = 12, 9, 24
+    ang = _angles(L) * 0.7 + 0.1
+    y = rng.normal(size=(1, L, M))
+    ones = np.ones((1, L, M))
+    wpre = np.ones((1, N, N))
+    exact = G.reverse_grangeat(y, ones, wpre, ang, N, exact=True)
+    real_u = G.polar_u
+    monkeypatch.setattr(G, "polar_u", lambda a, M, K: real_u(a, M, K)[:, ::-1].copy())
+    fast = G.reverse_grangeat(y, ones, wpre, ang, N)
+    monkeypatch.undo()
+    assert np.linalg.norm(fast - exact) / np.linalg.norm(exact) > 1e-2
+
+
+def test_planted_dft_sign_fails(monkeypatch):
+    N, M = 8, 16
+    rng = np.random.default_rng(6)
+    f = rng.normal(size=(N, N))
+    n = np.arange(N) - N // 2
+    R = np.zeros((1, M))
+    R[0, n + M // 2] = f.sum(axis=0)
+    real = G.line_spectra
+    monkeypatch.setattr(G, "line_spectra", lambda y, w: np.conj(real(np.conj(y), w)))
+    Y = G.line_spectra(R + 0j, np.ones_like(R))
+    monkeypatch.undo()
+    rho = (np.arange(M) - M // 2) / M
+    Fx = np.exp(-2j * np.pi * np.outer(rho, n)) @ f.sum(axis=0)
+    assert np.max(np.abs(Y[0] - Fx)) > 1e-3
