@@ -895,7 +895,8 @@ NUFFT_RESAMPLE_SOURCES = ("polar_nufft.cu", "fft.cuh")
 def run_nufft_resample(args):
     """NUFFT-based resampling of the polar Radon grid (Eq. 2.11, J = 6, K = 2n
     per axis): the 360 x 256 x 512 grid of the 256^3 workload's plane integrals
-    onto the same grid shifted by (0.37, 0.21, 0.43) cells, 47,185,920 targets.
+    onto the same grid shifted by (0.37, 0.21, 0.43) cells, 47,185,920 targets
+    (nufft_resample128: the 180 x 128 x 256 grid of the 128^3 workload).
     A step is the whole method: the three axis passes (F P F^-1 into the
     720 x 512 x 1024 oversampled spectrum) and the gather."""
     import numpy as np
@@ -906,7 +907,9 @@ def run_nufft_resample(args):
 
     world, rank, local = dist_setup(args)
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = I.workload("full256")
+    # nufft_resample128: the 180 x 128 x 256 grid of the 128^3 workload (the
+    # small case for detailed profiles)
+    w = I.workload("mid128" if args.workload == "nufft_resample128" else "full256")
     shape = (w.n_az, w.n_pol, w.m)
     J = 6
     gen = torch.Generator(device=dev)
@@ -1023,10 +1026,132 @@ def run_nufft_resample(args):
                 "value": world * P / (ms * 1e-3), "unit": "pts/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "nufft_resample256", "grid": list(shape), "oversampled": K, "targets": P,
+                "config": {"workload": args.workload, "grid": list(shape), "oversampled": K, "targets": P,
                            "taps": J, "shift": list(RESAMPLE_SHIFT),
                            "parallelism": "single" if world == 1 else f"replicas{world}",
                            "l2": "working set per step >> L2 (3.0 GB spectrum, 1.5 GB intermediate)"},
+                "clocks": clk, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "gpu_launches": 4 * args.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+GRANGEAT_SOURCES = ("grangeat.cu", "fft.cuh")
+
+
+def run_grangeat(args):
+    """Per-view reverse Grangeat step (Sec. 2.2.2, C3a-C3d) for the paper's
+    128^3 experiment size: 256 views of 128 x 128 detector images, each view's
+    umbrella subset L = 256 lines (2N, as the count of C3c implies) of M = 256
+    samples, [5 5] taps, K = 256.  Seeded normal data, post-weights and pre-
+    weights uniform in [0.5, 1.5] (the Grangeat weights are inputs)."""
+    import numpy as np
+    import torch
+
+    from paper_1605_05231_gb300 import binding
+
+    world, rank, local = dist_setup(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N, V, L, M, J = 128, 256, 256, 256, 5
+    ang = np.pi * (np.arange(L) + 0.5) / L
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(13)
+    y = torch.complex(torch.randn((V, L, M), generator=gen, device=dev), torch.randn((V, L, M), generator=gen, device=dev))
+    wpost = 0.5 + torch.rand((V, L, M), generator=gen, device=dev)
+    wpre = 0.5 + torch.rand((V, N, N), generator=gen, device=dev)
+    out = torch.empty((V, N, N), dtype=torch.complex64, device=dev)
+    t0 = time.perf_counter()
+    g = binding.ReverseGrangeat(N, ang, M, J=J, max_views=V)
+    plan_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        g.run(y, wpost, wpre, out=out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.run(y, wpost, wpre, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(world, ev0.elapsed_time(ev1) / args.steps)
+    if not bool(torch.isfinite(out[:, :: 7, :: 7]).all()):
+        raise RuntimeError("non-finite detector images")
+    peaks = load_peaks()
+    K = 2 * N
+    P = L * M
+    # HBM bytes of the four kernels: lines read y (8) and w_post (4), write the
+    # spectra (8); the spread reads the sparse matrix (12 B per entry) and the
+    # spectra, writes K^2 cells; the two inverse passes read / write the grid,
+    # the cropped rows, w_pre and the images (8 B per complex64, 4 per float)
+    nbytes = V * P * (8 + 4 + 8) + P * J * J * 12 + V * (P * 8 + K * K * 8) + \
+        V * (K * K * 8 + N * K * 8) + V * (N * K * 8 + N * N * (4 + 8))
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    info = g.info()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "kernel": "k_view_lines, k_view_spread, k_view_ifft_y, k_view_ifft_x",
+            "peak_source": peaks["source"], "algorithmic_bytes": nbytes,
+            "basis": "every array of the chain read once and written once (whole step)",
+            "traffic": ncu_traffic("grangeat.step", GRANGEAT_SOURCES)}
+    e2e = None
+    if not args.no_e2e:
+        yh = y.cpu().pin_memory()
+        ph = wpost.cpu().pin_memory()
+        qh = wpre.cpu().pin_memory()
+        oh = torch.empty_like(out, device="cpu").pin_memory()
+        yd, pd, qd = torch.empty_like(y), torch.empty_like(wpost), torch.empty_like(wpre)
+        for _ in range(2):
+            yd.copy_(yh, non_blocking=True)
+            pd.copy_(ph, non_blocking=True)
+            qd.copy_(qh, non_blocking=True)
+            g.run(yd, pd, qd, out=out)
+            oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        n_e2e = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            yd.copy_(yh, non_blocking=True)
+            pd.copy_(ph, non_blocking=True)
+            qd.copy_(qh, non_blocking=True)
+            g.run(yd, pd, qd, out=out)
+            oh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(world, (time.perf_counter() - t0) * 1e3 / n_e2e)
+        e2e = {"value": world * V / (ms_e2e * 1e-3), "unit": "views/s", "h2d_bytes_per_step": V * P * 12 + V * N * N * 4,
+               "d2h_bytes_per_step": V * N * N * 8, "ms_per_step": ms_e2e,
+               "copies": "pinned host buffers, one stream: data and weights in, images out, every step"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import reverse_grangeat as R
+
+        nv = 2
+        yc = y[:nv].cpu().numpy().astype(np.complex128)
+        pc = wpost[:nv].cpu().numpy().astype(np.float64)
+        qc = wpre[:nv].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        R.reverse_grangeat(yc, pc, qc, ang, N, J=J)
+        t_s = time.perf_counter() - t0
+        cpu = {"value": nv / t_s, "unit": "views/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{nv} of {V} views, FP64 NumPy; {t_s:.1f} s of CPU work"}
+    g.close()
+    if rank == 0:
+        line = {"metric": "detector views/s, reverse Grangeat step (Sec. 2.2.2, C3a-C3d, [5 5] taps)",
+                "value": world * V / (ms * 1e-3), "unit": "views/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "grangeat128", "detector": [N, N], "views": V, "lines_per_view": L,
+                           "samples_per_line": M, "taps": J, "oversampled": K, "spread_nnz": info["nnz"],
+                           "plan_s": plan_s, "parallelism": "single" if world == 1 else f"replicas{world}",
+                           "l2": "working set per step above L2 (0.13 GB data, 0.08 GB weights, 0.13 GB spectra, 0.13 GB grid)"},
                 "clocks": clk, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "gpu_launches": 4 * args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -1044,8 +1169,10 @@ def main():
         return run_batch(args)
     if args.workload == "resample256":
         return run_resample(args)
-    if args.workload == "nufft_resample256":
+    if args.workload in ("nufft_resample256", "nufft_resample128"):
         return run_nufft_resample(args)
+    if args.workload == "grangeat128":
+        return run_grangeat(args)
     return run_ours(args)
 
 

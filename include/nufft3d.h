@@ -221,6 +221,44 @@ int nufft3d_polar_nufft_resample(nufft3d_polar_nufft p, const void* grid_dev, co
                                  long long n_targets, void* out_dev, void* cuda_stream);
 int nufft3d_polar_nufft_destroy(nufft3d_polar_nufft p);
 
+/* Per-view reverse Grangeat step (Sec. 2.2.2, Fig. 2.15; costs C3a-C3d of
+ * Sec. 2.4): every cone-beam view's umbrella subset of the (derivative of
+ * the) Radon data, L lines at detector-plane angles alpha_l with M samples at
+ * offsets t - M/2, to its N x N detector image:
+ *   C3a  y'[l][t] = w_post[l][t] y[l][t]
+ *   C3b  Y[l][q]  = sum_t y'[l][t] e^{-2 pi i (q - M/2)(t - M/2) / M}
+ *   C3c  z[n]     ~= sum_{l,q} Y[l][q] e^{+i omega_lq . n},
+ *        omega_lq = 2 pi (q - M/2)/M (cos alpha_l, sin alpha_l) = (omega_x,
+ *        omega_y), n = (n_y, n_x) centred in [-N/2, N/2)^2: the 2D min-max
+ *        NUFFT transpose (K = 2N, J x J taps; the paper uses [5 5])
+ *   C3d  out[n]   = w_pre[n] z[n]
+ * No ramp filter (the data are already derivatives).  The Grangeat weights
+ * are defined outside the paper, so both are the caller's.  Accuracy: the
+ * min-max error of J taps at K = 2N (about 1e-4 relative for J = 5, 1e-6 for
+ * J = 6), FP32 arithmetic.
+ *
+ * nufft3d_grangeat_create: N (detector edge) one of 16, 32, 64, 128, 256; M
+ *   one of 16, 32, 64, 128, 256, 512; 1 <= L <= 65535; 2 <= J <= 8; angles
+ *   host float64 [L] (finite; copied); max_views >= 1 sets the workspace:
+ *   (L M + 4 N^2 + 2 N^2) complex64 per view plus the sparse spread matrix
+ *   (L M J^2 entries, 12 bytes each).  The plan is built on the current
+ *   device; calls run there and restore the caller's device.  Returns
+ *   NUFFT3D_OK, NUFFT3D_ERR_ARG, NUFFT3D_ERR_UNSUPPORTED (another size, or a
+ *   coefficient fit above 1e-7), NUFFT3D_ERR_NOMEM or NUFFT3D_ERR_CUDA.
+ * nufft3d_grangeat_run: n_views views in chunks of max_views on cuda_stream:
+ *   y_dev complex64 [n_views][L][M], w_post_dev float32 [n_views][L][M],
+ *   w_pre_dev float32 [n_views][N][N] (all device, not modified), out_dev
+ *   complex64 [n_views][N][N] (device, not overlapping the inputs).
+ *   Asynchronous.  NUFFT3D_OK also for n_views = 0 with any pointers.
+ * nufft3d_grangeat_info: workspace bytes, entries of the spread matrix and
+ *   the coefficient fit error (any output may be NULL). */
+typedef struct nufft3d_grangeat_s* nufft3d_grangeat;
+int nufft3d_grangeat_create(nufft3d_grangeat* out, int N, int L, int M, int J, const double* angles, int max_views);
+int nufft3d_grangeat_info(nufft3d_grangeat g, long long* workspace_bytes, long long* nnz, double* fit_error);
+int nufft3d_grangeat_run(nufft3d_grangeat g, const void* y_dev, const float* w_post_dev, const float* w_pre_dev,
+                         int n_views, void* out_dev, void* cuda_stream);
+int nufft3d_grangeat_destroy(nufft3d_grangeat g);
+
 /* Weights that turn the adjoint into the direct (Fourier-slice) reconstruction
  * that inverts the image-to-Radon step (Sec. 2.3: ramp filtering in the
  * Fourier domain, then the NUFFT transpose; Sec. 1: the 3D parallel-beam

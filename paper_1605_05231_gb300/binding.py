@@ -45,6 +45,10 @@ EXPORTS = (
     "nufft3d_polar_nufft_gather",
     "nufft3d_polar_nufft_resample",
     "nufft3d_polar_nufft_destroy",
+    "nufft3d_grangeat_create",
+    "nufft3d_grangeat_info",
+    "nufft3d_grangeat_run",
+    "nufft3d_grangeat_destroy",
     "nufft3d_fp32_fma_peak",
     "nufft3d_host_pipeline_create",
     "nufft3d_host_forward_adjoint",
@@ -131,6 +135,11 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.nufft3d_polar_nufft_gather.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
     lib.nufft3d_polar_nufft_resample.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp]
     lib.nufft3d_polar_nufft_destroy.argtypes = [vp]
+    lib.nufft3d_grangeat_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, ctypes.POINTER(ctypes.c_double), i]
+    lib.nufft3d_grangeat_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_double)]
+    lib.nufft3d_grangeat_run.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    lib.nufft3d_grangeat_destroy.argtypes = [vp]
     lib.nufft3d_fp32_fma_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ip, vp]
     lib.nufft3d_host_pipeline_create.argtypes = [vp, ctypes.POINTER(vp)]
     lib.nufft3d_host_forward_adjoint.argtypes = [vp, vp, vp, vp]
@@ -301,6 +310,66 @@ class PolarNufft:
     def close(self):
         if getattr(self, "_handle", None):
             self.lib.nufft3d_polar_nufft_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ReverseGrangeat:
+    """Per-view reverse Grangeat step (Sec. 2.2.2, C3a-C3d; nufft3d_grangeat_*):
+    umbrella subsets y (V, L, M) with post-weights (V, L, M) and pre-weights
+    (V, N, N) to detector images (V, N, N), complex64, on the GPU."""
+
+    def __init__(self, N: int, angles, M: int, J: int = 5, max_views: int = 64):
+        self.lib = load_library()
+        a = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).reshape(-1))
+        h = ctypes.c_void_p()
+        _check(self.lib.nufft3d_grangeat_create(ctypes.byref(h), int(N), int(a.size), int(M), int(J),
+                                                a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(max_views)),
+               "nufft3d_grangeat_create")
+        self._handle = h
+        self.N, self.L, self.M, self.J = int(N), int(a.size), int(M), int(J)
+
+    def info(self):
+        wb = ctypes.c_longlong(0)
+        nnz = ctypes.c_longlong(0)
+        fe = ctypes.c_double(0.0)
+        _check(self.lib.nufft3d_grangeat_info(self._handle, ctypes.byref(wb), ctypes.byref(nnz), ctypes.byref(fe)),
+               "nufft3d_grangeat_info")
+        return {"workspace_bytes": int(wb.value), "nnz": int(nnz.value), "fit_error": float(fe.value)}
+
+    def run(self, y, w_post, w_pre, out=None, stream=None):
+        import torch
+
+        V = y.shape[0] if y.dim() == 3 else -1
+        if y.dtype != torch.complex64 or tuple(y.shape) != (V, self.L, self.M) or not y.is_cuda \
+                or not y.is_contiguous():
+            raise ValueError(f"y must be a contiguous complex64 CUDA tensor (V, {self.L}, {self.M})")
+        dev = y.device
+        if w_post.dtype != torch.float32 or tuple(w_post.shape) != (V, self.L, self.M) or \
+                not w_post.is_contiguous() or w_post.device != dev:
+            raise ValueError("w_post must be a contiguous float32 tensor shaped like y on its device")
+        if w_pre.dtype != torch.float32 or tuple(w_pre.shape) != (V, self.N, self.N) or \
+                not w_pre.is_contiguous() or w_pre.device != dev:
+            raise ValueError(f"w_pre must be a contiguous float32 (V, {self.N}, {self.N}) tensor on y's device")
+        if out is None:
+            out = torch.empty((V, self.N, self.N), dtype=torch.complex64, device=dev)
+        elif out.dtype != torch.complex64 or tuple(out.shape) != (V, self.N, self.N) or not out.is_contiguous() \
+                or out.device != dev:
+            raise ValueError(f"out must be a contiguous complex64 (V, {self.N}, {self.N}) tensor on y's device")
+        _check(self.lib.nufft3d_grangeat_run(self._handle, ctypes.c_void_p(y.data_ptr()),
+                                             ctypes.c_void_p(w_post.data_ptr()), ctypes.c_void_p(w_pre.data_ptr()),
+                                             int(V), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, dev)),
+               "nufft3d_grangeat_run")
+        return out
+
+    def close(self):
+        if getattr(self, "_handle", None):
+            self.lib.nufft3d_grangeat_destroy(self._handle)
             self._handle = None
 
     def __del__(self):

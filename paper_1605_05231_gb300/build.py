@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnufft3d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cu", "fft_passes.cu", "interp_gather.cu", "interp_spread.cu", "interp_tma.cu", "interp_real.cu", "noalloc.cu", "polar_nufft.cu",
+SOURCES = ["plan.cu", "fft_passes.cu", "interp_gather.cu", "interp_spread.cu", "interp_tma.cu", "interp_real.cu", "noalloc.cu", "polar_nufft.cu", "grangeat.cu",
            "batch.cu", "polar_resample.cu", "peak.cu",
            "host_pipeline.cu"]
 # nvcc's whole-TU code generation (--split-compile=0) schedules the gather

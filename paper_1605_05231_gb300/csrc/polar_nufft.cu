@@ -210,6 +210,24 @@ __device__ __forceinline__ void s_axis_pairs(float up, int K, const RealPoly& P,
   }
 }
 
+// Loads of the spectrum carry an L2 evict-last policy: each of its rows is
+// read again by the targets of the next two theta lines and, one phi slice
+// later, by the next two phi slices, while the targets and outputs stream
+// through once (evict-first loads and stores).
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ float4 ld_keep(const float4* p, unsigned long long pol) {
+  float4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
 // T_sparse: one thread per target; Y holds the phased oversampled spectrum
 // Y'[k_phi][k_theta][k_s] (K_phi x K_theta x K_s).
 template <int J>
@@ -218,13 +236,14 @@ __global__ void __launch_bounds__(PG_NT) k_polar_nufft_gather(const float2* __re
                                                               float2* __restrict__ out) {
   const long long stride = (long long)gridDim.x * PG_NT;
   const int Kp = g.K[0], Kt = g.K[1], Ks = g.K[2];
+  const unsigned long long keep = l2_evict_last_policy();
   for (long long i = (long long)blockIdx.x * PG_NT + threadIdx.x; i < n; i += stride) {
-    const float us = targets[3 * i], ut = targets[3 * i + 1], up = targets[3 * i + 2];
+    const float us = __ldcs(targets + 3 * i), ut = __ldcs(targets + 3 * i + 1), up = __ldcs(targets + 3 * i + 2);
     // coordinates must be finite and below 2^22 in magnitude (2 u exact, its
     // integer part and fraction exact in FP32)
     const float lim = 4194304.f;
     if (!(fabsf(us) < lim && fabsf(ut) < lim && fabsf(up) < lim)) {
-      out[i] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+      __stcs(out + i, make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000)));
       continue;
     }
     float wp[J], wt[J], ws[J + 2];
@@ -243,7 +262,7 @@ __global__ void __launch_bounds__(PG_NT) k_polar_nufft_gather(const float2* __re
         float2 r = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q <= J / 2; ++q) {
-          const float4 v = (q < J / 2 || last_pair) ? __ldg(row + (ps[q] >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 v = (q < J / 2 || last_pair) ? ld_keep(row + (ps[q] >> 1), keep) : make_float4(0.f, 0.f, 0.f, 0.f);
           r.x = fmaf(ws[2 * q], v.x, r.x);
           r.y = fmaf(ws[2 * q], v.y, r.y);
           r.x = fmaf(ws[2 * q + 1], v.z, r.x);
@@ -257,7 +276,7 @@ __global__ void __launch_bounds__(PG_NT) k_polar_nufft_gather(const float2* __re
     // e^{i pi (u_s / n_s + u_theta / n_theta + u_phi / n_phi)}
     float sn, cs;
     sincospif(us * g.inv_n[2] + ut * g.inv_n[1] + up * g.inv_n[0], &sn, &cs);
-    out[i] = make_float2(acc.x * cs - acc.y * sn, acc.x * sn + acc.y * cs);
+    __stcs(out + i, make_float2(acc.x * cs - acc.y * sn, acc.x * sn + acc.y * cs));
   }
 }
 
@@ -546,11 +565,10 @@ int nufft3d_polar_nufft_gather(nufft3d_polar_nufft p, const float* targets_dev, 
   if (!targets_dev || !out_dev) return NUFFT3D_ERR_ARG;
   nufft::DeviceGuard g(p->device);
   if (g.status != cudaSuccess) return rc_of(g.status);
-  int sms = 0;
-  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (e != cudaSuccess) return rc_of(e);
+  // one target per thread: blocks start in target order, so the spectrum rows
+  // in use at any time stay within a few phi slices (L2 reuse)
   const long long blocks = (n_targets + nufft::PG_NT - 1) / nufft::PG_NT;
-  const long long cap = (long long)sms * 16;
+  const long long cap = 1LL << 30;
   const int grid = (int)(blocks < cap ? blocks : cap);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   switch (p->J) {

@@ -104,12 +104,9 @@ __global__ void __launch_bounds__(POLAR_NT) k_polar_resample(const float2* __res
   }
 }
 
-static int polar_grid_cap() {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    sms = 1;
-  return sms * 16;  // eight resident CTAs of 256 threads per SM, two waves
-}
+// one target per thread: blocks start in target order, so the grid rows in
+// use at any time stay within a few phi slices and are re-read from L2
+static int polar_grid_cap() { return 1 << 30; }
 
 template <int J>
 static cudaError_t launch_polar_t(const float2* grid, int n_phi, int n_theta, int n_s, const float* targets,

@@ -141,3 +141,91 @@ def test_planted_dft_sign_fails(monkeypatch):
     rho = (np.arange(M) - M // 2) / M
     Fx = np.exp(-2j * np.pi * np.outer(rho, n)) @ f.sum(axis=0)
     assert np.max(np.abs(Y[0] - Fx)) > 1e-3
+
+
+# ---- the library --------------------------------------------------------------
+
+def test_library_refuses_bad_plans():
+    import ctypes
+
+    from paper_1605_05231_gb300 import binding
+
+    lib = binding.load_library()
+    h = ctypes.c_void_p()
+    a = (ctypes.c_double * 4)(0.1, 0.2, 0.3, 0.4)
+    assert lib.nufft3d_grangeat_create(ctypes.byref(h), 24, 4, 32, 5, a, 8) == -4     # N not supported
+    assert lib.nufft3d_grangeat_create(ctypes.byref(h), 16, 4, 48, 5, a, 8) == -4     # M not supported
+    assert lib.nufft3d_grangeat_create(ctypes.byref(h), 16, 4, 32, 9, a, 8) == -1     # J
+    assert lib.nufft3d_grangeat_create(ctypes.byref(h), 16, 4, 32, 5, None, 8) == -1  # angles
+    assert lib.nufft3d_grangeat_create(ctypes.byref(h), 16, 4, 32, 5, a, 0) == -1     # views
+    nan = (ctypes.c_double * 1)(float("nan"))
+    assert lib.nufft3d_grangeat_create(ctypes.byref(h), 16, 1, 32, 5, nan, 8) == -1
+    assert lib.nufft3d_grangeat_destroy(None) == -1
+
+
+# ---- GPU parity against the oracle ---------------------------------------------
+# FP32 with coefficients fitted to 1e-7 against the oracle's FP64 steps with
+# exact coefficients: rel-L2 <= 1e-5 per view.
+
+def _gpu_run(cuda_lib, N, ang, M, J, y, wpost, wpre, max_views=64):
+    import torch
+
+    g = cuda_lib.ReverseGrangeat(N, ang, M, J=J, max_views=max_views)
+    out = g.run(torch.from_numpy(y.astype(np.complex64)).cuda(), torch.from_numpy(wpost.astype(np.float32)).cuda(),
+                torch.from_numpy(wpre.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    info = g.info()
+    g.close()
+    return out.cpu().numpy().astype(np.complex128), info
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("N,L,M,J,V,chunk", [(16, 10, 32, 5, 3, 64), (32, 24, 64, 5, 19, 8), (16, 7, 16, 4, 5, 2),
+                                             (64, 40, 128, 6, 17, 16), (32, 64, 64, 5, 33, 33)])
+def test_gpu_matches_oracle(cuda_lib, N, L, M, J, V, chunk):
+    rng = np.random.default_rng(N + L + V)
+    ang = np.sort(rng.uniform(0, np.pi, L))
+    y = rng.normal(size=(V, L, M)) + 1j * rng.normal(size=(V, L, M))
+    wpost = rng.uniform(0.5, 1.5, (V, L, M))
+    wpre = rng.uniform(0.5, 1.5, (V, N, N))
+    got, info = _gpu_run(cuda_lib, N, ang, M, J, y, wpost, wpre, max_views=chunk)
+    assert info["nnz"] == L * M * J * J and info["fit_error"] < 1e-7
+    want = G.reverse_grangeat(y.astype(np.complex64).astype(np.complex128), wpost.astype(np.float32).astype(np.float64),
+                              wpre.astype(np.float32).astype(np.float64), ang, N, J=J)
+    for v in range(V):
+        rel = np.linalg.norm(got[v] - want[v]) / np.linalg.norm(want[v])
+        assert rel < 1e-5, (v, rel)
+
+
+@pytest.mark.gpu
+def test_gpu_axis_aligned_fourier_slice(cuda_lib):
+    """Column and row sums of a detector image as the two lines of a view:
+    the GPU chain equals the oracle's, whose C3b is pinned to the 2D DFT."""
+    N, M = 32, 64
+    rng = np.random.default_rng(40)
+    f = rng.normal(size=(2, N, N))
+    n = np.arange(N) - N // 2
+    y = np.zeros((2, 2, M), dtype=np.complex128)
+    for v in range(2):
+        y[v, 0, n + M // 2] = f[v].sum(axis=0)
+        y[v, 1, n + M // 2] = f[v].sum(axis=1)
+    ang = np.array([0.0, np.pi / 2])
+    ones_l = np.ones((2, 2, M))
+    ones_n = np.ones((2, N, N))
+    got, _ = _gpu_run(cuda_lib, N, ang, M, 6, y, ones_l, ones_n)
+    want = G.reverse_grangeat(y, ones_l, ones_n, ang, N, J=6)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-5
+
+
+@pytest.mark.gpu
+def test_gpu_zero_views_and_argument_checks(cuda_lib):
+    import torch
+
+    g = cuda_lib.ReverseGrangeat(16, np.linspace(0, 3, 5), 32, J=5, max_views=4)
+    z = torch.zeros((0, 5, 32), dtype=torch.complex64, device="cuda")
+    out = g.run(z, torch.zeros((0, 5, 32), device="cuda"), torch.zeros((0, 16, 16), device="cuda"))
+    assert out.shape == (0, 16, 16)
+    with pytest.raises(ValueError):
+        g.run(torch.zeros((1, 5, 31), dtype=torch.complex64, device="cuda"), torch.zeros((1, 5, 31), device="cuda"),
+              torch.zeros((1, 16, 16), device="cuda"))
+    g.close()
