@@ -36,6 +36,7 @@ namespace nufft {
 constexpr int GV_W = 16;    // views per CTA of the line and FFT kernels (128-byte segments)
 constexpr int GV_P = GV_W + 1;
 constexpr int GV_NT = 256;
+constexpr int GV_CHUNK = 8;  // loads a thread issues before its shared stores
 constexpr int GS_WARPS = 8;  // warps per spread CTA
 constexpr int GS_VPL = 8;    // views per lane per pass of the spread
 
@@ -60,16 +61,30 @@ __global__ void __launch_bounds__(GV_NT) k_view_lines(const float2* __restrict__
   extern __shared__ float2 buf[];
   const int l = blockIdx.x;
   const int vb = blockIdx.y * GV_W;
-  for (int e = threadIdx.x; e < GV_W * M; e += GV_NT) {
-    const int c = e / M, t = e - c * M;
-    const int v = vb + c;
-    float2 val = make_float2(0.f, 0.f);
-    if (v < Vc) {
-      const size_t i = ((size_t)v * L + l) * M + t;
-      const float w = __ldg(w_post + i) * ((t & 1) ? -1.f : 1.f);
-      val = cscale(__ldg(y + i), w);
+  // a thread's GV_CHUNK loads are in flight together before its shared stores
+  for (int base = threadIdx.x; base < GV_W * M; base += GV_CHUNK * GV_NT) {
+    float2 yv[GV_CHUNK];
+    float wv[GV_CHUNK];
+#pragma unroll
+    for (int u = 0; u < GV_CHUNK; ++u) {
+      const int e = base + u * GV_NT;
+      const int c = e / M, t = e - c * M;
+      yv[u] = make_float2(0.f, 0.f);
+      wv[u] = 0.f;
+      if (e < GV_W * M && vb + c < Vc) {
+        const size_t i = ((size_t)(vb + c) * L + l) * M + t;
+        yv[u] = __ldg(y + i);
+        wv[u] = __ldg(w_post + i);
+      }
     }
-    buf[t * GV_P + c] = val;
+#pragma unroll
+    for (int u = 0; u < GV_CHUNK; ++u) {
+      const int e = base + u * GV_NT;
+      if (e < GV_W * M) {
+        const int c = e / M, t = e - c * M;
+        buf[t * GV_P + c] = cscale(yv[u], (t & 1) ? -wv[u] : wv[u]);
+      }
+    }
   }
   __syncthreads();
   smem_fft<M, GV_W, GV_NT, false>(buf, GV_P, twM);
@@ -90,7 +105,7 @@ __global__ void __launch_bounds__(GV_NT) k_view_lines(const float2* __restrict__
 // coalesced load and hands them out by shuffles, so the spectrum loads of
 // consecutive entries are in flight together.  A cell of one item stores its
 // sums; the items of a longer row add theirs to the zeroed grid atomically.
-__global__ void __launch_bounds__(GS_WARPS * 32) k_view_spread(const int4* __restrict__ items, int n_items,
+__global__ void __launch_bounds__(GS_WARPS * 32, 2) k_view_spread(const int4* __restrict__ items, int n_items,
                                                                const int* __restrict__ col,
                                                                const float2* __restrict__ wt,
                                                                const float2* __restrict__ Yhat, int Vc,
@@ -111,7 +126,7 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_view_spread(const int4* __res
       float2 acc[GS_VPL];
 #pragma unroll
       for (int k = 0; k < GS_VPL; ++k) acc[k] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll 4
       for (int j = 0; j < n; ++j) {
         const int p = __shfl_sync(0xffffffffu, my_p, j);
         const float2 w = make_float2(__shfl_sync(0xffffffffu, my_w.x, j), __shfl_sync(0xffffffffu, my_w.y, j));
@@ -146,9 +161,19 @@ __global__ void __launch_bounds__(GV_NT) k_view_ifft_y(const float2* __restrict_
                                                        float2* __restrict__ H, const float2* __restrict__ twK) {
   extern __shared__ float2 buf[];
   const long long g0 = (long long)blockIdx.x * GV_W;
-  for (int e = threadIdx.x; e < GV_W * K; e += GV_NT) {
-    const int i = e / GV_W, c = e - i * GV_W;
-    buf[i * GV_P + c] = g0 + c < S ? __ldg(G + (size_t)i * S + (size_t)(g0 + c)) : make_float2(0.f, 0.f);
+  for (int base = threadIdx.x; base < GV_W * K; base += GV_CHUNK * GV_NT) {
+    float2 t[GV_CHUNK];
+#pragma unroll
+    for (int u = 0; u < GV_CHUNK; ++u) {
+      const int e = base + u * GV_NT;
+      const int i = e / GV_W, c = e - i * GV_W;
+      t[u] = (e < GV_W * K && g0 + c < S) ? __ldg(G + (size_t)i * S + (size_t)(g0 + c)) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < GV_CHUNK; ++u) {
+      const int e = base + u * GV_NT;
+      if (e < GV_W * K) buf[(e / GV_W) * GV_P + (e % GV_W)] = t[u];
+    }
   }
   __syncthreads();
   smem_fft<K, GV_W, GV_NT, true>(buf, GV_P, twK);
@@ -169,10 +194,19 @@ __global__ void __launch_bounds__(GV_NT) k_view_ifft_x(const float2* __restrict_
   extern __shared__ float2 buf[];
   const int vb = blockIdx.x * GV_W;
   const int r = blockIdx.y;
-  for (int e = threadIdx.x; e < GV_W * K; e += GV_NT) {
-    const int i = e / GV_W, c = e - i * GV_W;
-    const int v = vb + c;
-    buf[i * GV_P + c] = v < Vc ? __ldg(H + ((size_t)r * K + i) * Vc + v) : make_float2(0.f, 0.f);
+  for (int base = threadIdx.x; base < GV_W * K; base += GV_CHUNK * GV_NT) {
+    float2 t[GV_CHUNK];
+#pragma unroll
+    for (int u = 0; u < GV_CHUNK; ++u) {
+      const int e = base + u * GV_NT;
+      const int i = e / GV_W, c = e - i * GV_W;
+      t[u] = (e < GV_W * K && vb + c < Vc) ? __ldg(H + ((size_t)r * K + i) * Vc + vb + c) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < GV_CHUNK; ++u) {
+      const int e = base + u * GV_NT;
+      if (e < GV_W * K) buf[(e / GV_W) * GV_P + (e % GV_W)] = t[u];
+    }
   }
   __syncthreads();
   smem_fft<K, GV_W, GV_NT, true>(buf, GV_P, twK);
