@@ -146,6 +146,27 @@ __device__ __forceinline__ void small_dft<5, false>(float2* v) { dft5<false>(v);
 template <>
 __device__ __forceinline__ void small_dft<5, true>(float2* v) { dft5<true>(v); }
 
+// v[r] *= w^r (w = tw[b], conjugated for the inverse), r = 1 .. R-1.  w and
+// w^2 come from the table; the higher powers are products of two lower ones
+// (w^3 = w w^2, w^4 = w^2 w^2, w^5 = w^2 w^3, w^6 = w^3 w^3, w^7 = w^3 w^4),
+// at most two roundings deep, so a butterfly reads two table entries instead
+// of R - 1 (the table reads share the L1 path with the shared-memory
+// exchanges of the stage).
+template <int R, bool INV>
+__device__ __forceinline__ void apply_twiddles(float2* v, const float2* __restrict__ tw, int b) {
+  float2 w[R];
+  w[1] = __ldg(&tw[b]);
+  if (INV) w[1].y = -w[1].y;
+  if (R > 2) {
+    w[2] = __ldg(&tw[2 * b]);
+    if (INV) w[2].y = -w[2].y;
+  }
+#pragma unroll
+  for (int r = 3; r < R; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+}
+
 template <int L, int R, int NS, int W, int NT, bool INV>
 __device__ __forceinline__ void stockham_stage(float2* buf, int pitch, const float2* __restrict__ tw) {
   constexpr int NBF = W * (L / R);
@@ -167,14 +188,7 @@ __device__ __forceinline__ void stockham_stage(float2* buf, int pitch, const flo
     if (NBF % NT == 0 || b < NBF) {
       const int c = b % W, j = b / W;
       const int k = j % NS;
-      if (NS > 1) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(&tw[k * r * (L / (NS * R))]);
-          if (INV) w.y = -w.y;
-          v[p][r] = cmul(v[p][r], w);
-        }
-      }
+      if (NS > 1) apply_twiddles<R, INV>(v[p], tw, k * (L / (NS * R)));
       small_dft<R, INV>(v[p]);
       const int o = (j / NS) * NS * R + k;
 #pragma unroll
@@ -270,12 +284,7 @@ __device__ __forceinline__ void reg_fft(float2* buf, int pitch, const float2* __
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = buf[(j + r * NS) * pitch + c];
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(&tw[j * r]);
-          if (INV) w.y = -w.y;
-          v[r] = cmul(v[r], w);
-        }
+        apply_twiddles<R, INV>(v, tw, j);
         small_dft<R, INV>(v);
         hook.template last<R>(v, j, c);
 #pragma unroll
