@@ -251,7 +251,9 @@ int nufft3d_polar_nufft_destroy(nufft3d_polar_nufft p);
  *   complex64 [n_views][N][N] (device, not overlapping the inputs).
  *   Asynchronous.  NUFFT3D_OK also for n_views = 0 with any pointers.
  * nufft3d_grangeat_info: workspace bytes, entries of the spread matrix and
- *   the coefficient fit error (any output may be NULL). */
+ *   the coefficient fit error (any output may be NULL).
+ * The spread sums the cells near the origin (rows of more than 32 entries)
+ * with FP32 atomics, so repeated calls can differ in the last bits there. */
 typedef struct nufft3d_grangeat_s* nufft3d_grangeat;
 int nufft3d_grangeat_create(nufft3d_grangeat* out, int N, int L, int M, int J, const double* angles, int max_views);
 int nufft3d_grangeat_info(nufft3d_grangeat g, long long* workspace_bytes, long long* nnz, double* fit_error);
