@@ -186,16 +186,17 @@ cudaError_t launch_gather_real(const InterpGeom& g, int grid_dtype, const void* 
 
 // ---------------------------------------------------------------------------
 // spread 7
-//  phase 1: thread per point: decode, real weights, v' = e^{-i gamma (ux+uy+uz)/2} v,
-//           the z row folded into v' (v' rho_z), the bound |v| max|rx| max|ry| max|rz|;
+//  phase 1: thread per point: decode, real weights rho_x, rho_y, rho_z and
+//           v' = e^{-i gamma (ux+uy+uz)/2} v into the point's row, the bound
+//           |v| max|rx| max|ry| max|rz|;
 //           the CTA's largest bound fixes the subproblem's exponent;
 //  phase 2: warp w spreads points w, w + 6, ...: lane taps as in spread 6, each
-//           contribution w_xy (v' rho_z) with w_xy = rho_x rho_y real, rounded
+//           contribution rho_z (w_xy v') with w_xy = rho_x rho_y real, rounded
 //           to units by one FMA per plane;
 //  flush:   all 192 threads add the tile to the grid and clear it.
 // ---------------------------------------------------------------------------
 constexpr int V7S_WARPS = 6, V7S_THREADS = V7S_WARPS * 32, V7S_MAX_PTS = 256;
-constexpr int V7S_CSTRIDE = 24;  // floats per point: rx[6] ry[6] (v' rz)[6] as float2
+constexpr int V7S_CSTRIDE = 24;  // floats per point: rx[6] ry[6] rz[6] v' (re, im), 4 unused (16-byte rows)
 
 struct V7SLayout {
   static constexpr int E = 13, E3 = E * E * E;
@@ -314,9 +315,8 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(const Src src, int
         c4[0] = make_float4(rx[0], rx[1], rx[2], rx[3]);
         c4[1] = make_float4(rx[4], rx[5], ry[0], ry[1]);
         c4[2] = make_float4(ry[2], ry[3], ry[4], ry[5]);
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          c4[3 + q] = make_float4(vp.x * rz[2 * q], vp.y * rz[2 * q], vp.x * rz[2 * q + 1], vp.y * rz[2 * q + 1]);
+        c4[3] = make_float4(rz[0], rz[1], rz[2], rz[3]);
+        c4[4] = make_float4(rz[4], rz[5], vp.x, vp.y);
         bound = max(bound, __float_as_uint(hypotf(val.x, val.y) * (mx * my * mz)));
       } else {
         atomicExch(wk.err, (int)DEVCHK_TILE_RANGE);
@@ -341,21 +341,22 @@ __global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(const Src src, int
       for (int p = warp; p < sp.z; p += V7S_WARPS) {
         const int mo = mos[p];
         const float* cp = coef + p * V7S_CSTRIDE;
+        // the lane's column weight rho_x rho_y times v' (complex), then the
+        // six real rho_z of the z row: 24 bytes of broadcast row per point
         const float wxy = cp[ln.mjx] * cp[6 + ln.mjy] * sm;
-        const float4 z01 = *(const float4*)(cp + 12), z23 = *(const float4*)(cp + 16),
-                     z45 = *(const float4*)(cp + 20);
-        const float wo = cp[ln.ojx] * cp[6 + ln.ojy] * so;
-        const float2 zo = *(const float2*)(cp + 12 + 2 * ln.ojz);
-        const float zv[12] = {z01.x, z01.y, z01.z, z01.w, z23.x, z23.y, z23.z, z23.w, z45.x, z45.y, z45.z, z45.w};
+        const float4 za = *(const float4*)(cp + 12), zb = *(const float4*)(cp + 16);
+        const float rzv[6] = {za.x, za.y, za.z, za.w, zb.x, zb.y};
+        const float wre = wxy * zb.z, wim = wxy * zb.w;
+        const float wo = cp[ln.ojx] * cp[6 + ln.ojy] * cp[12 + ln.ojz] * so;
         int* re = tre + mo + main_off;
         int* im = tim + mo + main_off;
 #pragma unroll
         for (int jz = 0; jz < 6; ++jz) {
-          atomicAdd(re + jz * E2, round_unit1(wxy, zv[2 * jz]));
-          atomicAdd(im + jz * E2, round_unit1(wxy, zv[2 * jz + 1]));
+          atomicAdd(re + jz * E2, round_unit1(rzv[jz], wre));
+          atomicAdd(im + jz * E2, round_unit1(rzv[jz], wim));
         }
-        atomicAdd(tre + mo + ovf_off, round_unit1(wo, zo.x));
-        atomicAdd(tim + mo + ovf_off, round_unit1(wo, zo.y));
+        atomicAdd(tre + mo + ovf_off, round_unit1(wo, zb.z));
+        atomicAdd(tim + mo + ovf_off, round_unit1(wo, zb.w));
       }
     }
     __syncthreads();
