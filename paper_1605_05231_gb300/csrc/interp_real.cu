@@ -253,7 +253,7 @@ struct PlanSpreadSrc {
 };
 
 template <class Src>
-__global__ void __launch_bounds__(V7S_THREADS, 4) k_spread_v7(const Src src, int n_subs, int nT,
+__global__ void __launch_bounds__(V7S_THREADS, 5) k_spread_v7(const Src src, int n_subs, int nT,
                                                              int* __restrict__ counter, float budget,
                                                              float inv_budget) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
