@@ -486,7 +486,7 @@ struct GroupGatherSrc {
 };
 
 template <int J, typename G, class Src>
-__global__ void __launch_bounds__(V10_NT, 8) k_gather_v10(const Src src, int nT, float inv_scale_in,
+__global__ void __launch_bounds__(V10_NT, 9) k_gather_v10(const Src src, int nT, float inv_scale_in,
                                                           const float* __restrict__ lp_bound) {
   typedef typename G::T TT;
   constexpr int T = 8, NT = V10_NT, E = T + J - 1, E2 = E * E;
