@@ -626,6 +626,28 @@ def time_steps(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def batch_one_by_one(b, vols, lines, outs, steps, stream):
+    """The batch's items run one after another on one stream through each
+    plan's own forward and adjoint calls (same plans and tuned kernels, no
+    graph, no overlap between items), all of them and each problem size
+    alone: what the one-graph batch is compared with."""
+    def run(idx):
+        for i in idx:
+            b.items[i].forward(vols[i], out=lines[i])
+            b.items[i].adjoint(lines[i], out=outs[i])
+
+    every = list(range(len(b.items)))
+    ms = time_steps(lambda: run(every), steps, 3, stream)
+    by_size = {}
+    for n in sorted({p.n for p in b.items}):
+        idx = [i for i, p in enumerate(b.items) if p.n == n]
+        ms_n = time_steps(lambda: run(idx), steps, 2, stream)
+        pts = sum(b.items[i].n_points for i in idx)
+        by_size[f"{n}^3"] = {"items": len(idx), "ms_per_step": ms_n, "value": pts / (ms_n * 1e-3)}
+    pts = sum(p.n_points for p in b.items)
+    return {"value": pts / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "by_size": by_size}
+
+
 def run_extras(args, w, dirs, x, dev, steps=10):
     """The forms reported beside the FP32 headline, on the same 256^3 workload
     and coefficients: the bf16 and fp16 grid storage (throughput, and rel-L2
@@ -709,7 +731,8 @@ def run_extras(args, w, dirs, x, dev, steps=10):
     out["batch24"] = {"value": Pb / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
                       "points": Pb, "worst_item_fwd_rel_l2_vs_oracle_8_lines": worst, "plan_and_tune_s": plan_s,
                       "items": "8 each at 64^3, 128^3, 192^3, K = M = 2N, azimuths {90,180,360} x polar {64,128}",
-                      "autotune": {k: v["best"] for k, v in tuned.items()}}
+                      "autotune": {k: v["best"] for k, v in tuned.items()},
+                      "items_one_by_one": batch_one_by_one(b, vols, lns, outs, steps, stream)}
     b.close()
     torch.cuda.empty_cache()
     return out
@@ -758,6 +781,7 @@ def run_batch(args):
     for p in b.items:
         if p.sync_status() != 0:
             raise RuntimeError("device check failed")
+    seq = batch_one_by_one(b, vols, lines, outs, max(3, min(args.steps, 10)), stream)
     if rank == 0:
         line = {"metric": "nonuniform pts/s fwd+adj NUFFT, 24 mixed problems in one CUDA graph",
                 "value": world * P / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -766,7 +790,8 @@ def run_batch(args):
                 "config": {"workload": "batch24", "items": [f"{w.n}^3 {w.n_az}x{w.n_pol}x{w.m}" for w in works],
                            "coefficients": "exact min-max per point" if args.coeffs == "exact" else "table, L = 1024",
                            "points": P, "graph_launches_per_step": 1},
-                "clocks": clk, "autotune": {k: v["best"] for k, v in tuned.items()}, "plan_s": plan_s}
+                "clocks": clk, "autotune": {k: v["best"] for k, v in tuned.items()}, "plan_s": plan_s,
+                "items_one_by_one": seq}
         print(json.dumps(line), flush=True)
     b.close()
     return 0

@@ -59,7 +59,53 @@ __device__ __forceinline__ void sinc_axis(float u, int n, bool periodic, float (
   }
 }
 
+// One non-periodic axis with the J taps kept consecutive: they run from
+// base = clamp(k0, 0, n - J) (n >= J), and a tap outside k0 .. k0 + J - 1 gets
+// weight 0, so the same taps add the same terms as sinc_axis while the
+// addresses of the J taps differ by constants.
 template <int J>
+__device__ __forceinline__ int sinc_axis_contig(float u, int n, float (&w)[J]) {
+  const int k0 = (int)floorf(u - 0.5f * (float)J) + 1;
+  const int base = min(max(k0, 0), n - J);
+  const float su = sinpif(u);
+  constexpr float kInvPi = 0.318309886183790671537767526745f;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int kj = base + j;
+    const float t = u - (float)kj;
+    const float wj = t == 0.f ? 1.f : __fdividef(((kj & 1) ? -su : su) * kInvPi, t);
+    w[j] = (unsigned)(kj - k0) < (unsigned)J ? wj : 0.f;
+  }
+  return base;
+}
+
+// The periodic axis: the J taps wrapped into [0, n) (n >= J); the first by
+// one add when k0 is within a period of the range, else by a modulo.
+template <int J>
+__device__ __forceinline__ void sinc_axis_periodic(float u, int n, float (&w)[J], int (&k)[J]) {
+  const int k0 = (int)floorf(u - 0.5f * (float)J) + 1;
+  const float su = sinpif(u);
+  constexpr float kInvPi = 0.318309886183790671537767526745f;
+  int p0 = k0;
+  if ((unsigned)(k0 + n) < (unsigned)(2 * n)) {
+    p0 += k0 < 0 ? n : 0;
+  } else {
+    p0 = k0 % n;
+    p0 += p0 < 0 ? n : 0;
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int kj = k0 + j;
+    const float t = u - (float)kj;
+    w[j] = t == 0.f ? 1.f : __fdividef(((kj & 1) ? -su : su) * kInvPi, t);
+    const int idx = p0 + j;
+    k[j] = idx - (idx >= n ? n : 0);
+  }
+}
+
+// CONTIG: every axis has at least J cells and the grid fewer than 2^31 cells,
+// so taps are consecutive along s and theta and offsets fit in 32 bits.
+template <int J, bool CONTIG>
 __global__ void __launch_bounds__(POLAR_NT) k_polar_resample(const float2* __restrict__ grid, int n_phi, int n_theta,
                                                             int n_s, const float* __restrict__ targets,
                                                             long long n, float2* __restrict__ out) {
@@ -73,32 +119,59 @@ __global__ void __launch_bounds__(POLAR_NT) k_polar_resample(const float2* __res
       continue;
     }
     float ws[J], wt[J], wp[J];
-    int ks[J], kt[J], kp[J];
-    sinc_axis<J>(us, n_s, false, ws, ks);
-    sinc_axis<J>(ut, n_theta, false, wt, kt);
-    sinc_axis<J>(up, n_phi, true, wp, kp);
-    // the J^3 loads are independent and all in flight at once; targets that
-    // follow the grid share rows through L1 / L2
     float2 acc = make_float2(0.f, 0.f);
+    if constexpr (CONTIG) {
+      int kp[J];
+      const int bs = sinc_axis_contig<J>(us, n_s, ws);
+      const int bt = sinc_axis_contig<J>(ut, n_theta, wt);
+      sinc_axis_periodic<J>(up, n_phi, wp, kp);
+      // all J^3 loads independent and in flight at once; the J of a row at
+      // constant offsets from one address
 #pragma unroll
-    for (int a = 0; a < J; ++a) {
-      const float2* plane = grid + (size_t)kp[a] * n_theta * n_s;
-      float2 pacc = make_float2(0.f, 0.f);
+      for (int a = 0; a < J; ++a) {
+        float2 pacc = make_float2(0.f, 0.f);
+        const int plane = (kp[a] * n_theta + bt) * n_s + bs;
 #pragma unroll
-      for (int b = 0; b < J; ++b) {
-        const float2* row = plane + (size_t)kt[b] * n_s;
-        float2 racc = make_float2(0.f, 0.f);
+        for (int b = 0; b < J; ++b) {
+          const float2* row = grid + (plane + b * n_s);
+          float2 racc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < J; ++c) {
-          const float2 v = __ldg(row + ks[c]);
-          racc.x = fmaf(ws[c], v.x, racc.x);
-          racc.y = fmaf(ws[c], v.y, racc.y);
+          for (int c = 0; c < J; ++c) {
+            const float2 v = __ldg(row + c);
+            racc.x = fmaf(ws[c], v.x, racc.x);
+            racc.y = fmaf(ws[c], v.y, racc.y);
+          }
+          pacc.x = fmaf(wt[b], racc.x, pacc.x);
+          pacc.y = fmaf(wt[b], racc.y, pacc.y);
         }
-        pacc.x = fmaf(wt[b], racc.x, pacc.x);
-        pacc.y = fmaf(wt[b], racc.y, pacc.y);
+        acc.x = fmaf(wp[a], pacc.x, acc.x);
+        acc.y = fmaf(wp[a], pacc.y, acc.y);
       }
-      acc.x = fmaf(wp[a], pacc.x, acc.x);
-      acc.y = fmaf(wp[a], pacc.y, acc.y);
+    } else {
+      int ks[J], kt[J], kp[J];
+      sinc_axis<J>(us, n_s, false, ws, ks);
+      sinc_axis<J>(ut, n_theta, false, wt, kt);
+      sinc_axis<J>(up, n_phi, true, wp, kp);
+#pragma unroll
+      for (int a = 0; a < J; ++a) {
+        const float2* plane = grid + (size_t)kp[a] * n_theta * n_s;
+        float2 pacc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < J; ++b) {
+          const float2* row = plane + (size_t)kt[b] * n_s;
+          float2 racc = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int c = 0; c < J; ++c) {
+            const float2 v = __ldg(row + ks[c]);
+            racc.x = fmaf(ws[c], v.x, racc.x);
+            racc.y = fmaf(ws[c], v.y, racc.y);
+          }
+          pacc.x = fmaf(wt[b], racc.x, pacc.x);
+          pacc.y = fmaf(wt[b], racc.y, pacc.y);
+        }
+        acc.x = fmaf(wp[a], pacc.x, acc.x);
+        acc.y = fmaf(wp[a], pacc.y, acc.y);
+      }
     }
     out[i] = acc;
   }
@@ -113,8 +186,12 @@ static cudaError_t launch_polar_t(const float2* grid, int n_phi, int n_theta, in
                                   long long n, float2* out, cudaStream_t st) {
   const long long blocks = (n + POLAR_NT - 1) / POLAR_NT;
   const int cap = polar_grid_cap();
-  k_polar_resample<J><<<(int)(blocks < cap ? blocks : cap), POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets,
-                                                                             n, out);
+  const int nb = (int)(blocks < cap ? blocks : cap);
+  const bool contig = n_s >= J && n_theta >= J && n_phi >= J && (long long)n_phi * n_theta * n_s < (1LL << 31);
+  if (contig)
+    k_polar_resample<J, true><<<nb, POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets, n, out);
+  else
+    k_polar_resample<J, false><<<nb, POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets, n, out);
   return cudaGetLastError();
 }
 

@@ -144,6 +144,21 @@ def test_gpu_matches_oracle(cuda_lib, J, n):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("J", [3, 6])
+@pytest.mark.parametrize("shape", [(2, 9, 40), (12, 2, 40), (12, 9, 2), (1, 1, 1), (5, 4, 3)])
+def test_gpu_axes_shorter_than_the_taps(cuda_lib, J, shape):
+    """An axis with fewer cells than taps: the library keeps per-tap indices
+    there (taps wrap several times on the periodic azimuth, or fall off both
+    ends of theta / s), instead of the consecutive taps it uses when every
+    axis holds at least J cells."""
+    x = _grid(shape, 50 + J)
+    t = _targets(1000, shape, 60 + J).astype(np.float32)
+    got = _gpu(cuda_lib, x, t, J)
+    want = R.polar_sinc_resample(x.astype(np.complex64), t.astype(np.float64), J)
+    assert O.rel_l2(got, want) < TOL
+
+
+@pytest.mark.gpu
 def test_gpu_edges_wrap_and_integers(cuda_lib):
     shape = (16, 8, 32)
     x = _grid(shape, 30)
