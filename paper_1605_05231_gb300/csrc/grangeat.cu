@@ -38,7 +38,7 @@ constexpr int GV_P = GV_W + 1;
 constexpr int GV_NT = 256;
 constexpr int GV_CHUNK = 8;  // loads a thread issues before its shared stores
 constexpr int GS_WARPS = 8;  // warps per spread CTA
-constexpr int GS_VPL = 8;    // views per lane per pass of the spread
+constexpr int GS_VPL = 4;    // views per lane per pass of the spread (64 registers, four CTAs per SM)
 
 // acc + a b (complex)
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(GV_NT) k_view_lines(const float2* __restrict__
 // coalesced load and hands them out by shuffles, so the spectrum loads of
 // consecutive entries are in flight together.  A cell of one item stores its
 // sums; the items of a longer row add theirs to the zeroed grid atomically.
-__global__ void __launch_bounds__(GS_WARPS * 32, 2) k_view_spread(const int4* __restrict__ items, int n_items,
+__global__ void __launch_bounds__(GS_WARPS * 32, 4) k_view_spread(const int4* __restrict__ items, int n_items,
                                                                const int* __restrict__ col,
                                                                const float2* __restrict__ wt,
                                                                const float2* __restrict__ Yhat, int Vc,
