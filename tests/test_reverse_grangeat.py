@@ -198,6 +198,27 @@ def test_gpu_matches_oracle(cuda_lib, N, L, M, J, V, chunk):
 
 
 @pytest.mark.gpu
+def test_gpu_full_size_views_sampled(cuda_lib):
+    """The configuration bench.py times: 256 views of 128 x 128, L = M = 256,
+    [5 5] taps, all views in one chunk (max_views = 256); two of the views
+    (views are independent) against the oracle at rel-L2 <= 1e-5."""
+    N, V, L, M, J = 128, 256, 256, 256, 5
+    ang = np.pi * (np.arange(L) + 0.5) / L
+    rng = np.random.default_rng(70)
+    y = (rng.normal(size=(V, L, M)) + 1j * rng.normal(size=(V, L, M))).astype(np.complex64)
+    wpost = rng.uniform(0.5, 1.5, (V, L, M)).astype(np.float32)
+    wpre = rng.uniform(0.5, 1.5, (V, N, N)).astype(np.float32)
+    got, info = _gpu_run(cuda_lib, N, ang, M, J, y, wpost, wpre, max_views=V)
+    assert info["nnz"] == L * M * J * J
+    sel = [0, 137]
+    want = G.reverse_grangeat(y[sel].astype(np.complex128), wpost[sel].astype(np.float64),
+                              wpre[sel].astype(np.float64), ang, N, J=J)
+    for i, v in enumerate(sel):
+        rel = np.linalg.norm(got[v] - want[i]) / np.linalg.norm(want[i])
+        assert rel < 1e-5, (v, rel)
+
+
+@pytest.mark.gpu
 def test_gpu_axis_aligned_fourier_slice(cuda_lib):
     """Column and row sums of a detector image as the two lines of a view:
     the GPU chain equals the oracle's, whose C3b is pinned to the 2D DFT."""
