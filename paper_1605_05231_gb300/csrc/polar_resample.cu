@@ -106,9 +106,9 @@ __device__ __forceinline__ void sinc_axis_periodic(float u, int n, float (&w)[J]
 // CONTIG: every axis has at least J cells and the grid fewer than 2^31 cells,
 // so taps are consecutive along s and theta and offsets fit in 32 bits.
 template <int J, bool CONTIG>
-__global__ void __launch_bounds__(POLAR_NT) k_polar_resample(const float2* __restrict__ grid, int n_phi, int n_theta,
-                                                            int n_s, const float* __restrict__ targets,
-                                                            long long n, float2* __restrict__ out) {
+__device__ __forceinline__ void polar_resample_targets(const float2* __restrict__ grid, int n_phi, int n_theta,
+                                                       int n_s, const float* __restrict__ targets, long long n,
+                                                       float2* __restrict__ out) {
   const long long stride = (long long)gridDim.x * POLAR_NT;
   for (long long i = (long long)blockIdx.x * POLAR_NT + threadIdx.x; i < n; i += stride) {
     const float us = targets[3 * i], ut = targets[3 * i + 1], up = targets[3 * i + 2];
@@ -177,6 +177,25 @@ __global__ void __launch_bounds__(POLAR_NT) k_polar_resample(const float2* __res
   }
 }
 
+template <int J, bool CONTIG>
+__global__ void __launch_bounds__(POLAR_NT) k_polar_resample(const float2* __restrict__ grid, int n_phi, int n_theta,
+                                                            int n_s, const float* __restrict__ targets,
+                                                            long long n, float2* __restrict__ out) {
+  polar_resample_targets<J, CONTIG>(grid, n_phi, n_theta, n_s, targets, n, out);
+}
+
+// J <= 3 with consecutive taps fits in 32 registers: eight CTAs (64 warps) per
+// SM to hide the latency of the tap loads.  (A minimum-blocks bound on the
+// other instances made the compiler use registers up to its cap, so they keep
+// the plain bound.)
+template <int J>
+__global__ void __launch_bounds__(POLAR_NT, 8) k_polar_resample_contig8(const float2* __restrict__ grid, int n_phi,
+                                                                       int n_theta, int n_s,
+                                                                       const float* __restrict__ targets, long long n,
+                                                                       float2* __restrict__ out) {
+  polar_resample_targets<J, true>(grid, n_phi, n_theta, n_s, targets, n, out);
+}
+
 // one target per thread: blocks start in target order, so the grid rows in
 // use at any time stay within a few phi slices and are re-read from L2
 static int polar_grid_cap() { return 1 << 30; }
@@ -188,10 +207,18 @@ static cudaError_t launch_polar_t(const float2* grid, int n_phi, int n_theta, in
   const int cap = polar_grid_cap();
   const int nb = (int)(blocks < cap ? blocks : cap);
   const bool contig = n_s >= J && n_theta >= J && n_phi >= J && (long long)n_phi * n_theta * n_s < (1LL << 31);
-  if (contig)
-    k_polar_resample<J, true><<<nb, POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets, n, out);
-  else
-    k_polar_resample<J, false><<<nb, POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets, n, out);
+  if constexpr (J <= 3) {
+    if (contig) {
+      k_polar_resample_contig8<J><<<nb, POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets, n, out);
+      return cudaGetLastError();
+    }
+  } else {
+    if (contig) {
+      k_polar_resample<J, true><<<nb, POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets, n, out);
+      return cudaGetLastError();
+    }
+  }
+  k_polar_resample<J, false><<<nb, POLAR_NT, 0, st>>>(grid, n_phi, n_theta, n_s, targets, n, out);
   return cudaGetLastError();
 }
 
